@@ -1,0 +1,193 @@
+"""Seeded synthetic typed graphs shared by the CPU oracle and the GPU path.
+
+This module holds no part of the counting method.  It draws the inputs:
+simple undirected graphs (as symmetric CSR with rows sorted by neighbour id)
+and node types, from the families the paper uses for its synthetic
+experiments (Erdos-Renyi, Chung-Lu, Sec. 8.1 and 8.5) plus a stochastic block
+model and ego networks.  Every draw is a function of its seed only
+(SplitMix64 seeding xoshiro256**, see graphgen.c).
+
+A graph is a dict: n, m, L, row_ptr (int64[n+1]), col (int32[2m]),
+types (uint8[n]), name.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graphgen.c")
+_LIB_PATH = os.path.join(_HERE, "libgraphgen.so")
+_lock = threading.Lock()
+_lib = None
+
+# Fixed seeds of the five standard workloads: 20201029 + k.
+SEED_BASE = 20201029
+
+
+def build(force: bool = False) -> str:
+    """Compile graphgen.c into libgraphgen.so beside it (gcc, -O2)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+            vp = ctypes.c_void_p
+            lib.gg_types_uniform.argtypes = [i64, i32, u64, vp]
+            lib.gg_types_zipf.argtypes = [i64, i32, dbl, u64, vp]
+            lib.gg_er_edges.argtypes = [i64, i64, u64, vp, vp]
+            lib.gg_er_edges.restype = i64
+            lib.gg_chung_lu_edges.argtypes = [i64, i64, dbl, dbl, u64, vp, vp]
+            lib.gg_chung_lu_weights.argtypes = [i64, dbl, dbl, dbl, vp]
+            lib.gg_sbm_edges.argtypes = [i32, vp, vp, i64, u64, vp, vp, vp]
+            lib.gg_edges_to_csr.argtypes = [i64, i64, vp, vp, vp, vp]
+            lib.gg_ego_network.argtypes = [i64, vp, vp, i32, i64, i64, u64, vp, vp, vp, vp, vp, i64]
+            lib.gg_ego_network.restype = i64
+            lib.gg_degree_proportional_node.argtypes = [i64, vp, u64]
+            lib.gg_degree_proportional_node.restype = i32
+            lib.gg_unit_from_seed.argtypes = [u64]
+            lib.gg_unit_from_seed.restype = dbl
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _check(rc: int, what: str) -> None:
+    if rc < 0:
+        raise RuntimeError(f"graphgen: {what} failed (code {rc})")
+
+
+def csr_from_edges(n: int, eu: np.ndarray, ev: np.ndarray, types: np.ndarray, L: int, name: str) -> dict:
+    lib = _load()
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    m = int(eu.shape[0])
+    row_ptr = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(2 * m, dtype=np.int32)
+    _check(lib.gg_edges_to_csr(n, m, _p(eu), _p(ev), _p(row_ptr), _p(col)), "edges_to_csr")
+    return {"n": int(n), "m": m, "L": int(L), "row_ptr": row_ptr, "col": col,
+            "types": np.ascontiguousarray(types, dtype=np.uint8), "name": name}
+
+
+def uniform_types(n: int, L: int, seed: int) -> np.ndarray:
+    t = np.empty(n, dtype=np.uint8)
+    _check(_load().gg_types_uniform(n, L, seed, _p(t)), "types_uniform")
+    return t
+
+
+def zipf_types(n: int, L: int, s: float, seed: int) -> np.ndarray:
+    t = np.empty(n, dtype=np.uint8)
+    _check(_load().gg_types_zipf(n, L, s, seed, _p(t)), "types_zipf")
+    return t
+
+
+def erdos_renyi(n: int, m: int, L: int, seed: int) -> dict:
+    """G(n, m): m distinct pairs uniform over all C(n,2); types uniform over L."""
+    lib = _load()
+    eu = np.empty(m, dtype=np.int32)
+    ev = np.empty(m, dtype=np.int32)
+    _check(lib.gg_er_edges(n, m, seed, _p(eu), _p(ev)), "er_edges")
+    types = uniform_types(n, L, seed ^ 0x7E57)
+    return csr_from_edges(n, eu, ev, types, L, f"ER(n={n},m={m},L={L},seed={seed})")
+
+
+def chung_lu(n: int, m: int, gamma: float, wmax: float, L: int, seed: int,
+             type_zipf: float | None = None) -> dict:
+    """Chung-Lu graph with exactly m edges; types Zipf(type_zipf) or uniform."""
+    lib = _load()
+    eu = np.empty(m, dtype=np.int32)
+    ev = np.empty(m, dtype=np.int32)
+    _check(lib.gg_chung_lu_edges(n, m, gamma, wmax, seed, _p(eu), _p(ev)), "chung_lu_edges")
+    if type_zipf is None:
+        types = uniform_types(n, L, seed ^ 0x7E57)
+    else:
+        types = zipf_types(n, L, type_zipf, seed ^ 0x7E57)
+    return csr_from_edges(n, eu, ev, types, L,
+                          f"CL(n={n},m={m},gamma={gamma},wmax={wmax},L={L},seed={seed})")
+
+
+def sbm(sizes, affinity, m: int, seed: int) -> dict:
+    """Stochastic block model; block b carries node type b."""
+    lib = _load()
+    sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+    B = int(sizes.shape[0])
+    aff = np.ascontiguousarray(affinity, dtype=np.float64).reshape(B, B)
+    n = int(sizes.sum())
+    eu = np.empty(m, dtype=np.int32)
+    ev = np.empty(m, dtype=np.int32)
+    types = np.empty(n, dtype=np.uint8)
+    _check(lib.gg_sbm_edges(B, _p(sizes), _p(aff), m, seed, _p(eu), _p(ev), _p(types)), "sbm_edges")
+    return csr_from_edges(n, eu, ev, types, B, f"SBM(sizes={sizes.tolist()},m={m},seed={seed})")
+
+
+def ego_networks(parent: dict, count: int, n_min: int, n_max: int, m_cap: int, L: int,
+                 seed: int, first: int = 0) -> list:
+    """Ego networks `first .. first+count-1` of a parent graph.
+
+    Graph g: u ~ U(0,1) from seed+g, target size round(n_min * (n_max/n_min)^u),
+    seed node drawn in proportion to degree, breadth-first ball, induced
+    subgraph, at most m_cap edges (uniform subset), types uniform over L.
+    """
+    lib = _load()
+    n_p = parent["n"]
+    rp, col = parent["row_ptr"], parent["col"]
+    mark = np.full(n_p, -1, dtype=np.int32)
+    out = []
+    for g in range(first, first + count):
+        s = seed + g
+        u = lib.gg_unit_from_seed(s)
+        n_t = int(round(n_min * (n_max / n_min) ** u))
+        sn = lib.gg_degree_proportional_node(n_p, _p(rp), s ^ 0x5EED)
+        nodes = np.empty(n_t, dtype=np.int32)
+        n_out = ctypes.c_int64(0)
+        cap = 1 << 16
+        while True:
+            eu = np.empty(cap, dtype=np.int32)
+            ev = np.empty(cap, dtype=np.int32)
+            me = lib.gg_ego_network(n_p, _p(rp), _p(col), sn, n_t, m_cap, s ^ 0xD20F, _p(mark),
+                                    _p(nodes), ctypes.addressof(n_out), _p(eu), _p(ev), cap)
+            if me == -2:
+                cap *= 4
+                continue
+            _check(me, "ego_network")
+            break
+        nn = int(n_out.value)
+        types = uniform_types(nn, L, s ^ 0x7E57)
+        out.append(csr_from_edges(nn, eu[:me], ev[:me], types, L, f"ego(g={g},seed={seed})"))
+    return out
+
+
+# ---------------------------------------------------------------- workloads
+
+def workload(name: str) -> dict:
+    """The standard seeded workloads, by name.
+
+    er_small   ER G(n=2000, m=10000), L=3 uniform types
+    cl_large   Chung-Lu n=2e6, m=2e7, gamma=2.1, max weight 5e4, L=5 Zipf(1.2) types
+    sbm_typed  SBM sizes 500k/300k/150k/50k, affinity 1 between / 0.05 within, m=3e7, L=4
+    """
+    if name == "er_small":
+        return erdos_renyi(2000, 10000, 3, SEED_BASE + 1)
+    if name == "cl_large":
+        return chung_lu(2_000_000, 20_000_000, 2.1, 5.0e4, 5, SEED_BASE + 2, type_zipf=1.2)
+    if name == "sbm_typed":
+        aff = np.full((4, 4), 1.0)
+        np.fill_diagonal(aff, 0.05)
+        return sbm([500_000, 300_000, 150_000, 50_000], aff, 30_000_000, SEED_BASE + 3)
+    raise KeyError(name)

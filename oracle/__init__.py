@@ -1,0 +1,192 @@
+"""CPU oracle for typed-graphlet counting -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg may import this package.  The GPU library neither imports
+nor links it, and no product code path may fall back to it.
+
+Three independent routes over the same output layout (see oracle.c):
+
+* :func:`paper`  -- Alg. 1-3 and Lemmas 1-4 of the paper, per edge.
+* :func:`table3` -- each orbit from its Table 3 set-builder definition.
+* :func:`brute`  -- all 3- and 4-node subsets, classified by induced degrees.
+
+All counts are exact int64.  Parity with these is the acceptance bar for
+the GPU path (bit-exact).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ERRORS = {0: "ok", 1: "invalid argument", 2: "invalid graph", 3: "out of memory",
+          4: "inconsistent counts (a global sum not divisible by |E(H)|, a negative count or a rank out of range)"}
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc -O2, OpenMP when available) into liboracle.so."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        base = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC]
+        try:
+            subprocess.check_call(base[:4] + ["-fopenmp"] + base[4:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_SIGS = {
+    "oracle_per_edge_slots": ("i32 i32", "i64"),
+    "oracle_global_slots": ("i32 i32", "i64"),
+    "oracle_pair_index": ("i32 i32 i32", "i64"),
+    "oracle_multiset_rank": ("i32 i32 vp", "i64"),
+    "oracle_paper": ("i64 vp vp vp i32 i32 vp vp i32", "i32"),
+    "oracle_paper_edges": ("i64 vp vp vp i32 i32 vp i64 vp vp i32", "i32"),
+    "oracle_table3": ("i64 vp vp vp i32 vp vp", "i32"),
+    "oracle_brute": ("i64 vp vp vp i32 vp vp", "i32"),
+    "oracle_edges": ("i64 vp vp vp i32 vp vp", "i32"),
+    "oracle_validate": ("i64 vp vp vp i32", "i32"),
+    "oracle_max_threads": ("", "i32"),
+}
+_CT = {"i64": ctypes.c_int64, "i32": ctypes.c_int32, "vp": ctypes.c_void_p}
+
+
+def open_library(path: str):
+    """Load an oracle build (the default one, or a variant a test compiled)."""
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = [_CT[a] for a in args.split()]
+        f.restype = _CT[res]
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = open_library(_LIB_PATH)
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _args(g):
+    rp = np.ascontiguousarray(g["row_ptr"], dtype=np.int64)
+    col = np.ascontiguousarray(g["col"], dtype=np.int32)
+    ty = np.ascontiguousarray(g["types"], dtype=np.uint8)
+    return rp, col, ty
+
+
+def _check(rc):
+    if rc != 0:
+        raise OracleError(ERRORS.get(rc, f"error {rc}"))
+
+
+def per_edge_slots(L: int, k: int = 4, lib=None) -> int:
+    lib = lib or _load()
+    return int(lib.oracle_per_edge_slots(L, k))
+
+
+def global_slots(L: int, k: int = 4, lib=None) -> int:
+    lib = lib or _load()
+    return int(lib.oracle_global_slots(L, k))
+
+
+def pair_index(L: int, t: int, tp: int, lib=None) -> int:
+    lib = lib or _load()
+    return int(lib.oracle_pair_index(L, t, tp))
+
+
+def multiset_rank(L: int, types, lib=None) -> int:
+    lib = lib or _load()
+    a = np.ascontiguousarray(types, dtype=np.int32)
+    return int(lib.oracle_multiset_rank(L, len(a), _p(a)))
+
+
+def max_threads(lib=None) -> int:
+    lib = lib or _load()
+    return int(lib.oracle_max_threads())
+
+
+def validate(g, lib=None) -> int:
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    return int(lib.oracle_validate(g["n"], _p(rp), _p(col), _p(ty), g["L"]))
+
+
+def edges(g, lib=None):
+    """(src, dst) int64 arrays in edge-id order, src < dst."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    m = int(rp[-1]) // 2
+    s = np.empty(m, dtype=np.int64)
+    d = np.empty(m, dtype=np.int64)
+    _check(lib.oracle_edges(g["n"], _p(rp), _p(col), _p(ty), g["L"], _p(s), _p(d)))
+    return s, d
+
+
+def paper(g, k: int = 4, per_edge: bool = True, nthreads: int = 0, lib=None):
+    """Alg. 1-3 + Lemmas 1-4 on every edge -> (per_edge int64 [m,S] or None, global int64 [G])."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    L = g["L"]
+    m = int(rp[-1]) // 2
+    pe = np.zeros((m, per_edge_slots(L, k, lib)), dtype=np.int64) if per_edge else None
+    gl = np.zeros(global_slots(L, k, lib), dtype=np.int64)
+    _check(lib.oracle_paper(g["n"], _p(rp), _p(col), _p(ty), L, k, _p(pe), _p(gl), nthreads))
+    return pe, gl
+
+
+def paper_edges(g, edge_ids, k: int = 4, nthreads: int = 0, lib=None):
+    """Alg. 1-3 + Lemmas on selected edges -> (rows int64 [len,S], raw per-graphlet sums int64 [G])."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    L = g["L"]
+    ids = np.ascontiguousarray(edge_ids, dtype=np.int64)
+    pe = np.zeros((len(ids), per_edge_slots(L, k, lib)), dtype=np.int64)
+    sums = np.zeros(global_slots(L, k, lib), dtype=np.int64)
+    _check(lib.oracle_paper_edges(g["n"], _p(rp), _p(col), _p(ty), L, k, _p(ids), len(ids),
+                                      _p(pe), _p(sums), nthreads))
+    return pe, sums
+
+
+def table3(g, lib=None):
+    """Every orbit from Table 3's definitions -> (per_edge int64 [m,S], global int64 [G])."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    L = g["L"]
+    m = int(rp[-1]) // 2
+    pe = np.zeros((m, per_edge_slots(L, 4, lib)), dtype=np.int64)
+    gl = np.zeros(global_slots(L, 4, lib), dtype=np.int64)
+    _check(lib.oracle_table3(g["n"], _p(rp), _p(col), _p(ty), L, _p(pe), _p(gl)))
+    return pe, gl
+
+
+def brute(g, lib=None):
+    """All 3- and 4-subsets -> (per_edge int64 [m,S], global int64 [G]).  Small n only."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    L = g["L"]
+    m = int(rp[-1]) // 2
+    pe = np.zeros((m, per_edge_slots(L, 4, lib)), dtype=np.int64)
+    gl = np.zeros(global_slots(L, 4, lib), dtype=np.int64)
+    _check(lib.oracle_brute(g["n"], _p(rp), _p(col), _p(ty), L, _p(pe), _p(gl)))
+    return pe, gl

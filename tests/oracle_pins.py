@@ -1,0 +1,240 @@
+"""Pin helpers shared by the oracle tests (CPU only).
+
+Each helper states the expected counts of a graph family or an identity
+that the mathematics fixes, independently of the oracle's code, so that a
+mistake in the oracle fails a check here.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+import os
+
+import numpy as np
+
+import graphgen
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+# 4-node orbit numbering (Table 3): g3 4-path end edge, g4 4-path centre edge,
+# g5 4-star, g6 4-cycle, g7 tailed-triangle tail, g8 tailed-triangle edge
+# opposite the degree-3 node, g9 tailed-triangle edge at the degree-3 node,
+# g10 chordal-cycle outer edge, g11 chordal-cycle chord, g12 4-clique.
+GRAPHLET_EDGES = {1: 2, 2: 3, 3: 3, 4: 3, 5: 4, 6: 4, 7: 5, 8: 6}
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def graph_from_edges(n, edges, types, L, name="g"):
+    e = np.array(sorted((min(a, b), max(a, b)) for a, b in edges), dtype=np.int32).reshape(-1, 2)
+    return graphgen.csr_from_edges(n, e[:, 0], e[:, 1], np.array(types, dtype=np.uint8), L, name)
+
+
+def random_graph(n, p, L, seed):
+    rng = np.random.default_rng(seed)
+    edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+    types = rng.integers(0, L, n)
+    return graph_from_edges(n, edges, types, L, f"G({n},{p},L={L},seed={seed})")
+
+
+# ------------------------------------------------------------ layout, by enumeration
+
+def pairs(L):
+    """(t,t') with t <= t' in lexicographic order (itertools order)."""
+    return list(itertools.combinations_with_replacement(range(L), 2))
+
+
+def multisets(L, K):
+    """sorted K-multisets over [0,L) in lexicographic order (itertools order)."""
+    return list(itertools.combinations_with_replacement(range(L), K))
+
+
+def per_edge_slot(L, orbit, t, tp=None):
+    """slot of (orbit, types) in a per-edge row: orbit 1 (3-path) / 2 (triangle)
+    take one type, orbits 3..12 take the unordered pair {t, tp}."""
+    if orbit in (1, 2):
+        return (orbit - 1) * L + t
+    P = L * (L + 1) // 2
+    return 2 * L + (orbit - 3) * P + pairs(L).index(tuple(sorted((t, tp))))
+
+
+def global_slot(L, graphlet, types):
+    """slot of (graphlet, type multiset) in the global vector; graphlet 0 is
+    the typed edge, 1 the 3-path, 2 the triangle, 3..8 the 4-node graphlets."""
+    sizes = [math.comb(L + 1, 2)] + [math.comb(L + 2, 3)] * 2 + [math.comb(L + 3, 4)] * 6
+    K = 2 if graphlet == 0 else (3 if graphlet <= 2 else 4)
+    return sum(sizes[:graphlet]) + multisets(L, K).index(tuple(sorted(types)))
+
+
+def global_size(L):
+    return math.comb(L + 1, 2) + 2 * math.comb(L + 2, 3) + 6 * math.comb(L + 3, 4)
+
+
+def edge_list(g):
+    """edge ids -> (u, v), u < v, lexicographic."""
+    out = []
+    rp, col = g["row_ptr"], g["col"]
+    for u in range(g["n"]):
+        for v in sorted(col[rp[u]:rp[u + 1]]):
+            if v > u:
+                out.append((u, int(v)))
+    return out
+
+
+# ------------------------------------------------------------- closed forms
+
+def expected_clique(types, L):
+    """K_n: every pair adjacent.  Per edge, T^t = all other nodes of type t,
+    S_i = S_j = I = empty, so only g2 and g12 (and g11 = 0) are nonzero."""
+    n = len(types)
+    cnt = np.bincount(types, minlength=L)
+    m = n * (n - 1) // 2
+    S = 2 * L + 10 * L * (L + 1) // 2
+    pe = np.zeros((m, S), dtype=np.int64)
+    edges = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    for e, (a, b) in enumerate(edges):
+        c = cnt.copy()
+        c[types[a]] -= 1
+        c[types[b]] -= 1
+        for t in range(L):
+            pe[e, per_edge_slot(L, 2, t)] = c[t]
+        for t, tp in pairs(L):
+            pe[e, per_edge_slot(L, 12, t, tp)] = math.comb(int(c[t]), 2) if t == tp else int(c[t]) * int(c[tp])
+    gl = np.zeros(global_size(L), dtype=np.int64)
+    for K, gid in ((2, 0), (3, 2), (4, 8)):
+        for ms in multisets(L, K):
+            mult = np.bincount(ms, minlength=L)
+            gl[global_slot(L, gid, ms)] = int(np.prod([math.comb(int(cnt[t]), int(mult[t])) for t in range(L)]))
+    return edges, pe, gl
+
+
+def expected_star(center_type, leaf_types, L):
+    """K_{1,n}: per edge (centre, leaf), S_centre = the other leaves, all
+    pairs of them non-adjacent: g1 and g5 only."""
+    n = len(leaf_types)
+    types = [center_type] + list(leaf_types)
+    S = 2 * L + 10 * L * (L + 1) // 2
+    pe = np.zeros((n, S), dtype=np.int64)
+    edges = [(0, b) for b in range(1, n + 1)]
+    for e, (_, b) in enumerate(edges):
+        others = [types[x] for x in range(1, n + 1) if x != b]
+        for t in others:
+            pe[e, per_edge_slot(L, 1, t)] += 1
+        for x, y in itertools.combinations(others, 2):
+            pe[e, per_edge_slot(L, 5, x, y)] += 1
+    gl = np.zeros(global_size(L), dtype=np.int64)
+    for _, b in edges:
+        gl[global_slot(L, 0, (center_type, types[b]))] += 1
+    for x, y in itertools.combinations(leaf_types, 2):
+        gl[global_slot(L, 1, (center_type, x, y))] += 1
+    for x, y, z in itertools.combinations(leaf_types, 3):
+        gl[global_slot(L, 4, (center_type, x, y, z))] += 1
+    return types, edges, pe, gl
+
+
+def expected_cycle(types, L):
+    """C_n, n >= 5: per edge (v_k, v_k+1) the 3-paths through v_k-1 and v_k+2,
+    4-path ends (v_k-2, v_k-1) and (v_k+2, v_k+3), 4-path centre
+    (v_k-1, v_k+2).  For n = 5 the two ends share v_k+3 = v_k-2."""
+    n = len(types)
+    assert n >= 5
+    S = 2 * L + 10 * L * (L + 1) // 2
+    edges = sorted((min(k, (k + 1) % n), max(k, (k + 1) % n)) for k in range(n))
+    pe = np.zeros((n, S), dtype=np.int64)
+    for k in range(n):
+        a, b = k, (k + 1) % n
+        e = edges.index((min(a, b), max(a, b)))
+        ty = lambda x: types[x % n]
+        pe[e, per_edge_slot(L, 1, ty(k - 1))] += 1
+        pe[e, per_edge_slot(L, 1, ty(k + 2))] += 1
+        pe[e, per_edge_slot(L, 3, ty(k - 1), ty(k - 2))] += 1
+        pe[e, per_edge_slot(L, 3, ty(k + 2), ty(k + 3))] += 1
+        pe[e, per_edge_slot(L, 4, ty(k - 1), ty(k + 2))] += 1
+    gl = np.zeros(global_size(L), dtype=np.int64)
+    for k in range(n):
+        gl[global_slot(L, 0, (types[k], types[(k + 1) % n]))] += 1
+        gl[global_slot(L, 1, (types[k], types[(k + 1) % n], types[(k + 2) % n]))] += 1
+        gl[global_slot(L, 3, tuple(types[(k + d) % n] for d in range(4)))] += 1
+    return edges, pe, gl
+
+
+def expected_complete_bipartite(a, b):
+    """K_{a,b} with node type = side (0 for the a side, 1 for the b side).
+    Per edge (l, r): S_l = the other b-1 right nodes, S_r = the other a-1
+    left nodes, T = I = empty; every left-right pair is adjacent (4-cycles),
+    no same-side pair is (4-stars)."""
+    L = 2
+    S = 2 * L + 10 * 3
+    types = [0] * a + [1] * b
+    edges = [(l, a + r) for l in range(a) for r in range(b)]
+    pe = np.zeros((len(edges), S), dtype=np.int64)
+    for e in range(len(edges)):
+        pe[e, per_edge_slot(L, 1, 1)] = b - 1
+        pe[e, per_edge_slot(L, 1, 0)] = a - 1
+        pe[e, per_edge_slot(L, 6, 0, 1)] = (a - 1) * (b - 1)
+        pe[e, per_edge_slot(L, 5, 1, 1)] = math.comb(b - 1, 2)
+        pe[e, per_edge_slot(L, 5, 0, 0)] = math.comb(a - 1, 2)
+    gl = np.zeros(global_size(L), dtype=np.int64)
+    gl[global_slot(L, 0, (0, 1))] = a * b
+    gl[global_slot(L, 1, (0, 1, 1))] = a * math.comb(b, 2)
+    gl[global_slot(L, 1, (0, 0, 1))] = b * math.comb(a, 2)
+    gl[global_slot(L, 5, (0, 0, 1, 1))] = math.comb(a, 2) * math.comb(b, 2)
+    gl[global_slot(L, 4, (0, 1, 1, 1))] = a * math.comb(b, 3)
+    gl[global_slot(L, 4, (0, 0, 0, 1))] = b * math.comb(a, 3)
+    return types, edges, pe, gl
+
+
+def expected_path(types, L):
+    """P_n (nodes 0..n-1 in a line)."""
+    n = len(types)
+    S = 2 * L + 10 * L * (L + 1) // 2
+    edges = [(k, k + 1) for k in range(n - 1)]
+    pe = np.zeros((n - 1, S), dtype=np.int64)
+    for e, (a, b) in enumerate(edges):
+        if a >= 1:
+            pe[e, per_edge_slot(L, 1, types[a - 1])] += 1
+        if b + 1 <= n - 1:
+            pe[e, per_edge_slot(L, 1, types[b + 1])] += 1
+        if a >= 2:
+            pe[e, per_edge_slot(L, 3, types[a - 1], types[a - 2])] += 1
+        if b + 2 <= n - 1:
+            pe[e, per_edge_slot(L, 3, types[b + 1], types[b + 2])] += 1
+        if a >= 1 and b + 1 <= n - 1:
+            pe[e, per_edge_slot(L, 4, types[a - 1], types[b + 1])] += 1
+    gl = np.zeros(global_size(L), dtype=np.int64)
+    for k in range(n - 1):
+        gl[global_slot(L, 0, types[k:k + 2])] += 1
+    for k in range(n - 2):
+        gl[global_slot(L, 1, types[k:k + 3])] += 1
+    for k in range(n - 3):
+        gl[global_slot(L, 3, types[k:k + 4])] += 1
+    return edges, pe, gl
+
+
+# ------------------------------------------------------------- untyped identities
+
+def untyped_identities(g, gl_untyped):
+    """Standard identities between degree sums and untyped graphlet counts
+    (L = 1 global vector: [edges, 3-path, triangle, 4-path, 4-star, 4-cycle,
+    tailed-triangle, chordal-cycle, 4-clique]).  Returns (lhs, rhs) pairs."""
+    deg = np.diff(g["row_ptr"]).astype(object)
+    _, n3p, ntri, np4, nstar, nc4, npaw, ndia, nk4 = [int(x) for x in gl_untyped]
+    out = []
+    out.append((sum(d * (d - 1) // 2 for d in deg), n3p + 3 * ntri))
+    out.append((sum(d * (d - 1) * (d - 2) // 6 for d in deg), nstar + npaw + 2 * ndia + 4 * nk4))
+    rp, col = g["row_ptr"], g["col"]
+    s = 0
+    for u in range(g["n"]):
+        for v in col[rp[u]:rp[u + 1]]:
+            if v > u:
+                s += (deg[u] - 1) * (deg[v] - 1)
+    out.append((s - 3 * ntri, np4 + 4 * nc4 + 2 * npaw + 6 * ndia + 12 * nk4))
+    return out
