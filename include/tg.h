@@ -1,0 +1,231 @@
+/*
+ * tg.h -- exact typed-graphlet counting on one GPU (C ABI).
+ *
+ * Computes, for an undirected simple graph whose nodes carry one of L types,
+ * the two problems of "Heterogeneous Graphlets" (Rossi et al., TKDD 2020):
+ *
+ *   Problem 1 (Sec. 4, "local typed graphlet counting"): for every edge
+ *     (i,j), the count of every typed 3- and 4-node graphlet orbit that
+ *     contains the edge.
+ *   Problem 2 (Sec. 6, "global typed graphlet counting"): the total count of
+ *     every typed 2-, 3- and 4-node graphlet, C_H = (1/|E(H)|) x^T e.
+ *
+ * Every count is an exact integer.  Node types only (Alg. 1-3 use node
+ * types; the edge types of Def. 1 are not part of this library).
+ *
+ * ------------------------------------------------------------------------
+ * Conventions
+ *
+ * Graph input: a symmetric CSR.  row_ptr (int64, n+1 entries, row_ptr[0] =
+ *   0, non-decreasing, row_ptr[n] = nnz), col (int32, nnz entries, each in
+ *   [0,n)), node_types (uint8, n entries, each in [0,L)).  Every undirected
+ *   edge {u,v} appears once in row u and once in row v; rows may be
+ *   unsorted.  Self-loops, repeated entries and one-sided entries make the
+ *   graph invalid.  1 <= L <= TG_MAX_TYPES.
+ *
+ * Pointers: any pointer argument that carries graph data or results may be
+ *   host memory (pageable or pinned) or device memory of the current device;
+ *   the library inspects each one.  Host inputs are copied in on the given
+ *   stream; host outputs are copied out and the call then synchronises the
+ *   stream.  The library never frees or keeps caller memory.
+ *
+ * Streams: every call that takes `stream` (a cudaStream_t, NULL = legacy
+ *   default stream) is stream-ordered.  Device outputs are complete when the
+ *   stream reaches the call's end.
+ *
+ * Edge ids: the edges {u,v}, u < v in the caller's node ids, numbered
+ *   0..m-1 in lexicographic order of (u,v).  For a batch (tg_build_batch)
+ *   the node id ranges of the graphs follow each other, so graph g's edges
+ *   form the id range [edge_off[g], edge_off[g+1]).
+ *
+ * Per-edge output (Problem 1): uint32 rows of S(L) slots, row e = edge e.
+ *   P = L(L+1)/2 unordered type pairs; pair(t,t') for t <= t' is the position
+ *   of (t,t') in the lexicographic list (0,0),(0,1),...,(0,L-1),(1,1),...
+ *     slot t          (0 <= t < L): typed 3-paths through the edge whose
+ *                     third node has type t: |S_i^t| + |S_j^t| (Cor. 3)
+ *     slot L + t:     typed triangles, |T_ij^t| (Cor. 1)
+ *     slot 2L + (o-3)P + pair(t,t'), o = 3..12: orbit g_o (Table 3) with the
+ *                     two other nodes of types {t,t'}.  Orbits: g3 4-path
+ *                     end edge, g4 4-path centre edge, g5 4-star, g6 4-cycle,
+ *                     g7 tailed-triangle tail, g8 tailed-triangle edge
+ *                     opposite the degree-3 node, g9 tailed-triangle edge at
+ *                     the degree-3 node, g10 chordal-cycle outer edge, g11
+ *                     chordal-cycle chord, g12 4-clique.
+ *   S(L) = 2L + 10P for k = 4; S(L) = 2L for k = 3 (3-node slots only).
+ *   A count above 2^32-1 is stored as 2^32-1 and raises TG_ERR_OVERFLOW
+ *   in the status word; global totals are always exact.
+ *
+ * Global output (Problem 2): int64, G(L) slots per graph, in blocks
+ *     block 0  typed edges           C(L+1,2) type multisets of size 2
+ *     block 1  typed 3-paths         C(L+2,3) multisets of size 3
+ *     block 2  typed triangles       C(L+2,3)
+ *     blocks 3..8 typed 4-paths, 4-stars, 4-cycles, tailed-triangles,
+ *              chordal-cycles, 4-cliques   C(L+3,4) multisets of size 4 each
+ *   (k = 3: blocks 0..2 only).  Inside a block, slot = position of the
+ *   sorted type multiset in the lexicographic list of sorted multisets.
+ *   The block sizes are Table 2's ((L multichoose K)).
+ *
+ * Errors: host-detectable errors are returned at once and change nothing.
+ *   Errors found on the device (invalid graph, overflow, a bounded wait that
+ *   ran out, an internal consistency check) are OR-ed into the graph's
+ *   device status word, which tg_query_status returns.  No call traps,
+ *   aborts or exits.
+ * ------------------------------------------------------------------------
+ */
+#ifndef TG_H_
+#define TG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TG_MAX_TYPES 8
+#define TG_ABI_VERSION 1
+
+typedef enum {
+    TG_OK = 0,
+    TG_ERR_INVALID_ARG = 1,     /* bad argument (size, k, NULL where required) */
+    TG_ERR_INVALID_GRAPH = 2,   /* not a simple symmetric CSR, or a type >= L */
+    TG_ERR_TOO_MANY_TYPES = 3,  /* L < 1 or L > TG_MAX_TYPES */
+    TG_ERR_OOM = 4,             /* device memory exhausted */
+    TG_ERR_OVERFLOW = 5,        /* a per-edge count exceeded 2^32-1 (saturated) */
+    TG_ERR_TIMEOUT = 6,         /* a bounded device wait ran out */
+    TG_ERR_CUDA = 7,            /* a CUDA runtime call failed */
+    TG_ERR_INTERNAL = 8,        /* an internal consistency check failed */
+    TG_ERR_TOO_LARGE = 9        /* graph exceeds an index-width limit */
+} tg_status;
+
+typedef struct tg_graph tg_graph;   /* opaque; owns device copies of the graph */
+
+/* Slot layout for (L, k).  Pure host function. */
+typedef struct {
+    int32_t L, k;
+    int64_t pairs;               /* P = L(L+1)/2 */
+    int64_t per_edge_slots;      /* S(L) */
+    int64_t global_slots;        /* G(L) */
+    int64_t orbit_offset[13];    /* per-edge slot of orbit o's first pair; o = 1 (3-path), 2 (triangle),
+                                    3..12; entry 0 unused */
+    int64_t global_block_offset[9];
+    int64_t global_block_size[9];
+    int32_t graphlet_edges[9];   /* |E(H)| of each global block: 1,2,3,3,3,4,4,5,6 */
+} tg_layout_t;
+
+/* Tuning knobs (0 = library default).  Results never depend on them. */
+typedef struct {
+    int32_t light_edge_max_degree;    /* edges with min(d_i,d_j) <= this: warp per edge */
+    int32_t light_anchor_max_wedges;  /* wedge anchors with at most this many wedges: warp per anchor */
+    int32_t anchor_table_budget_mb;   /* device memory for per-CTA wedge tables */
+    int32_t ctas_per_sm;              /* resident CTAs per SM for the per-edge kernels */
+    int32_t reserved[4];
+} tg_options;
+
+/* ---- layout ---------------------------------------------------------- */
+
+/* Fills *out for L types and k in {3,4}.  Errors: TG_ERR_TOO_MANY_TYPES,
+ * TG_ERR_INVALID_ARG. */
+tg_status tg_layout(int32_t L, int32_t k, tg_layout_t *out);
+
+/* Default tuning knobs. */
+void tg_default_options(tg_options *opt);
+
+/* ---- graph handles --------------------------------------------------- */
+
+/* Builds a device handle for one graph (Sec. 4.1, Def. 6-7: typed
+ * neighbourhoods).  The library copies what it needs; the caller may free
+ * its inputs when the stream reaches the end of the call.  On the device it
+ * validates the graph, orders nodes by (degree, id), sorts every adjacency
+ * list by (type, id) with per-type offsets (typed neighbourhoods Gamma_i^t
+ * and typed degrees d_i^t), numbers the edges and precomputes per-node
+ * typed degree sums.  opt may be NULL.  Synchronises `stream` once (to size
+ * work lists).  Errors: TG_ERR_INVALID_ARG, TG_ERR_TOO_MANY_TYPES,
+ * TG_ERR_INVALID_GRAPH, TG_ERR_OOM, TG_ERR_TOO_LARGE, TG_ERR_CUDA; on error
+ * *out is NULL. */
+tg_status tg_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                   const uint8_t *node_types, int32_t L, const tg_options *opt,
+                   void *stream, tg_graph **out);
+
+/* Builds one handle for `ngraphs` independent graphs given as one
+ * block-diagonal CSR: graph g owns nodes [node_off[g], node_off[g+1]) (host
+ * array of ngraphs+1 int64, node_off[0] = 0, node_off[ngraphs] = n) and no
+ * edge joins two graphs.  Counting the handle counts every graph at once
+ * (pattern: batched small graphs) and writes per-graph global totals.
+ * Errors as tg_build. */
+tg_status tg_build_batch(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col, const uint8_t *node_types,
+                         int32_t L, const tg_options *opt, void *stream, tg_graph **out);
+
+/* Releases everything the handle owns (after synchronising its stream). */
+void tg_free(tg_graph *g);
+
+int64_t tg_num_nodes(const tg_graph *g);
+int64_t tg_num_edges(const tg_graph *g);
+int32_t tg_num_graphs(const tg_graph *g);
+int32_t tg_num_types(const tg_graph *g);
+/* Device memory the handle holds now, in bytes. */
+int64_t tg_device_bytes(const tg_graph *g);
+
+/* Edge id -> endpoints in the caller's node ids: src[e] < dst[e], int32,
+ * m entries each (host or device).  Stream-ordered on the build stream. */
+tg_status tg_edge_endpoints(const tg_graph *g, int32_t *src, int32_t *dst);
+
+/* Per-graph first edge ids: out[ngraphs+1] (host). */
+tg_status tg_edge_offsets(const tg_graph *g, int64_t *out);
+
+/* ---- counting -------------------------------------------------------- */
+
+/* Problem 1 + Problem 2 for every graph of the handle.
+ *   k = 3: typed triangles and 3-paths (Cor. 1-3).
+ *   k = 4: additionally the ten typed 4-node orbits (Alg. 1-3, Lemmas 1-4,
+ *          Table 3) and the six typed 4-node graphlets (Sec. 4.4).
+ * per_edge_out: uint32 [m][S(L)] or NULL (global totals only).
+ * global_out:   int64 [ngraphs][G(L)] or NULL.
+ * Working memory is allocated on the first call and kept by the handle.
+ * Errors: TG_ERR_INVALID_ARG, TG_ERR_OOM, TG_ERR_CUDA (device-detected
+ * errors go to the status word). */
+tg_status tg_count(tg_graph *g, int32_t k, uint32_t *per_edge_out, int64_t *global_out,
+                   void *stream);
+
+/* As tg_count for the edge id range [e_begin, e_end) only (chunked or
+ * sharded runs; edges are independent given the graph, Sec. 4.7).
+ * per_edge_out row 0 is edge e_begin.  global_accum (int64 [ngraphs][G],
+ * may be NULL) receives, added to its contents, the raw per-edge sums
+ * sum_e x_e of the range -- not yet divided by |E(H)|; tg_finalize_global
+ * turns the sum over all ranges into totals.  The per-graph preparation
+ * (typed triangle counts, wedge tables) runs once per handle and k. */
+tg_status tg_count_range(tg_graph *g, int32_t k, int64_t e_begin, int64_t e_end,
+                         uint32_t *per_edge_out, int64_t *global_accum, void *stream);
+
+/* Divides raw per-graphlet edge sums by |E(H)| (Sec. 6).  Host arrays of
+ * ngraphs*G(L) int64.  Returns TG_ERR_INTERNAL if a sum is not a multiple. */
+tg_status tg_finalize_global(int32_t L, int32_t k, int32_t ngraphs, const int64_t *raw,
+                             int64_t *out);
+
+/* Batched form: counts every graph of a batch handle with the whole
+ * sequence of kernels captured once into a CUDA graph and replayed on later
+ * calls with the same (k, per_edge_out, global_out, stream).  Results are
+ * identical to tg_count. */
+tg_status tg_count_batch(tg_graph *g, int32_t k, uint32_t *per_edge_out, int64_t *global_out,
+                         void *stream);
+
+/* Synchronises the handle's last stream and returns the first error
+ * recorded in its device status word (TG_OK if none), then clears it. */
+tg_status tg_query_status(tg_graph *g);
+
+/* Static description of a status code. */
+const char *tg_status_string(tg_status s);
+
+/* Number of kernel launches issued by the last tg_count / tg_count_range /
+ * tg_count_batch call on this handle (a CUDA-graph replay counts its
+ * kernels). */
+int64_t tg_last_launch_count(const tg_graph *g);
+
+/* Library ABI version (TG_ABI_VERSION). */
+int32_t tg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TG_H_ */

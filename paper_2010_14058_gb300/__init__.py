@@ -1,0 +1,52 @@
+"""Exact typed-graphlet counting on one GB300 (sm_103a).
+
+The computation lives in libtg.so (CUDA, C ABI in include/tg.h); this
+package is its Python binding plus device-memory plumbing through PyTorch.
+
+    import paper_2010_14058_gb300 as tg
+    g = tg.tg_build(row_ptr, col, types, L)          # tensors or arrays
+    tg.tg_count(g, 4, per_edge_out, global_out)      # uint32 [m,S], int64 [G]
+
+``count`` below does the same for a graph given as host arrays.
+"""
+from __future__ import annotations
+
+from .tg import (Graph, LibraryMissing, STATUS, STATUS_CODE, TGError, TG_MAX_TYPES, load, tg_abi_version,
+                 tg_build, tg_build_batch, tg_count, tg_count_batch, tg_count_range, tg_edge_endpoints,
+                 tg_edge_offsets, tg_finalize_global, tg_free, tg_layout, tg_query_status, tg_status_string)
+
+__all__ = ["Graph", "LibraryMissing", "STATUS", "STATUS_CODE", "TGError", "TG_MAX_TYPES", "load", "tg_abi_version",
+           "tg_build", "tg_build_batch", "tg_count", "tg_count_batch", "tg_count_range", "tg_edge_endpoints",
+           "tg_edge_offsets", "tg_finalize_global", "tg_free", "tg_layout", "tg_query_status", "tg_status_string",
+           "to_device", "count"]
+
+
+def to_device(graph: dict, device="cuda"):
+    """(row_ptr int64, col int32, types uint8) as device tensors."""
+    import torch
+    rp = torch.as_tensor(graph["row_ptr"], dtype=torch.int64).to(device)
+    col = torch.as_tensor(graph["col"], dtype=torch.int32).to(device)
+    ty = torch.as_tensor(graph["types"], dtype=torch.uint8).to(device)
+    return rp, col, ty
+
+
+def count(graph: dict, k: int = 4, per_edge: bool = True, device="cuda", options=None, check=True):
+    """Builds and counts one graph on the GPU.
+
+    Returns (per_edge uint32 tensor [m, S] or None, global int64 tensor [G]),
+    both on `device`.  Raises TGError if the device status word reports an
+    error (check=True).
+    """
+    import torch
+    rp, col, ty = to_device(graph, device)
+    g = tg_build(rp, col, ty, graph["L"], options=options)
+    lay = tg_layout(graph["L"], k)
+    pe = torch.empty((g.m, lay["per_edge_slots"]), dtype=torch.int32, device=device) if per_edge else None
+    gl = torch.empty(lay["global_slots"], dtype=torch.int64, device=device)
+    tg_count(g, k, pe, gl)
+    if check:
+        st = tg_query_status(g)
+        if st != 0:
+            raise TGError(st, "device status")
+    g.free()
+    return pe, gl

@@ -1,0 +1,331 @@
+// tg_api.cu -- the extern "C" entry points of libtg (declared in include/tg.h).
+//
+// Every entry catches the library's internal errors and returns a tg_status;
+// nothing here traps, aborts or exits.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tg_host.hpp"
+
+using tg::Error;
+using tg::Graph;
+
+namespace {
+
+template <class F>
+tg_status guarded(F f) {
+    try {
+        f();
+        return TG_OK;
+    } catch (const Error &e) {
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        return TG_ERR_OOM;
+    } catch (...) {
+        return TG_ERR_INTERNAL;
+    }
+}
+
+__global__ void k_endpoints(int64_t m, const int32_t *__restrict__ e_lo, const int32_t *__restrict__ e_hi,
+                            const int32_t *__restrict__ old_of, int32_t *src, int32_t *dst) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    int32_t a = old_of[e_lo[e]], b = old_of[e_hi[e]];
+    src[e] = a < b ? a : b;
+    dst[e] = a < b ? b : a;
+}
+
+void check_types(int32_t L) {
+    if (L < 1 || L > TG_MAX_TYPES) throw Error{TG_ERR_TOO_MANY_TYPES, "L"};
+}
+
+void build_common(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                  const int32_t *col, const uint8_t *types, int32_t L, const tg_options *opt, void *stream,
+                  tg_graph **out) {
+    if (!out) throw Error{TG_ERR_INVALID_ARG, "out"};
+    *out = nullptr;
+    check_types(L);
+    if (ngraphs < 1 || !node_off || n < 0 || nnz < 0 || (nnz & 1) || !row_ptr) throw Error{TG_ERR_INVALID_ARG, "sizes"};
+    if ((n > 0 && !types) || (nnz > 0 && !col)) throw Error{TG_ERR_INVALID_ARG, "NULL array"};
+    if (node_off[0] != 0 || node_off[ngraphs] != n) throw Error{TG_ERR_INVALID_ARG, "node_off"};
+    for (int g = 0; g < ngraphs; ++g)
+        if (node_off[g + 1] < node_off[g]) throw Error{TG_ERR_INVALID_ARG, "node_off"};
+    if (n >= ((int64_t)1 << tg::kTypeShift) || nnz >= ((int64_t)1 << 31)) throw Error{TG_ERR_TOO_LARGE, "index width"};
+    tg_options o;
+    tg::fill_defaults(&o);
+    if (opt) {
+        if (opt->light_edge_max_degree > 0) o.light_edge_max_degree = opt->light_edge_max_degree;
+        if (opt->light_anchor_max_wedges > 0) o.light_anchor_max_wedges = opt->light_anchor_max_wedges;
+        if (opt->anchor_table_budget_mb > 0) o.anchor_table_budget_mb = opt->anchor_table_budget_mb;
+        if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
+    }
+    o.light_edge_max_degree = std::min(o.light_edge_max_degree, 256);     // warp T list capacity
+    o.light_anchor_max_wedges = std::min(o.light_anchor_max_wedges, 2048);
+    o.ctas_per_sm = std::min(std::max(o.ctas_per_sm, 1), 8);
+    tg_graph *h = new tg_graph();
+    try {
+        tg::build_graph(h->g, ngraphs, node_off, n, nnz, row_ptr, col, types, L, o, (cudaStream_t)stream);
+    } catch (...) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        delete h;
+        throw;
+    }
+    *out = h;
+}
+
+// device pointer for an output, staged through `stage` when the caller passed host memory
+template <class T>
+T *device_out(T *p, size_t bytes, tg::DBuf &stage, bool &staged) {
+    staged = false;
+    if (!p) return nullptr;
+    if (tg::is_device_pointer(p)) return p;
+    if (stage.bytes < bytes) stage.alloc(bytes);
+    staged = true;
+    return stage.as<T>();
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_layout(int32_t L, int32_t k, tg_layout_t *out) {
+    return guarded([&] {
+        check_types(L);
+        if ((k != 3 && k != 4) || !out) throw Error{TG_ERR_INVALID_ARG, "k"};
+        tg_layout_t r;
+        std::memset(&r, 0, sizeof(r));
+        r.L = L;
+        r.k = k;
+        r.pairs = tg::npairs(L);
+        r.per_edge_slots = tg::per_edge_slots(L, k);
+        r.global_slots = tg::global_slots(L, k);
+        r.orbit_offset[1] = 0;
+        r.orbit_offset[2] = L;
+        for (int o = 3; o <= 12; ++o) r.orbit_offset[o] = k == 4 ? 2 * L + (o - 3) * r.pairs : -1;
+        const int edges_of[9] = {1, 2, 3, 3, 3, 4, 4, 5, 6};
+        int64_t off = 0;
+        for (int b = 0; b < 9; ++b) {
+            int64_t sz = b == 0 ? tg::binom_small(L + 1, 2) : (b <= 2 ? tg::binom_small(L + 2, 3) : tg::binom_small(L + 3, 4));
+            if (k == 3 && b > 2) sz = 0;
+            r.global_block_offset[b] = off;
+            r.global_block_size[b] = sz;
+            r.graphlet_edges[b] = edges_of[b];
+            off += sz;
+        }
+        *out = r;
+    });
+}
+
+void tg_default_options(tg_options *opt) {
+    if (opt) tg::fill_defaults(opt);
+}
+
+tg_status tg_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, const uint8_t *node_types,
+                   int32_t L, const tg_options *opt, void *stream, tg_graph **out) {
+    const int64_t off[2] = {0, n};
+    return guarded([&] { build_common(1, off, n, nnz, row_ptr, col, node_types, L, opt, stream, out); });
+}
+
+tg_status tg_build_batch(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col, const uint8_t *node_types, int32_t L, const tg_options *opt,
+                         void *stream, tg_graph **out) {
+    return guarded([&] { build_common(ngraphs, node_off, n, nnz, row_ptr, col, node_types, L, opt, stream, out); });
+}
+
+void tg_free(tg_graph *g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->g.stream);
+    delete g;
+}
+
+int64_t tg_num_nodes(const tg_graph *g) { return g ? g->g.n : -1; }
+int64_t tg_num_edges(const tg_graph *g) { return g ? g->g.m : -1; }
+int32_t tg_num_graphs(const tg_graph *g) { return g ? g->g.ngraphs : -1; }
+int32_t tg_num_types(const tg_graph *g) { return g ? g->g.L : -1; }
+int64_t tg_device_bytes(const tg_graph *g) { return g ? g->g.device_bytes() : -1; }
+int64_t tg_last_launch_count(const tg_graph *g) { return g ? g->g.last_launches : -1; }
+int32_t tg_abi_version(void) { return TG_ABI_VERSION; }
+
+tg_status tg_edge_endpoints(const tg_graph *gh, int32_t *src, int32_t *dst) {
+    return guarded([&] {
+        if (!gh || !src || !dst) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        const Graph &G = gh->g;
+        cudaStream_t s = G.stream;
+        const size_t bytes = sizeof(int32_t) * (size_t)std::max<int64_t>(G.m, 1);
+        bool dev_s = tg::is_device_pointer(src), dev_d = tg::is_device_pointer(dst);
+        tg::TBuf ts(dev_s ? 0 : bytes, s), td(dev_d ? 0 : bytes, s);
+        int32_t *ps = dev_s ? src : ts.as<int32_t>(), *pd = dev_d ? dst : td.as<int32_t>();
+        if (G.m > 0) {
+            k_endpoints<<<(unsigned)((G.m + 255) / 256), 256, 0, s>>>(G.m, G.e_lo.as<int32_t>(), G.e_hi.as<int32_t>(),
+                                                                  G.old_of.as<int32_t>(), ps, pd);
+            TG_CK(cudaGetLastError());
+            if (!dev_s) TG_CK(cudaMemcpyAsync(src, ps, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
+            if (!dev_d) TG_CK(cudaMemcpyAsync(dst, pd, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
+        }
+        TG_CK(cudaStreamSynchronize(s));
+    });
+}
+
+tg_status tg_edge_offsets(const tg_graph *gh, int64_t *out) {
+    return guarded([&] {
+        if (!gh || !out) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        std::copy(gh->g.h_edge_off.begin(), gh->g.h_edge_off.end(), out);
+    });
+}
+
+tg_status tg_count(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_t *global_out, void *stream) {
+    return guarded([&] {
+        if (!gh || (k != 3 && k != 4)) throw Error{TG_ERR_INVALID_ARG, "k"};
+        Graph &G = gh->g;
+        cudaStream_t s = (cudaStream_t)stream;
+        G.stream = s;
+        tg::prepare_counting(G, k, s);
+        tg::prepare_edges(G, k, s);
+        const size_t pe_bytes = (size_t)G.m * tg::per_edge_slots(G.L, k) * sizeof(uint32_t);
+        const size_t gl_bytes = (size_t)G.ngraphs * tg::global_slots(G.L, k) * sizeof(int64_t);
+        bool pe_staged = false, gl_staged = false;
+        uint32_t *pe = device_out(per_edge_out, pe_bytes, G.stage_pe, pe_staged);
+        int64_t *gl = device_out(global_out, gl_bytes, G.stage_gl, gl_staged);
+        TG_CK(cudaMemsetAsync(G.gacc.p, 0, (size_t)G.ngraphs * tg::global_slots(G.L, 4) * sizeof(unsigned long long), s));
+        int64_t launches = tg::launch_prepare(G, k, s);
+        launches += tg::launch_edges(G, k, 0, G.m, pe, G.gacc.as<unsigned long long>(), s);
+        if (gl) launches += tg::launch_finalize(G, k, gl, s);
+        if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
+        if (gl_staged) TG_CK(cudaMemcpyAsync(global_out, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
+        if (pe_staged || gl_staged) TG_CK(cudaStreamSynchronize(s));
+        G.last_launches = launches;
+    });
+}
+
+tg_status tg_count_range(tg_graph *gh, int32_t k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out,
+                         int64_t *global_accum, void *stream) {
+    return guarded([&] {
+        if (!gh || (k != 3 && k != 4)) throw Error{TG_ERR_INVALID_ARG, "k"};
+        Graph &G = gh->g;
+        if (e_begin < 0 || e_end < e_begin || e_end > G.m) throw Error{TG_ERR_INVALID_ARG, "range"};
+        cudaStream_t s = (cudaStream_t)stream;
+        G.stream = s;
+        tg::prepare_counting(G, k, s);
+        tg::prepare_edges(G, k, s);
+        int64_t launches = 0;
+        if (!(G.prepared_k == k || (G.prepared_k == 4 && k == 3))) launches += tg::launch_prepare(G, k, s);
+        const size_t pe_bytes = (size_t)(e_end - e_begin) * tg::per_edge_slots(G.L, k) * sizeof(uint32_t);
+        const size_t gl_bytes = (size_t)G.ngraphs * tg::global_slots(G.L, k) * sizeof(int64_t);
+        bool pe_staged = false, gl_staged = false;
+        uint32_t *pe = device_out(per_edge_out, pe_bytes, G.stage_pe, pe_staged);
+        int64_t *gl = device_out(global_accum, gl_bytes, G.stage_gl, gl_staged);
+        if (gl_staged) TG_CK(cudaMemcpyAsync(gl, global_accum, gl_bytes, cudaMemcpyHostToDevice, s));
+        unsigned long long *acc = gl ? reinterpret_cast<unsigned long long *>(gl) : nullptr;
+        tg::DBuf scratch;
+        if (!acc) {
+            scratch.alloc(gl_bytes);
+            TG_CK(cudaMemsetAsync(scratch.p, 0, gl_bytes, s));
+            acc = scratch.as<unsigned long long>();
+        }
+        launches += tg::launch_edges(G, k, e_begin, e_end, pe, acc, s);
+        if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
+        if (gl_staged) TG_CK(cudaMemcpyAsync(global_accum, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
+        if (pe_staged || gl_staged || scratch.p) TG_CK(cudaStreamSynchronize(s));
+        G.last_launches = launches;
+    });
+}
+
+tg_status tg_finalize_global(int32_t L, int32_t k, int32_t ngraphs, const int64_t *raw, int64_t *out) {
+    return guarded([&] {
+        check_types(L);
+        if ((k != 3 && k != 4) || ngraphs < 0 || !raw || !out) throw Error{TG_ERR_INVALID_ARG, "args"};
+        tg_layout_t lay;
+        if (tg_layout(L, k, &lay) != TG_OK) throw Error{TG_ERR_INVALID_ARG, "layout"};
+        bool bad = false;
+        for (int32_t g = 0; g < ngraphs; ++g)
+            for (int b = 0; b < 9; ++b)
+                for (int64_t x = 0; x < lay.global_block_size[b]; ++x) {
+                    const int64_t idx = g * lay.global_slots + lay.global_block_offset[b] + x;
+                    if (raw[idx] % lay.graphlet_edges[b]) bad = true;
+                    out[idx] = raw[idx] / lay.graphlet_edges[b];
+                }
+        if (bad) throw Error{TG_ERR_INTERNAL, "remainder"};
+    });
+}
+
+tg_status tg_count_batch(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_t *global_out, void *stream) {
+    return guarded([&] {
+        if (!gh || (k != 3 && k != 4) || !stream) throw Error{TG_ERR_INVALID_ARG, "k or stream"};
+        if ((per_edge_out && !tg::is_device_pointer(per_edge_out)) || (global_out && !tg::is_device_pointer(global_out)))
+            throw Error{TG_ERR_INVALID_ARG, "batched outputs must be device memory"};
+        Graph &G = gh->g;
+        cudaStream_t s = (cudaStream_t)stream;
+        G.stream = s;
+        const bool same = G.batch_exec && G.batch_k == k && G.batch_pe == per_edge_out && G.batch_gl == global_out &&
+                          G.batch_stream == s;
+        if (!same) {
+            if (G.batch_exec) {
+                cudaGraphExecDestroy(G.batch_exec);
+                G.batch_exec = nullptr;
+            }
+            tg::prepare_counting(G, k, s);
+            tg::prepare_edges(G, k, s);
+            TG_CK(cudaStreamSynchronize(s));
+            cudaGraph_t graph = nullptr;
+            TG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            int64_t launches = 0;
+            try {
+                TG_CK(cudaMemsetAsync(G.gacc.p, 0, (size_t)G.ngraphs * tg::global_slots(G.L, 4) * sizeof(unsigned long long), s));
+                launches += tg::launch_prepare(G, k, s);
+                launches += tg::launch_edges(G, k, 0, G.m, per_edge_out, G.gacc.as<unsigned long long>(), s);
+                if (global_out) launches += tg::launch_finalize(G, k, global_out, s);
+            } catch (...) {
+                cudaStreamEndCapture(s, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            TG_CK(cudaStreamEndCapture(s, &graph));
+            cudaError_t ie = cudaGraphInstantiate(&G.batch_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            TG_CK(ie);
+            G.batch_k = k;
+            G.batch_pe = per_edge_out;
+            G.batch_gl = global_out;
+            G.batch_stream = s;
+            G.last_launches = launches;
+        }
+        TG_CK(cudaGraphLaunch(G.batch_exec, s));
+    });
+}
+
+tg_status tg_query_status(tg_graph *gh) {
+    if (!gh) return TG_ERR_INVALID_ARG;
+    uint32_t v = 0;
+    tg_status st = guarded([&] {
+        Graph &G = gh->g;
+        TG_CK(cudaStreamSynchronize(G.stream));
+        TG_CK(cudaMemcpy(&v, G.status.p, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        TG_CK(cudaMemset(G.status.p, 0, sizeof(uint32_t)));
+    });
+    if (st != TG_OK) return st;
+    if (v & tg::ST_INVALID_GRAPH) return TG_ERR_INVALID_GRAPH;
+    if (v & tg::ST_TOO_LARGE) return TG_ERR_TOO_LARGE;
+    if (v & tg::ST_TIMEOUT) return TG_ERR_TIMEOUT;
+    if (v & tg::ST_INTERNAL) return TG_ERR_INTERNAL;
+    if (v & tg::ST_OVERFLOW) return TG_ERR_OVERFLOW;
+    return TG_OK;
+}
+
+const char *tg_status_string(tg_status s) {
+    switch (s) {
+        case TG_OK: return "ok";
+        case TG_ERR_INVALID_ARG: return "invalid argument";
+        case TG_ERR_INVALID_GRAPH: return "invalid graph (not a simple symmetric CSR, or a type >= L)";
+        case TG_ERR_TOO_MANY_TYPES: return "number of types outside [1, TG_MAX_TYPES]";
+        case TG_ERR_OOM: return "device memory exhausted";
+        case TG_ERR_OVERFLOW: return "a per-edge count exceeded 2^32-1 and was saturated";
+        case TG_ERR_TIMEOUT: return "a bounded device wait ran out";
+        case TG_ERR_CUDA: return "CUDA runtime error";
+        case TG_ERR_INTERNAL: return "internal consistency check failed";
+        case TG_ERR_TOO_LARGE: return "graph exceeds an index-width limit";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

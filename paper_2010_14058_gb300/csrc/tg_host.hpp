@@ -1,0 +1,171 @@
+// tg_host.hpp -- host-side handle and helpers of libtg (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "tg.h"
+#include "tg_internal.cuh"
+
+namespace tg {
+
+// Internal error carrying a tg_status; caught at every extern "C" entry.
+struct Error {
+    tg_status status;
+    const char *what;
+};
+
+inline void throw_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    (void)cudaGetLastError();   // clear the sticky-free error state
+    throw Error{e == cudaErrorMemoryAllocation ? TG_ERR_OOM : TG_ERR_CUDA, what};
+}
+
+#define TG_CK(call) ::tg::throw_cuda((call), #call)
+
+// Device buffer owned by a handle; freed by release() or the destructor.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void alloc(size_t b) {
+        release();
+        if (b == 0) b = 16;
+        TG_CK(cudaMalloc(&p, b));
+        bytes = b;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync).
+struct TBuf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    TBuf(size_t b, cudaStream_t st) : s(st) {
+        if (b == 0) b = 16;
+        TG_CK(cudaMallocAsync(&p, b, s));
+    }
+    TBuf(const TBuf &) = delete;
+    TBuf &operator=(const TBuf &) = delete;
+    ~TBuf() { if (p) cudaFreeAsync(p, s); }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+inline bool is_device_pointer(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;      // stream of the last call
+    int32_t ngraphs = 1, L = 1;
+    int64_t n = 0, nnz = 0, m = 0;
+    int64_t max_graph_nodes = 0;
+    int64_t max_degree = 0;
+    std::vector<int64_t> h_node_off, h_edge_off;
+    tg_options opt;
+
+    // graph (built once)
+    DBuf node_off, edge_off, rp, adj, toff, ty, old_of, slot_eid, e_lo, e_hi, e_slot_lo, e_slot_hi, delta;
+    // work lists
+    DBuf anchors_light, anchors_heavy, edges_light, edges_heavy;
+    int64_t n_anchors_light = 0, n_anchors_heavy = 0, n_edges_light = 0, n_edges_heavy = 0;
+    // counting state
+    DBuf C, tau, A, tables, gacc, status, tiles_full, tscratch, stage_pe, stage_gl;
+    int64_t n_tiles_full = 0, tscratch_stride = 0;
+    int32_t tscratch_blocks = 0;
+    int64_t table_stride = 0;
+    int32_t n_tables = 0;
+    int32_t prepared_k = 0;             // 0: nothing, 3: C and tau, 4: C, tau and A
+    int64_t last_launches = 0;
+    // CUDA graph of the last batched count
+    cudaGraphExec_t batch_exec = nullptr;
+    int32_t batch_k = 0;
+    const void *batch_pe = nullptr, *batch_gl = nullptr;
+    cudaStream_t batch_stream = nullptr;
+
+    GraphView view() const {
+        GraphView v;
+        v.ngraphs = ngraphs; v.L = L; v.n = n; v.nnz = nnz; v.m = m;
+        v.node_off = node_off.as<int64_t>();
+        v.edge_off = edge_off.as<int64_t>();
+        v.rp = rp.as<int64_t>();
+        v.adj = adj.as<int32_t>();
+        v.toff = toff.as<int32_t>();
+        v.ty = ty.as<uint8_t>();
+        v.slot_eid = slot_eid.as<int32_t>();
+        v.e_lo = e_lo.as<int32_t>();
+        v.e_hi = e_hi.as<int32_t>();
+        v.e_slot_lo = e_slot_lo.as<int64_t>();
+        v.e_slot_hi = e_slot_hi.as<int64_t>();
+        v.delta = delta.as<int64_t>();
+        return v;
+    }
+    CountView cview() const {
+        CountView c;
+        c.C = C.as<uint32_t>();
+        c.tau = tau.as<int64_t>();
+        c.A = A.as<uint32_t>();
+        c.tables = tables.as<uint32_t>();
+        c.table_stride = table_stride;
+        c.gacc = gacc.as<unsigned long long>();
+        c.status = status.as<uint32_t>();
+        return c;
+    }
+    int64_t device_bytes() const {
+        const DBuf *all[] = {&node_off, &edge_off, &rp, &adj, &toff, &ty, &old_of, &slot_eid, &e_lo, &e_hi,
+                             &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
+                             &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &tscratch,
+                             &stage_pe, &stage_gl};
+        int64_t s = 0;
+        for (const DBuf *b : all) s += (int64_t)b->bytes;
+        return s;
+    }
+    ~Graph() {
+        if (batch_exec) cudaGraphExecDestroy(batch_exec);
+    }
+};
+
+inline void fill_defaults(tg_options *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->light_edge_max_degree = 256;
+    o->light_anchor_max_wedges = 256;
+    o->anchor_table_budget_mb = 4096;
+    o->ctas_per_sm = 4;
+}
+
+// number of SMs of the current device
+int sm_count();
+
+// build entry (tg_build.cu)
+void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_t n, int64_t nnz,
+                 const int64_t *row_ptr, const int32_t *col, const uint8_t *types, int32_t L,
+                 const tg_options &opt, cudaStream_t s);
+
+// count entries (tg_count.cu)
+void prepare_counting(Graph &G, int k, cudaStream_t s);
+void prepare_edges(Graph &G, int k, cudaStream_t s);
+int64_t launch_prepare(Graph &G, int k, cudaStream_t s);
+int64_t launch_edges(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out,
+                     unsigned long long *gacc, cudaStream_t s);
+int64_t launch_finalize(Graph &G, int k, int64_t *global_out, cudaStream_t s);
+
+}  // namespace tg
+
+struct tg_graph {
+    tg::Graph g;
+};

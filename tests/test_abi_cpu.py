@@ -1,0 +1,94 @@
+"""The C-ABI library loads and exports every symbol include/tg.h declares;
+its pure host functions agree with the oracle's layout (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tg_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2010_14058_gb300 import build, tg
+    build.build()
+    return tg.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2010_14058_gb300 import tg
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in tg.SIGNATURES, name
+    assert set(tg.SIGNATURES) == set(names)
+
+
+def test_abi_version(lib):
+    from paper_2010_14058_gb300 import tg
+    assert tg.tg_abi_version() == 1
+
+
+@pytest.mark.parametrize("L", range(1, 9))
+@pytest.mark.parametrize("k", [3, 4])
+def test_layout_matches_oracle(L, k, lib):
+    from paper_2010_14058_gb300 import tg
+    lay = tg.tg_layout(L, k)
+    assert lay["per_edge_slots"] == oracle.per_edge_slots(L, k)
+    assert lay["global_slots"] == oracle.global_slots(L, k)
+    assert lay["pairs"] == L * (L + 1) // 2
+    assert lay["orbit_offset"][2] == L
+    assert sum(lay["global_block_size"]) == lay["global_slots"]
+    assert lay["graphlet_edges"] == [1, 2, 3, 3, 3, 4, 4, 5, 6]
+
+
+def test_layout_rejects_bad_arguments(lib):
+    from paper_2010_14058_gb300 import tg
+    with pytest.raises(tg.TGError) as e:
+        tg.tg_layout(9, 4)
+    assert e.value.name == "TG_ERR_TOO_MANY_TYPES"
+    with pytest.raises(tg.TGError) as e:
+        tg.tg_layout(3, 5)
+    assert e.value.name == "TG_ERR_INVALID_ARG"
+
+
+def test_finalize_global_divides_and_checks(lib):
+    from paper_2010_14058_gb300 import tg
+    L, k = 2, 4
+    lay = tg.tg_layout(L, k)
+    raw = np.zeros(lay["global_slots"], dtype=np.int64)
+    for b in range(9):
+        off, sz = lay["global_block_offset"][b], lay["global_block_size"][b]
+        raw[off:off + sz] = lay["graphlet_edges"][b] * np.arange(1, sz + 1)
+    out = tg.tg_finalize_global(L, k, 1, raw)
+    for b in range(9):
+        off, sz = lay["global_block_offset"][b], lay["global_block_size"][b]
+        np.testing.assert_array_equal(out[off:off + sz], np.arange(1, sz + 1))
+    raw[lay["global_block_offset"][8]] += 1
+    with pytest.raises(tg.TGError) as e:
+        tg.tg_finalize_global(L, k, 1, raw)
+    assert e.value.name == "TG_ERR_INTERNAL"
+
+
+def test_status_strings(lib):
+    from paper_2010_14058_gb300 import tg
+    for code in tg.STATUS:
+        assert tg.tg_status_string(code) not in ("", "unknown status")
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2010_14058_gb300 import tg
+    with pytest.raises(tg.LibraryMissing):
+        tg.load(str(tmp_path / "libtg.so"))

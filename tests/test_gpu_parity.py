@@ -1,0 +1,213 @@
+"""GPU path (through the C ABI) vs the CPU oracle: bit-exact counts.
+
+Per-edge rows (uint32) and global totals (int64) must equal the oracle's
+exactly on every graph: tiny graphs against brute force, seeded ER /
+Chung-Lu / SBM graphs that span many tiles and a ragged last tile, graphs
+that force every kernel variant (warp and CTA per edge, shared-memory and
+global T lists, warp and CTA wedge anchors), the 3-node mode, edge ranges,
+batches, host buffers, and the error paths.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from gpu_helpers import concat_graphs, gpu_count
+from oracle_pins import graph_from_edges, random_graph
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2010_14058_gb300 as tg  # noqa: E402
+
+# options that route every edge and every anchor through the CTA variants
+ALL_HEAVY = {"light_edge_max_degree": 1, "light_anchor_max_wedges": 1}
+
+
+def assert_parity(g, k=4, options=None, reference="paper"):
+    pe, gl, st = gpu_count(g, k=k, options=options)
+    assert st == 0, tg.STATUS[st]
+    if reference == "brute":
+        pe_o, gl_o = oracle.brute(g)
+        if k == 3:
+            L = g["L"]
+            pe_o = pe_o[:, :2 * L]
+            gl_o = gl_o[:oracle.global_slots(L, 3)]
+    else:
+        pe_o, gl_o = oracle.paper(g, k=k)
+    np.testing.assert_array_equal(pe, pe_o)
+    np.testing.assert_array_equal(gl, gl_o)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_tiny_graphs_vs_brute_force(seed):
+    n = 5 + seed % 11
+    p = [0.3, 0.5, 0.7, 0.95][seed % 4]
+    L = [1, 2, 3, 4, 5, 8][seed % 6]
+    assert_parity(random_graph(n, p, L, 9000 + seed), reference="brute")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_graphs_all_cta_variants(seed):
+    g = random_graph(9 + seed, 0.6, [2, 3, 8][seed % 3], 9100 + seed)
+    assert_parity(g, options=ALL_HEAVY, reference="brute")
+
+
+def test_degenerate_graphs():
+    # no edges, isolated nodes, one edge, a path, a star, a clique, K_{3,4}
+    assert_parity(graph_from_edges(4, [], [0, 1, 2, 0], 3))
+    assert_parity(graph_from_edges(1, [], [0], 1))
+    assert_parity(graph_from_edges(6, [(2, 5)], [0, 1, 2, 0, 1, 2], 3))
+    assert_parity(graph_from_edges(5, [(0, 1), (1, 2), (2, 3), (3, 4)], [0, 1, 0, 1, 0], 2))
+    assert_parity(graph_from_edges(7, [(0, x) for x in range(1, 7)], [1, 0, 1, 2, 0, 2, 2], 3))
+    assert_parity(graph_from_edges(8, [(a, b) for a in range(8) for b in range(a + 1, 8)], [0, 1, 2, 3, 0, 1, 2, 3], 4))
+    assert_parity(graph_from_edges(7, [(a, b) for a in range(3) for b in range(3, 7)], [0, 0, 0, 1, 1, 1, 1], 2))
+
+
+@pytest.mark.parametrize("L", [1, 2, 5, 8])
+def test_er_several_tiles_and_ragged_tail(L):
+    # 9,123 edges: 4 full tiles of 2,048 edges plus a ragged one
+    g = graphgen.erdos_renyi(1500, 9123, L, 31 + L)
+    assert_parity(g)
+
+
+def test_er_small_workload():
+    assert_parity(graphgen.workload("er_small"))
+
+
+def test_er_small_workload_k3():
+    assert_parity(graphgen.workload("er_small"), k=3)
+
+
+@pytest.mark.parametrize("options", [None, ALL_HEAVY, {"light_edge_max_degree": 16, "light_anchor_max_wedges": 8}])
+def test_chung_lu_with_hubs(options):
+    # hubs route edges and anchors through both variants
+    g = graphgen.chung_lu(4000, 30000, 2.1, 1200.0, 5, 77, type_zipf=1.2)
+    assert_parity(g, options=options)
+
+
+def test_global_t_list_path():
+    # edge (0,1) has |T| = 9000 > the shared-memory T list of a CTA
+    a = 9000
+    edges = [(0, 1)] + [(0, 2 + x) for x in range(a)] + [(1, 2 + x) for x in range(a)]
+    edges += [(2 + x, 2 + x + 1) for x in range(0, 200, 2)]
+    rng = np.random.default_rng(5)
+    types = rng.integers(0, 3, a + 2)
+    assert_parity(graph_from_edges(a + 2, edges, types, 3))
+
+
+def test_sbm_small():
+    aff = np.full((4, 4), 1.0)
+    np.fill_diagonal(aff, 0.05)
+    g = graphgen.sbm([500, 300, 150, 50], aff, 20000, 12)
+    assert_parity(g)
+
+
+def test_host_buffers_match_device_buffers():
+    g = graphgen.erdos_renyi(800, 5000, 4, 3)
+    pe_d, gl_d, st_d = gpu_count(g)
+    pe_h, gl_h, st_h = gpu_count(g, host_buffers=True)
+    assert st_d == 0 and st_h == 0
+    np.testing.assert_array_equal(pe_d, pe_h)
+    np.testing.assert_array_equal(gl_d, gl_h)
+
+
+def test_edge_endpoints_and_ranges():
+    g = graphgen.chung_lu(3000, 20000, 2.2, 800.0, 3, 8)
+    src, dst = oracle.edges(g)
+    h = tg.tg_build(*tg.to_device(g), g["L"])
+    s = torch.zeros(h.m, dtype=torch.int32, device="cuda")
+    d = torch.zeros(h.m, dtype=torch.int32, device="cuda")
+    tg.tg_edge_endpoints(h, s, d)
+    np.testing.assert_array_equal(s.cpu().numpy(), src)
+    np.testing.assert_array_equal(d.cpu().numpy(), dst)
+    lay = tg.tg_layout(g["L"], 4)
+    full = torch.zeros((h.m, lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
+    glob = torch.zeros(lay["global_slots"], dtype=torch.int64, device="cuda")
+    tg.tg_count(h, 4, full, glob)
+    raw = torch.zeros(lay["global_slots"], dtype=torch.int64, device="cuda")
+    cuts = [0, 1, 777, 5000, 5001, 19999, h.m]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        part = torch.zeros((b - a, lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
+        tg.tg_count_range(h, 4, a, b, part, raw)
+        assert torch.equal(part, full[a:b])
+    assert tg.tg_query_status(h) == 0
+    np.testing.assert_array_equal(tg.tg_finalize_global(g["L"], 4, 1, raw.cpu().numpy()), glob.cpu().numpy())
+    h.free()
+
+
+def test_batch_equals_separate_graphs():
+    graphs = [graphgen.erdos_renyi(50 + 30 * x, 200 + 150 * x, 3, 400 + x) for x in range(7)]
+    graphs.append(graphgen.chung_lu(2000, 9000, 2.1, 500.0, 3, 9))
+    graphs.insert(3, graph_from_edges(5, [], [0, 1, 2, 0, 1], 3))      # an empty graph inside the batch
+    node_off, rp, col, ty = concat_graphs(graphs)
+    L = 3
+    lay = tg.tg_layout(L, 4)
+    h = tg.tg_build_batch(node_off, torch.as_tensor(rp, device="cuda"), torch.as_tensor(col, device="cuda"),
+                          torch.as_tensor(ty, device="cuda"), L)
+    assert h.ngraphs == len(graphs)
+    eoff = tg.tg_edge_offsets(h)
+    pe = torch.zeros((h.m, lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
+    gl = torch.zeros((len(graphs), lay["global_slots"]), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        tg.tg_count_batch(h, 4, pe, gl, stream=stream)
+        first = gl.clone()
+        pe.zero_()
+        gl.zero_()
+        tg.tg_count_batch(h, 4, pe, gl, stream=stream)        # CUDA-graph replay
+    stream.synchronize()
+    assert tg.tg_query_status(h) == 0
+    assert torch.equal(first, gl)
+    pe_np = pe.cpu().numpy().view(np.uint32).astype(np.int64)
+    for x, g in enumerate(graphs):
+        pe_o, gl_o = oracle.paper(g)
+        np.testing.assert_array_equal(gl.cpu().numpy()[x], gl_o)
+        np.testing.assert_array_equal(pe_np[eoff[x]:eoff[x + 1]], pe_o)
+    # plain count of the same batch handle gives the same numbers
+    gl2 = torch.zeros_like(gl)
+    tg.tg_count(h, 4, None, gl2)
+    assert torch.equal(gl2, gl)
+    h.free()
+
+
+def test_invalid_graphs_are_rejected():
+    ok = graph_from_edges(3, [(0, 1), (1, 2)], [0, 1, 0], 2)
+    cases = [
+        dict(ok, types=np.array([0, 2, 0], dtype=np.uint8)),                                     # type >= L
+        dict(ok, row_ptr=np.array([0, 2, 3, 4]), col=np.array([0, 1, 0, 1], dtype=np.int32)),    # self-loop
+        dict(ok, row_ptr=np.array([0, 1, 2, 2]), col=np.array([1, 2], dtype=np.int32)),          # one-sided
+        dict(ok, row_ptr=np.array([0, 2, 4, 4]), col=np.array([1, 1, 0, 0], dtype=np.int32)),    # repeated
+        dict(ok, col=np.array([1, 0, 5, 1], dtype=np.int32)),                                    # id out of range
+    ]
+    for bad in cases:
+        with pytest.raises(tg.TGError) as e:
+            tg.tg_build(*tg.to_device(bad), bad["L"])
+        assert e.value.name == "TG_ERR_INVALID_GRAPH"
+    with pytest.raises(tg.TGError) as e:
+        tg.tg_build(*tg.to_device(ok), 9)
+    assert e.value.name == "TG_ERR_TOO_MANY_TYPES"
+    # a cross-graph edge in a batch
+    g2 = graph_from_edges(4, [(0, 1), (1, 3), (2, 3)], [0, 1, 0, 1], 2)
+    with pytest.raises(tg.TGError) as e:
+        tg.tg_build_batch(np.array([0, 2, 4]), *tg.to_device(g2), 2)
+    assert e.value.name == "TG_ERR_INVALID_GRAPH"
+
+
+def test_repeated_counts_are_identical():
+    g = graphgen.chung_lu(3000, 15000, 2.1, 600.0, 4, 21)
+    h = tg.tg_build(*tg.to_device(g), g["L"])
+    lay = tg.tg_layout(g["L"], 4)
+    outs = []
+    for _ in range(3):
+        pe = torch.zeros((h.m, lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
+        gl = torch.zeros(lay["global_slots"], dtype=torch.int64, device="cuda")
+        tg.tg_count(h, 4, pe, gl)
+        outs.append((pe, gl))
+    assert tg.tg_query_status(h) == 0
+    for pe, gl in outs[1:]:
+        assert torch.equal(pe, outs[0][0]) and torch.equal(gl, outs[0][1])
+    h.free()
