@@ -131,8 +131,10 @@ __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const u
         if ((int64_t)(k >> 32) != x || y == x) set_status(status, ST_INVALID_GRAPH);
         if (s > b && keys[s - 1] == k) set_status(status, ST_INVALID_GRAPH);
     }
-    // type t starts at the first slot whose packed type is >= t
-    if (lane <= L) {
+    // type t < L starts at the first slot whose packed type is >= t; the
+    // end sentinel (t = L) is the row length (L << 29 would not fit 32 bits
+    // for L = 8)
+    if (lane < L) {
         uint32_t key = (uint32_t)lane << kTypeShift;
         int64_t lo = b, hi = e;
         while (lo < hi) {
@@ -140,6 +142,8 @@ __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const u
             if ((uint32_t)keys[mid] < key) lo = mid + 1; else hi = mid;
         }
         toff[x * (L + 1) + lane] = (int32_t)(lo - b);
+    } else if (lane == L) {
+        toff[x * (L + 1) + L] = (int32_t)(e - b);
     }
 }
 
