@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark: exact typed 3+4-node graphlet counting, edges per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload cl_large|sbm_typed|er_small]
+
+One step = the whole counting path on one graph resident in HBM: tg_build
+(device preprocessing) + tg_count(k=4) (per-edge uint32 rows and global
+int64 totals, both written to HBM) + tg_free.  value = edges of all ranks /
+max-over-ranks time of K steps (CUDA events on the launching stream, barrier
+and synchronize on both sides).  The inputs and outputs (CSR 176 MB, per-edge
+rows 12.8 GB for the Chung-Lu workload) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+e2e: the same metric through the public API with host buffers (pinned CSR
+in, per-edge rows and totals out), copies inside the timed region.
+cpu_baseline: the CPU oracle (Alg. 1-3 + Lemmas) on a seeded uniform edge
+sample, on the host cores.  --impl reference times that oracle as the
+reference arm.
+
+Multi-GPU (torchrun): every rank counts its own copy of the workload (edges
+are independent problems; weak scaling), no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "typed-graphlet edges/sec (3+4-node, exact)"
+UNIT = "edges/s"
+WORKLOADS = {
+    "cl_large": "Chung-Lu n=2,000,000 m=20,000,000 gamma=2.1 max weight 5e4, L=5 Zipf(1.2) types",
+    "sbm_typed": "SBM 500k/300k/150k/50k nodes, L=4 types, m=30,000,000, affinity 1 between / 0.05 within",
+    "er_small": "Erdos-Renyi n=2,000 m=10,000, L=3 uniform types",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cl_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+        self._thread = None
+
+    def start(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self._proc = None
+            return
+        self._thread = threading.Thread(target=self._read, daemon=True)
+        self._thread.start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+            if self._stop.is_set():
+                break
+
+    def stop(self) -> dict:
+        self._stop.set()
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "", 1).isdigit()]
+        smax = [float(s[2]) for s in self.samples if s[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if len(s) > 5 + k and s[5 + k] == "Active"})
+        power = [float(s[3]) for s in self.samples if s[3].replace(".", "", 1).isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(power) if power else None}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def edge_bytes_per_kernel(g: dict, L: int, light_max: int = 256) -> dict:
+    """Algorithmic bytes of the per-edge kernels (what each edge must touch
+    in this formulation): its output row, its own triangle counts, the
+    typed-triangle and typed-degree sums of both endpoints, its two 4-cycle
+    slots, its edge record and the shorter side of each typed intersection."""
+    rp = g["row_ptr"]
+    deg = np.diff(rp)
+    n = g["n"]
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    col = g["col"]
+    up = col > rows
+    mn = np.minimum(deg[rows[up]], deg[col[up]]).astype(np.int64)
+    S = 2 * L + 10 * L * (L + 1) // 2
+    per_edge = 4 * S + 4 * L + 2 * 8 * L * L + 2 * 8 * L * L + 2 * 4 * L * L + 24
+    light = mn <= light_max
+    return {"k_edge4_light": float(per_edge * light.sum() + 4 * mn[light].sum()),
+            "k_edge4_heavy": float(per_edge * (~light).sum() + 4 * mn[~light].sum()),
+            "k_tri": float((4 * L + 24) * len(mn) + 4 * mn.sum())}
+
+
+# ------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+
+    import graphgen
+    import paper_2010_14058_gb300 as tg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2010_14058_gb300 import build as tgbuild
+    tgbuild.build()
+    g = graphgen.workload(args.workload)
+    L, m = g["L"], g["m"]
+    lay = tg.tg_layout(L, 4)
+    S, G = lay["per_edge_slots"], lay["global_slots"]
+    rp, col, ty = tg.to_device(g, dev)
+    pe = torch.empty((m, S), dtype=torch.int32, device=dev)
+    gl = torch.empty(G, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    kernel_ms = {}
+    launches = [0]
+
+    def step(timing: bool):
+        h = tg.tg_build(rp, col, ty, L, stream=stream)
+        launches[0] += h.last_launch_count
+        if timing:
+            tg.tg_set_timing(h, True)
+        tg.tg_count(h, 4, pe, gl, stream=stream)
+        launches[0] += h.last_launch_count
+        if timing:
+            for name, (ms, n) in tg.tg_get_timing(h).items():
+                a = kernel_ms.setdefault(name, [0.0, 0])
+                a[0] += ms
+                a[1] += n
+        st = tg.tg_query_status(h) if timing else 0
+        h.free()
+        return st
+
+    for _ in range(args.warmup):
+        step(False)
+    status = 0
+    # timed region
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    launches[0] = 0
+    t0.record(stream)
+    for _ in range(args.steps):
+        st = step(True)
+        status = status or st
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * m * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (largest share of the timed device time)
+    peak, peak_kind = load_peaks()
+    top = max(kernel_ms.items(), key=lambda kv: kv[1][0])
+    algo = edge_bytes_per_kernel(g, L)
+    per_launch_ms = top[1][0] / max(top[1][1], 1)
+    abytes = algo.get(top[0])
+    roofline = None
+    if abytes is not None:
+        achieved = abytes / (per_launch_ms / 1e3) / 1e9
+        roofline = {"kernel": top[0], "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
+                    "algorithmic_bytes": abytes, "ms_per_launch": round(per_launch_ms, 3), "traffic": None}
+    kernel_share = {k: round(v[0] / sum(x[0] for x in kernel_ms.values()), 4) for k, v in kernel_ms.items()}
+
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        h_rp = torch.from_numpy(np.ascontiguousarray(g["row_ptr"])).pin_memory()
+        h_col = torch.from_numpy(np.ascontiguousarray(g["col"])).pin_memory()
+        h_ty = torch.from_numpy(np.ascontiguousarray(g["types"])).pin_memory()
+        h_pe = torch.empty((m, S), dtype=torch.int32).pin_memory()
+        h_gl = torch.empty(G, dtype=torch.int64).pin_memory()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
+            tg.tg_count(h, 4, h_pe, h_gl, stream=stream)
+            h.free()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        bi = h_rp.numel() * 8 + h_col.numel() * 4 + h_ty.numel()
+        bo = h_pe.numel() * 4 + h_gl.numel() * 8
+        e2e = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo)}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(g, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "nodes": g["n"],
+                       "edges": m, "types": L, "k": 4, "per_edge_slots": S, "global_slots": G,
+                       "l2": "inputs and outputs larger than L2 (no flush)",
+                       "step": "tg_build + tg_count(k=4) + tg_free, device-resident inputs and outputs"},
+            "status": tg.STATUS[status], "roofline": roofline, "kernel_share": kernel_share,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches[0]),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- CPU oracle arm
+
+def cpu_baseline(g: dict, seconds: float) -> dict:
+    """The CPU oracle (Alg. 1-3 + Lemmas, OpenMP over edges) on a seeded
+    uniform sample of edge ids, sized to take about `seconds`."""
+    import oracle
+    rng = np.random.default_rng(20201029)
+    m = g["m"]
+    n_try = min(m, 2000)
+    ids = np.sort(rng.choice(m, size=n_try, replace=False))
+    t = time.perf_counter()
+    oracle.paper_edges(g, ids)
+    el = time.perf_counter() - t
+    if el < seconds and n_try < m:
+        n2 = int(min(m, n_try * max(1.0, 0.9 * seconds / max(el, 1e-3))))
+        ids = np.sort(rng.choice(m, size=n2, replace=False))
+        t = time.perf_counter()
+        oracle.paper_edges(g, ids)
+        el = time.perf_counter() - t
+    return {"value": round(len(ids) / el, 1), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{len(ids)} edge ids drawn uniformly (seed 20201029) from the {m} edges; "
+                      f"all 3- and 4-node orbits of each; {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import graphgen
+    import oracle
+    g = graphgen.workload(args.workload)
+    m = g["m"]
+    rng = np.random.default_rng(7)
+    # size each step's sample so that warmup + steps end within a few minutes
+    ids = np.sort(rng.choice(m, size=min(m, 500), replace=False))
+    t = time.perf_counter()
+    oracle.paper_edges(g, ids)
+    el = time.perf_counter() - t
+    per_step = int(min(m, max(500, 500 * 8.0 / max(el, 1e-3))))
+    for _ in range(args.warmup):
+        oracle.paper_edges(g, np.sort(rng.choice(m, size=per_step, replace=False)))
+    total, el = 0, 0.0
+    for _ in range(args.steps):
+        ids = np.sort(rng.choice(m, size=per_step, replace=False))
+        t = time.perf_counter()
+        oracle.paper_edges(g, ids)
+        el += time.perf_counter() - t
+        total += len(ids)
+    value = total / el
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "edges": m,
+                       "types": g["L"], "k": 4},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} uniform edge ids per step from {m}; CPU oracle (Alg. 1-3 + "
+                                       f"Lemmas), OpenMP over edges"},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

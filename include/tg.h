@@ -216,10 +216,23 @@ tg_status tg_query_status(tg_graph *g);
 /* Static description of a status code. */
 const char *tg_status_string(tg_status s);
 
-/* Number of kernel launches issued by the last tg_count / tg_count_range /
- * tg_count_batch call on this handle (a CUDA-graph replay counts its
- * kernels). */
+/* Number of this library's own kernel launches (not counting the CUB
+ * primitives the build sorts with) issued by the last tg_build /
+ * tg_build_batch, tg_count, tg_count_range or tg_count_batch call on this
+ * handle (a CUDA-graph replay counts its kernels). */
 int64_t tg_last_launch_count(const tg_graph *g);
+
+/* Per-kernel timing.  While enabled, every kernel that tg_count or
+ * tg_count_range launches is bracketed by a CUDA event pair recorded on the
+ * launching stream, and the elapsed times are accumulated per kernel name.
+ * (Not recorded inside tg_count_batch's captured graph.) */
+tg_status tg_set_timing(tg_graph *g, int32_t on);
+
+/* Synchronises the handle's stream and reports the accumulated timing:
+ * up to `max` entries of kernel name (static string), total milliseconds and
+ * launch count; *n receives the number of entries.  Then clears it. */
+tg_status tg_get_timing(tg_graph *g, int32_t max, const char **names, double *ms, int64_t *launches,
+                        int32_t *n);
 
 /* Library ABI version (TG_ABI_VERSION). */
 int32_t tg_abi_version(void);

@@ -3,6 +3,7 @@
 // Every entry catches the library's internal errors and returns a tg_status;
 // nothing here traps, aborts or exits.
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -291,6 +292,43 @@ tg_status tg_count_batch(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_
             G.last_launches = launches;
         }
         TG_CK(cudaGraphLaunch(G.batch_exec, s));
+    });
+}
+
+tg_status tg_set_timing(tg_graph *gh, int32_t on) {
+    return guarded([&] {
+        if (!gh) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        gh->g.timing = on != 0;
+    });
+}
+
+tg_status tg_get_timing(tg_graph *gh, int32_t max, const char **names, double *ms, int64_t *launches, int32_t *n) {
+    return guarded([&] {
+        if (!gh || !n || max < 0) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        Graph &G = gh->g;
+        TG_CK(cudaStreamSynchronize(G.stream));
+        for (auto &r : G.timer_pending) {
+            float t = 0.f;
+            TG_CK(cudaEventElapsedTime(&t, r.a, r.b));
+            bool found = false;
+            for (auto &tot : G.timer_totals)
+                if (std::strcmp(tot.first, r.name) == 0) { tot.second.first += t; tot.second.second += 1; found = true; }
+            if (!found) G.timer_totals.push_back({r.name, {(double)t, 1}});
+            G.event_pool.push_back(r.a);
+            G.event_pool.push_back(r.b);
+        }
+        G.timer_pending.clear();
+        int32_t c = 0;
+        for (auto &tot : G.timer_totals) {
+            if (c < max) {
+                if (names) names[c] = tot.first;
+                if (ms) ms[c] = tot.second.first;
+                if (launches) launches[c] = tot.second.second;
+            }
+            ++c;
+        }
+        *n = c < max ? c : max;
+        G.timer_totals.clear();
     });
 }
 

@@ -117,7 +117,7 @@ __global__ void k_gather_types(int64_t n, const int32_t *__restrict__ old_of, co
 
 // warp per internal row x: adjacency ids, self-loop / repeat checks, type offsets
 __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const unsigned long long *__restrict__ keys,
-                       int32_t *adj, int32_t *toff, uint32_t *status) {
+                       int32_t *adj, int32_t *toff, int32_t *pivot, uint32_t *status) {
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
     int lane = threadIdx.x & (kWarp - 1);
     if (warp >= n) return;
@@ -144,6 +144,19 @@ __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const u
         toff[x * (L + 1) + lane] = (int32_t)(lo - b);
     } else if (lane == L) {
         toff[x * (L + 1) + L] = (int32_t)(e - b);
+    }
+    // pivot: first slot of each type segment whose id exceeds x (the
+    // neighbours of higher priority)
+    __syncwarp();
+    const int32_t sb = lane < L ? toff[x * (L + 1) + lane] : 0;
+    const int32_t se = lane < L ? toff[x * (L + 1) + lane + 1] : 0;
+    if (lane < L) {
+        int64_t lo = b + sb, hi = b + se;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (adj[mid] < (int32_t)x + 1) lo = mid + 1; else hi = mid;
+        }
+        pivot[x * L + lane] = (int32_t)(lo - b);
     }
 }
 
@@ -308,8 +321,9 @@ __global__ void k_gather_keys(int64_t c, const int32_t *__restrict__ ids, const 
     if (i < c) out[i] = key[ids[i]];
 }
 
-void sort_desc_by_key(DBuf &ids, int64_t c, const unsigned long long *key, cudaStream_t s) {
+void sort_desc_by_key(DBuf &ids, int64_t c, const unsigned long long *key, cudaStream_t s, int64_t &launches) {
     if (c <= 1) return;
+    ++launches;
     TBuf k_in(sizeof(unsigned long long) * c, s), k_out(sizeof(unsigned long long) * c, s);
     TBuf v_out(sizeof(int32_t) * c, s);
     k_gather_keys<<<blocks_for(c, kThreads), kThreads, 0, s>>>(c, ids.as<int32_t>(), key, k_in.as<unsigned long long>());
@@ -345,6 +359,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
                  const int64_t *row_ptr, const int32_t *col, const uint8_t *types, int32_t L,
                  const tg_options &opt, cudaStream_t s) {
     G.stream = s;
+    G.last_launches = 0;
     G.ngraphs = ngraphs;
     G.L = L;
     G.n = n;
@@ -380,7 +395,9 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
     const uint8_t *ty = ty_in.as<uint8_t>();
 
     // 1. ranges, row pointers, types
+    ++G.last_launches;
     k_check_rows<<<blocks_for(n + 1, kThreads), kThreads, 0, s>>>(n, nnz, rp, ty, L, status);
+    if (nnz > 0) ++G.last_launches;
     if (nnz > 0) k_check_cols<<<blocks_for(nnz, kThreads), kThreads, 0, s>>>(nnz, n, cl, status);
     TG_CK(cudaGetLastError());
     if (read_status(G.status, s) & ST_INVALID_GRAPH) throw Error{TG_ERR_INVALID_GRAPH, "row pointers, ids or types"};
@@ -393,6 +410,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         TBuf keys(sizeof(unsigned long long) * std::max<int64_t>(n, 1), s), keys2(sizeof(unsigned long long) * std::max<int64_t>(n, 1), s);
         TBuf vals(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
         if (n > 0) {
+            ++G.last_launches;
             k_degree_keys<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, rp, G.node_off.as<int64_t>(), ngraphs,
                                                                        keys.as<unsigned long long>(), vals.as<int32_t>());
             TG_CK(cudaGetLastError());
@@ -403,6 +421,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
             }, s);
         }
         TBuf ndeg(sizeof(int64_t) * (n + 1), s);
+        ++G.last_launches;
         k_inverse<<<blocks_for(n + 1, kThreads), kThreads, 0, s>>>(n, G.old_of.as<int32_t>(), rp, new_of.as<int32_t>(),
                                                                    ndeg.as<int64_t>());
         TG_CK(cudaGetLastError());
@@ -414,10 +433,12 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
     // 3. rows sorted by (type, internal id)
     G.adj.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
     G.toff.alloc(sizeof(int32_t) * std::max<int64_t>(n * (L + 1), 1));
+    G.pivot.alloc(sizeof(int32_t) * std::max<int64_t>(n * L, 1));
     G.ty.alloc(std::max<int64_t>(n, 1));
     {
         TBuf keys(sizeof(unsigned long long) * std::max<int64_t>(nnz, 1), s), keys2(sizeof(unsigned long long) * std::max<int64_t>(nnz, 1), s);
         if (n > 0) {
+            ++G.last_launches;
             k_fill_keys<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(
                 n, rp, cl, ty, new_of.as<int32_t>(), G.rp.as<int64_t>(), G.node_off.as<int64_t>(), ngraphs,
                 keys.as<unsigned long long>(), status);
@@ -431,13 +452,16 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
             }, s);
         }
         if (n > 0) {
+            ++G.last_launches;
             k_rows<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(n, L, G.rp.as<int64_t>(), keys2.as<unsigned long long>(),
-                                                                       G.adj.as<int32_t>(), G.toff.as<int32_t>(), status);
+                                                                       G.adj.as<int32_t>(), G.toff.as<int32_t>(),
+                                                                       G.pivot.as<int32_t>(), status);
             TG_CK(cudaGetLastError());
         }
     }
     // types by internal id
     if (n > 0) {
+        ++G.last_launches;
         k_gather_types<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, G.old_of.as<int32_t>(), ty, G.ty.as<uint8_t>());
         TG_CK(cudaGetLastError());
     }
@@ -456,6 +480,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         TBuf counter(sizeof(unsigned long long), s);
         TG_CK(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), s));
         if (n > 0) {
+            ++G.last_launches;
             k_edge_keys<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(
                 n, G.rp.as<int64_t>(), G.adj.as<int32_t>(), G.old_of.as<int32_t>(), m, ekeys.as<unsigned long long>(),
                 eslots.as<int64_t>(), counter.as<unsigned long long>(), status);
@@ -470,6 +495,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
                 return cub::DeviceRadixSort::SortPairs(t, b, ekeys.as<unsigned long long>(), ekeys2.as<unsigned long long>(),
                                                        eslots.as<int64_t>(), eslots2.as<int64_t>(), m, 0, 64, s);
             }, s);
+            ++G.last_launches;
             k_edges<<<blocks_for(m, kThreads), kThreads, 0, s>>>(
                 m, ekeys2.as<unsigned long long>(), eslots2.as<int64_t>(), G.view(), new_of.as<int32_t>(),
                 G.e_lo.as<int32_t>(), G.e_hi.as<int32_t>(), G.e_slot_lo.as<int64_t>(), G.e_slot_hi.as<int64_t>(),
@@ -497,6 +523,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
     // 5. per-node typed degree sums
     G.delta.alloc(sizeof(int64_t) * std::max<int64_t>(n * L * L, 1));
     if (n > 0) {
+        ++G.last_launches;
         k_delta<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(G.view(), G.delta.as<int64_t>());
         TG_CK(cudaGetLastError());
     }
@@ -507,7 +534,9 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         TBuf fl(std::max<int64_t>(n, 1), s), fh(std::max<int64_t>(n, 1), s), ids(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
         TBuf key(sizeof(unsigned long long) * std::max<int64_t>(n, 1), s);
         if (n > 0) {
+            ++G.last_launches;
             k_anchor_work<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(G.view(), work.as<int64_t>());
+            ++G.last_launches;
             k_classify_anchors<<<blocks_for(n, kThreads), kThreads, 0, s>>>(
                 n, work.as<int64_t>(), opt.light_anchor_max_wedges, fl.as<uint8_t>(), fh.as<uint8_t>(), ids.as<int32_t>(),
                 key.as<unsigned long long>());
@@ -515,12 +544,13 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         }
         G.n_anchors_light = select_flagged(ids.as<int32_t>(), fl.as<uint8_t>(), n, G.anchors_light, s);
         G.n_anchors_heavy = select_flagged(ids.as<int32_t>(), fh.as<uint8_t>(), n, G.anchors_heavy, s);
-        sort_desc_by_key(G.anchors_heavy, G.n_anchors_heavy, key.as<unsigned long long>(), s);
+        sort_desc_by_key(G.anchors_heavy, G.n_anchors_heavy, key.as<unsigned long long>(), s, G.last_launches);
     }
     {
         TBuf fl(std::max<int64_t>(m, 1), s), fh(std::max<int64_t>(m, 1), s), ids(sizeof(int32_t) * std::max<int64_t>(m, 1), s);
         TBuf cost(sizeof(unsigned long long) * std::max<int64_t>(m, 1), s);
         if (m > 0) {
+            ++G.last_launches;
             k_classify_edges<<<blocks_for(m, kThreads), kThreads, 0, s>>>(
                 m, G.view(), opt.light_edge_max_degree, fl.as<uint8_t>(), fh.as<uint8_t>(), ids.as<int32_t>(),
                 cost.as<unsigned long long>());
@@ -528,7 +558,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         }
         G.n_edges_light = select_flagged(ids.as<int32_t>(), fl.as<uint8_t>(), m, G.edges_light, s);
         G.n_edges_heavy = select_flagged(ids.as<int32_t>(), fh.as<uint8_t>(), m, G.edges_heavy, s);
-        sort_desc_by_key(G.edges_heavy, G.n_edges_heavy, cost.as<unsigned long long>(), s);
+        sort_desc_by_key(G.edges_heavy, G.n_edges_heavy, cost.as<unsigned long long>(), s, G.last_launches);
     }
     if (read_status(G.status, s) & ST_INVALID_GRAPH) throw Error{TG_ERR_INVALID_GRAPH, "asymmetric rows"};
 }

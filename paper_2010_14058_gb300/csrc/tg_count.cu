@@ -359,22 +359,29 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
 // Shared workspace of one edge.
 struct EdgeWs {
     unsigned long long TCi[kMaxL * kMaxL], TCj[kMaxL * kMaxL], DT[kMaxL * kMaxL], K[kMaxL * kMaxL];
+    int64_t Pm[kMaxL * kMaxL];                  // 3-paths j - w - r - i by (type w, type r); then Q
+    int64_t Ks[kMaxL * kMaxL];                  // ordered adjacent pairs in T (K + K^T)
+    int64_t taui[kMaxL * kMaxL], tauj[kMaxL * kMaxL], deli[kMaxL * kMaxL], delj[kMaxL * kMaxL];
+    int64_t c[kMaxL], a[kMaxL], b[kMaxL], di[kMaxL], dj[kMaxL];
     int32_t tstart[kMaxL + 1];   // T list offsets per type
     int32_t nT;
-    int32_t wcount[16];          // per-warp compaction counts (CTA variant)
+    int32_t p, q;                // types of the endpoints
+    int32_t wcount[32];          // per-warp compaction counts (CTA variant)
 };
 
 // Enumerates T_ij (typed intersection), appends it to Tlist in (type, id)
 // order and accumulates TCi, TCj, DT.  `gsize` threads of the group, thread
 // rank `gr`; the group has gsize/32 warps.  bar() is the group barrier.
 template <class Bar>
-__device__ void enumerate_T(const GraphView &g, const CountView &cv, int32_t i, int32_t j, EdgeWs &ws,
+__device__ void enumerate_T(const GraphView &g, const CountView &cv, int64_t e, int32_t i, int32_t j, EdgeWs &ws,
                             int32_t *Tlist, int64_t Tcap, int gsize, int gr, Bar bar) {
     const int L = g.L;
     const int lane = gr & 31, wid = gr >> 5, nwarp = gsize >> 5;
     int32_t base = 0;
     for (int t = 0; t < L; ++t) {
         if (gr == 0) ws.tstart[t] = base;
+        const uint32_t ct = cv.C[e * L + t];      // |T_ij^t| from k_tri: nothing to find when 0
+        if (ct == 0) continue;
         int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
         int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
         bool swapped = false;
@@ -383,6 +390,10 @@ __device__ void enumerate_T(const GraphView &g, const CountView &cv, int32_t i, 
             x = ei; ei = ej; ej = x;
             swapped = true;
         }
+        // per-thread sums over this type segment, reduced per warp at its end
+        unsigned long long a_ci[kMaxL], a_cj[kMaxL], a_dt[kMaxL];
+#pragma unroll
+        for (int q = 0; q < kMaxL; ++q) { a_ci[q] = 0; a_cj[q] = 0; a_dt[q] = 0; }
         for (int64_t r0 = bi; r0 < ei; r0 += gsize) {
             const int64_t s = r0 + gr;
             bool found = false;
@@ -415,14 +426,29 @@ __device__ void enumerate_T(const GraphView &g, const CountView &cv, int32_t i, 
                 const uint32_t *ci = cv.C + (int64_t)g.slot_eid[si] * L;
                 const uint32_t *cj = cv.C + (int64_t)g.slot_eid[sj] * L;
                 const int32_t *o = g.toff + (int64_t)w * (L + 1);
-                for (int q = 0; q < L; ++q) {
-                    atomicAdd(&ws.TCi[t * kMaxL + q], (unsigned long long)ci[q]);
-                    atomicAdd(&ws.TCj[t * kMaxL + q], (unsigned long long)cj[q]);
-                    atomicAdd(&ws.DT[t * kMaxL + q], (unsigned long long)(o[q + 1] - o[q]));
+#pragma unroll
+                for (int q = 0; q < kMaxL; ++q) {
+                    if (q < L) {
+                        a_ci[q] += ci[q];
+                        a_cj[q] += cj[q];
+                        a_dt[q] += (unsigned)(o[q + 1] - o[q]);
+                    }
                 }
             }
             base += total;
             if (nwarp > 1) bar();
+        }
+        if (bi < ei) {
+#pragma unroll
+            for (int q = 0; q < kMaxL; ++q) {
+                if (q >= L) break;
+                const unsigned long long x1 = warp_sum_u64(a_ci[q]), x2 = warp_sum_u64(a_cj[q]), x3 = warp_sum_u64(a_dt[q]);
+                if (lane == 0) {
+                    if (x1) atomicAdd(&ws.TCi[t * kMaxL + q], x1);
+                    if (x2) atomicAdd(&ws.TCj[t * kMaxL + q], x2);
+                    if (x3) atomicAdd(&ws.DT[t * kMaxL + q], x3);
+                }
+            }
         }
     }
     if (gr == 0) {
@@ -433,131 +459,234 @@ __device__ void enumerate_T(const GraphView &g, const CountView &cv, int32_t i, 
 }
 
 // K: adjacent pairs (w, x) of T with w < x, by type.  For each w, either
-// scan Gamma_w's part above w and look each x up in T (cost d+_w log|T|),
-// or take each x > w of T and look it up in Gamma_w (cost |T| log d_w).
+// scan N+(w) = {x in Gamma_w : x > w} (all types, flattened over the warp's
+// lanes, each x looked up in T's sorted segment of its type), or take each
+// x > w of T and look it up in Gamma_w -- whichever touches fewer entries.
 template <class Bar>
 __device__ void count_K(const GraphView &g, EdgeWs &ws, const int32_t *Tlist, int gsize, int gr, Bar bar) {
     const int L = g.L;
     const int lane = gr & 31, wid = gr >> 5, nwarp = gsize >> 5;
     const int32_t nT = ws.nT;
+    if (nT < 2) {
+        bar();
+        return;
+    }
+    int32_t ts[kMaxL + 1];
+#pragma unroll
+    for (int q = 0; q <= kMaxL; ++q) ts[q] = q <= L ? ws.tstart[q] : nT;
+    const int32_t npair = nT * (nT - 1) / 2;
+    if (npair <= 2 * gsize) {
+        // few pairs: one pair {T[a], T[b]} per thread, adjacency by binary search
+        // of the larger id in the smaller id's typed segment; each adjacent pair
+        // is counted once, as (smaller id, larger id)
+        for (int32_t pk = gr; pk < npair; pk += gsize) {
+            int32_t a = 0, rem = pk;
+            while (rem >= nT - 1 - a) { rem -= nT - 1 - a; ++a; }
+            const int32_t b = a + 1 + rem;
+            int ta = 0, tb = 0;
+#pragma unroll
+            for (int qq = 1; qq < kMaxL; ++qq) {
+                ta += (qq < L && ts[qq] <= a) ? 1 : 0;
+                tb += (qq < L && ts[qq] <= b) ? 1 : 0;
+            }
+            int32_t w = Tlist[a], x = Tlist[b];
+            int tw = ta, tx = tb;
+            if (x < w) { int32_t y = w; w = x; x = y; int ty = tw; tw = tx; tx = ty; }
+            const int64_t sb = seg_begin(g, w, tx), se = seg_end(g, w, tx);
+            const int64_t r = lower_bound_i32(g.adj, sb, se, x);
+            if (r < se && g.adj[r] == x) atomicAdd(&ws.K[tw * kMaxL + tx], 1ull);
+        }
+        bar();
+        return;
+    }
     for (int32_t kw = wid; kw < nT; kw += nwarp) {
         const int32_t w = Tlist[kw];
         int tw = 0;
-        while (ws.tstart[tw + 1] <= kw) ++tw;
-        // out-degree of w above w, per type (lanes < L), and the cost of each way
-        int64_t cut = 0, dplus = 0;
+#pragma unroll
+        for (int q = 1; q < kMaxL; ++q) tw += (q < L && ts[q] <= kw) ? 1 : 0;
+        // N+(w) per type: [pb_q, pb_q + cnt_q)
+        int64_t pb = 0;
+        int32_t cnt = 0;
+        const int64_t rw = g.rp[w];
         if (lane < L) {
-            int64_t b = seg_begin(g, w, lane), e = seg_end(g, w, lane);
-            cut = lower_bound_i32(g.adj, b, e, w + 1);
-            dplus = e - cut;
+            pb = rw + g.pivot[(int64_t)w * L + lane];
+            cnt = (int32_t)(rw + g.toff[(int64_t)w * (L + 1) + lane + 1] - pb);
         }
-        int64_t dsum = dplus;
-        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-        const int64_t dw = g.rp[w + 1] - g.rp[w];
-        int lg = 1;
-        while ((1ll << lg) < dw + 1) ++lg;
+        int32_t pre = cnt;                                   // inclusive prefix over lanes < L
+#pragma unroll
+        for (int o = 1; o < kMaxL; o <<= 1) {
+            int32_t v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        int64_t pbq[kMaxL];
+        int32_t preq[kMaxL];
+#pragma unroll
+        for (int q = 0; q < kMaxL; ++q) {
+            pbq[q] = __shfl_sync(0xffffffffu, pb, q);
+            preq[q] = q < L ? __shfl_sync(0xffffffffu, pre, q) : 0x7fffffff;
+        }
+        const int32_t dplus = preq[L - 1];
+        if (dplus == 0) continue;
+        unsigned cq[kMaxL];
+#pragma unroll
+        for (int q = 0; q < kMaxL; ++q) cq[q] = 0;
         int lgT = 1;
         while ((1 << lgT) < nT + 1) ++lgT;
-        const bool scan_w = dsum * lgT <= (int64_t)nT * lg;
-        unsigned long long acc[kMaxL];
+        const int64_t dw = g.rp[w + 1] - rw;
+        int lgd = 1;
+        while ((1ll << lgd) < dw + 1) ++lgd;
+        // members of T above w, per type: [tg_q, ts_{q+1}) (each T segment is id-sorted)
+        int32_t tgt = 0;
+        if (lane < L) {
+            int32_t lo = ts[0], hi = ts[0];
 #pragma unroll
-        for (int q = 0; q < kMaxL; ++q) acc[q] = 0;
-        if (scan_w) {
-            for (int q = 0; q < L; ++q) {
-                const int64_t b = __shfl_sync(0xffffffffu, cut, q);
-                const int64_t e = seg_end(g, w, q);
-                const int32_t tb = ws.tstart[q], te = ws.tstart[q + 1];
-                if (tb == te) continue;
-                for (int64_t s = b + lane; s < e; s += 32) {
-                    const int32_t x = g.adj[s];
-                    int32_t lo = tb, hi = te;
-                    while (lo < hi) {
-                        int32_t mid = (lo + hi) >> 1;
-                        if (Tlist[mid] < x) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < te && Tlist[lo] == x) acc[q] += 1;
+            for (int qq = 0; qq < kMaxL; ++qq)
+                if (qq == lane) { lo = ts[qq]; hi = ts[qq + 1]; }
+            while (lo < hi) {
+                int32_t mid = (lo + hi) >> 1;
+                if (Tlist[mid] <= w) lo = mid + 1; else hi = mid;
+            }
+            tgt = lo;
+        }
+        int32_t above = 0;
+        if (lane < L) {
+            int32_t te = 0;
+#pragma unroll
+            for (int qq = 0; qq < kMaxL; ++qq)
+                if (qq == lane) te = ts[qq + 1];
+            above = te - tgt;
+        }
+        int32_t nabove = above;
+        for (int o = 16; o > 0; o >>= 1) nabove += __shfl_xor_sync(0xffffffffu, nabove, o);
+        if (nabove == 0) continue;
+        if ((int64_t)dplus * lgT <= (int64_t)nabove * lgd) {
+            for (int32_t f = lane; f < dplus; f += 32) {
+                int q = 0;
+#pragma unroll
+                for (int qq = 0; qq < kMaxL - 1; ++qq) q += (f >= preq[qq]) ? 1 : 0;
+                int64_t slot = 0;
+#pragma unroll
+                for (int qq = 0; qq < kMaxL; ++qq)
+                    if (qq == q) slot = pbq[qq] + (f - (qq ? preq[qq - 1] : 0));
+                const int32_t x = g.adj[slot];
+                int32_t lo = 0, hi = 0;
+#pragma unroll
+                for (int qq = 0; qq < kMaxL; ++qq)
+                    if (qq == q) { lo = ts[qq]; hi = ts[qq + 1]; }
+                const int32_t te = hi;
+                while (lo < hi) {
+                    int32_t mid = (lo + hi) >> 1;
+                    if (Tlist[mid] < x) lo = mid + 1; else hi = mid;
+                }
+                if (lo < te && Tlist[lo] == x) {
+#pragma unroll
+                    for (int qq = 0; qq < kMaxL; ++qq) cq[qq] += (qq == q) ? 1u : 0u;
                 }
             }
         } else {
             for (int q = 0; q < L; ++q) {
-                const int32_t tb = ws.tstart[q], te = ws.tstart[q + 1];
+                const int32_t kb = __shfl_sync(0xffffffffu, tgt, q);
+                const int32_t ke = ts[q + 1 <= kMaxL ? q + 1 : kMaxL];
+                if (kb >= ke) continue;
                 const int64_t b = seg_begin(g, w, q), e = seg_end(g, w, q);
                 if (b == e) continue;
-                for (int32_t k = tb + lane; k < te; k += 32) {
+                unsigned c = 0;
+                for (int32_t k = kb + lane; k < ke; k += 32) {
                     const int32_t x = Tlist[k];
-                    if (x <= w) continue;
                     const int64_t r = lower_bound_i32(g.adj, b, e, x);
-                    if (r < e && g.adj[r] == x) acc[q] += 1;
+                    c += (r < e && g.adj[r] == x) ? 1u : 0u;
                 }
+#pragma unroll
+                for (int qq = 0; qq < kMaxL; ++qq) cq[qq] += (qq == q) ? c : 0u;
             }
         }
-        for (int q = 0; q < L; ++q) {
-            unsigned long long v = warp_sum_u64(acc[q]);
-            if (lane == 0 && v) atomicAdd(&ws.K[tw * kMaxL + q], v);
+#pragma unroll
+        for (int q = 0; q < kMaxL; ++q) {
+            if (q >= L) break;
+            unsigned v = warp_sum_u32(cq[q]);
+            if (lane == 0 && v) atomicAdd(&ws.K[tw * kMaxL + q], (unsigned long long)v);
         }
     }
     bar();
 }
 
-// Orbit values of one type pair (t <= u) from the workspace; returns false
-// if an internal identity fails (negative count or odd diagonal).
-struct EdgeScalars {
-    int L, p, q;
-    int64_t c[kMaxL], a[kMaxL], b[kMaxL], di[kMaxL], dj[kMaxL];
-    const int64_t *tau_i, *tau_j, *del_i, *del_j;
-    const uint32_t *A;   // nullptr-free: A base
-    int64_t nnz, slot_ij, slot_ji;
-};
-
-__device__ __forceinline__ int64_t ld(const unsigned long long *m, int t, int u) {
-    return (int64_t)m[t * kMaxL + u];
+// Derived typed counts of one edge, each matrix entry computed once, in
+// place, in dependency order (x, y index types; z = x * kMaxL + y):
+//   Ks  = K + K^T                       ordered adjacent pairs in T
+//   TCi -> CTi = TCi - Ks - [y=q] c_x   (w in T^x, r in S_i^y adjacent)
+//   TCj -> CTj = TCj - Ks - [y=p] c_x
+//   taui -> Wi = tau_i - CTi - CTi^T - Ks - [x=q] c_y - [y=q] c_x
+//   tauj -> Wj = tau_j - CTj - CTj^T - Ks - [x=p] c_y - [y=p] c_x
+//   Pm  -> Q   = P - CTj^T - CTi - Ks  (w in S_j^x, r in S_i^y: 4-cycles)
+//   deli -> Ri = delta_i - DT - [x=q] d_j^y - [y=p] a_x - Wi - CTi^T - Q^T
+//   delj -> Rj = delta_j - DT - [x=p] d_i^y - [y=q] b_x - Wj - CTj^T - Q
+//   DT  -> G8  = DT - ([y=p]+[y=q]) c_x - Ks - CTi - CTj
+template <class Bar>
+__device__ void derive_matrices(EdgeWs &ws, int L, int gsize, int gr, Bar bar) {
+    const int p = ws.p, q = ws.q;
+    const int n2 = L * L;
+    for (int k = gr; k < n2; k += gsize) {
+        const int x = k / L, y = k % L, z = x * kMaxL + y, zt = y * kMaxL + x;
+        ws.Ks[z] = (int64_t)ws.K[z] + (int64_t)ws.K[zt];
+    }
+    bar();
+    for (int k = gr; k < n2; k += gsize) {
+        const int x = k / L, y = k % L, z = x * kMaxL + y;
+        ws.TCi[z] = (unsigned long long)((int64_t)ws.TCi[z] - ws.Ks[z] - (y == q ? ws.c[x] : 0));
+        ws.TCj[z] = (unsigned long long)((int64_t)ws.TCj[z] - ws.Ks[z] - (y == p ? ws.c[x] : 0));
+    }
+    bar();
+    const long long *CTi = reinterpret_cast<const long long *>(ws.TCi);
+    const long long *CTj = reinterpret_cast<const long long *>(ws.TCj);
+    for (int k = gr; k < n2; k += gsize) {
+        const int x = k / L, y = k % L, z = x * kMaxL + y, zt = y * kMaxL + x;
+        ws.taui[z] = ws.taui[z] - CTi[z] - CTi[zt] - ws.Ks[z] - (x == q ? ws.c[y] : 0) - (y == q ? ws.c[x] : 0);
+        ws.tauj[z] = ws.tauj[z] - CTj[z] - CTj[zt] - ws.Ks[z] - (x == p ? ws.c[y] : 0) - (y == p ? ws.c[x] : 0);
+        ws.Pm[z] = ws.Pm[z] - CTj[zt] - CTi[z] - ws.Ks[z];
+    }
+    bar();
+    for (int k = gr; k < n2; k += gsize) {
+        const int x = k / L, y = k % L, z = x * kMaxL + y, zt = y * kMaxL + x;
+        const int64_t dt = (int64_t)ws.DT[z];
+        ws.deli[z] = ws.deli[z] - dt - (x == q ? ws.dj[y] : 0) - (y == p ? ws.a[x] : 0) - ws.taui[z] - CTi[zt] - ws.Pm[zt];
+        ws.delj[z] = ws.delj[z] - dt - (x == p ? ws.di[y] : 0) - (y == q ? ws.b[x] : 0) - ws.tauj[z] - CTj[zt] - ws.Pm[z];
+    }
+    bar();
+    for (int k = gr; k < n2; k += gsize) {
+        const int x = k / L, y = k % L, z = x * kMaxL + y;
+        ws.DT[z] = (unsigned long long)((int64_t)ws.DT[z] - ((y == p ? 1 : 0) + (y == q ? 1 : 0)) * ws.c[x] - ws.Ks[z] -
+                                        CTi[z] - CTj[z]);
+    }
+    bar();
 }
 
-__device__ bool orbit_values(const EdgeScalars &E, const EdgeWs &ws, int t, int u, int64_t *gv /*[10]: g3..g12*/) {
-    const int L = E.L, p = E.p, q = E.q;
-    auto K = [&](int x, int y) { return ld(ws.K, x, y) + ld(ws.K, y, x); };   // ordered adjacent pairs
-    auto CTi = [&](int x, int y) { return ld(ws.TCi, x, y) - K(x, y) - (y == q ? E.c[x] : 0); };
-    auto CTj = [&](int x, int y) { return ld(ws.TCj, x, y) - K(x, y) - (y == p ? E.c[x] : 0); };
-    auto Wi = [&](int x, int y) {
-        return E.tau_i[x * L + y] - CTi(x, y) - CTi(y, x) - K(x, y) - (x == q ? E.c[y] : 0) - (y == q ? E.c[x] : 0);
-    };
-    auto Wj = [&](int x, int y) {
-        return E.tau_j[x * L + y] - CTj(x, y) - CTj(y, x) - K(x, y) - (x == p ? E.c[y] : 0) - (y == p ? E.c[x] : 0);
-    };
-    auto P = [&](int x, int y) {
-        return (int64_t)E.A[(int64_t)(y * L + x) * E.nnz + E.slot_ij] + (int64_t)E.A[(int64_t)(x * L + y) * E.nnz + E.slot_ji];
-    };
-    auto Q = [&](int x, int y) { return P(x, y) - CTj(y, x) - CTi(x, y) - K(x, y); };
-    auto DT = [&](int x, int y) { return ld(ws.DT, x, y); };
-    auto Ri = [&](int x, int y) {
-        return E.del_i[x * L + y] - DT(x, y) - (x == q ? E.dj[y] : 0) - (y == p ? E.a[x] : 0) - Wi(x, y) - CTi(y, x) - Q(y, x);
-    };
-    auto Rj = [&](int x, int y) {
-        return E.del_j[x * L + y] - DT(x, y) - (x == p ? E.di[y] : 0) - (y == q ? E.b[x] : 0) - Wj(x, y) - CTj(y, x) - Q(x, y);
-    };
-    auto G8 = [&](int x, int y) {
-        return DT(x, y) - ((y == p ? 1 : 0) + (y == q ? 1 : 0)) * E.c[x] - K(x, y) - CTi(x, y) - CTj(x, y);
-    };
+// Orbit values of one type pair (t <= u) from the derived matrices;
+// returns false if an internal identity fails (negative count, odd diagonal).
+__device__ __noinline__ bool orbit_values(const EdgeWs &ws, int t, int u, int64_t *gv /*[10]: g3..g12*/) {
+    const long long *CTi = reinterpret_cast<const long long *>(ws.TCi);
+    const long long *CTj = reinterpret_cast<const long long *>(ws.TCj);
+    const long long *G8 = reinterpret_cast<const long long *>(ws.DT);
+    const int tu = t * kMaxL + u, ut = u * kMaxL + t, tt = t * kMaxL + t;
     bool ok = true;
     int64_t g3, g6, g7, g8, g10, g12;
     if (t != u) {
-        g3 = Ri(t, u) + Rj(t, u) + Ri(u, t) + Rj(u, t);
-        g6 = Q(t, u) + Q(u, t);
-        g7 = Wi(t, u) + Wj(t, u);
-        g8 = G8(t, u) + G8(u, t);
-        g10 = CTi(t, u) + CTj(t, u) + CTi(u, t) + CTj(u, t);
-        g12 = K(t, u);
+        g3 = ws.deli[tu] + ws.delj[tu] + ws.deli[ut] + ws.delj[ut];   // Ri + Rj, both orders
+        g6 = ws.Pm[tu] + ws.Pm[ut];                                   // Q
+        g7 = ws.taui[tu] + ws.tauj[tu];                               // Wi + Wj
+        g8 = G8[tu] + G8[ut];
+        g10 = CTi[tu] + CTj[tu] + CTi[ut] + CTj[ut];
+        g12 = ws.Ks[tu];
     } else {
-        g3 = Ri(t, t) + Rj(t, t);
-        g6 = Q(t, t);
-        int64_t w2 = Wi(t, t) + Wj(t, t), k2 = K(t, t);
-        ok = ok && !(w2 & 1) && !(k2 & 1);
+        g3 = ws.deli[tt] + ws.delj[tt];
+        g6 = ws.Pm[tt];
+        const int64_t w2 = ws.taui[tt] + ws.tauj[tt], k2 = ws.Ks[tt];
+        ok = !(w2 & 1) && !(k2 & 1);
         g7 = w2 / 2;
-        g8 = G8(t, t);
-        g10 = CTi(t, t) + CTj(t, t);
+        g8 = G8[tt];
+        g10 = CTi[tt] + CTj[tt];
         g12 = k2 / 2;
     }
-    const int64_t at = E.a[t], au = E.a[u], bt = E.b[t], bu = E.b[u], ct = E.c[t], cu = E.c[u];
+    const int64_t at = ws.a[t], au = ws.a[u], bt = ws.b[t], bu = ws.b[u], ct = ws.c[t], cu = ws.c[u];
     int64_t g4, g5, g9, g11;
     if (t == u) {
         g4 = at * bt - g6;                                   // Lemma 1
@@ -573,7 +702,6 @@ __device__ bool orbit_values(const EdgeScalars &E, const EdgeWs &ws, int t, int 
     gv[0] = g3; gv[1] = g4; gv[2] = g5; gv[3] = g6; gv[4] = g7;
     gv[5] = g8; gv[6] = g9; gv[7] = g10; gv[8] = g11; gv[9] = g12;
     for (int k = 0; k < 10; ++k) ok = ok && gv[k] >= 0;
-    (void)L;
     return ok;
 }
 
@@ -597,47 +725,56 @@ __device__ __forceinline__ int graphlet_block(int o) {
     }
 }
 
-// Epilogue of one edge: writes the row, adds to the CTA histogram.
+// Epilogue of one edge: stages the per-edge inputs in shared memory, then
+// writes the row and adds to the CTA histogram.
 template <class Bar>
 __device__ void edge_epilogue(const GraphView &g, const CountView &cv, int64_t e, int32_t i, int32_t j, EdgeWs &ws,
                               uint32_t *row, unsigned long long *hist, int gsize, int gr, Bar bar) {
     const int L = g.L;
-    EdgeScalars E;
-    E.L = L;
-    E.p = g.ty[i];
-    E.q = g.ty[j];
-    for (int t = 0; t < L; ++t) {
-        E.c[t] = cv.C[e * L + t];
-        E.di[t] = typed_degree(g, i, t);
-        E.dj[t] = typed_degree(g, j, t);
-        E.a[t] = E.di[t] - E.c[t] - (E.q == t ? 1 : 0);
-        E.b[t] = E.dj[t] - E.c[t] - (E.p == t ? 1 : 0);
+    const int p = g.ty[i], q = g.ty[j];
+    if (gr == 0) { ws.p = p; ws.q = q; }
+    for (int t = gr; t < L; t += gsize) {
+        const int64_t c = cv.C[e * L + t];
+        const int64_t di = typed_degree(g, i, t), dj = typed_degree(g, j, t);
+        ws.c[t] = c;
+        ws.di[t] = di;
+        ws.dj[t] = dj;
+        ws.a[t] = di - c - (q == t ? 1 : 0);
+        ws.b[t] = dj - c - (p == t ? 1 : 0);
     }
-    E.tau_i = cv.tau + (int64_t)i * L * L;
-    E.tau_j = cv.tau + (int64_t)j * L * L;
-    E.del_i = g.delta + (int64_t)i * L * L;
-    E.del_j = g.delta + (int64_t)j * L * L;
-    E.A = cv.A;
-    E.nnz = g.nnz;
-    E.slot_ij = g.e_slot_lo[e];
-    E.slot_ji = g.e_slot_hi[e];
+    const int64_t slot_ij = g.e_slot_lo[e], slot_ji = g.e_slot_hi[e];
+    const int64_t *tau_i = cv.tau + (int64_t)i * L * L, *tau_j = cv.tau + (int64_t)j * L * L;
+    const int64_t *del_i = g.delta + (int64_t)i * L * L, *del_j = g.delta + (int64_t)j * L * L;
+    for (int k = gr; k < L * L; k += gsize) {
+        const int x = k / L, y = k % L;
+        const int z = x * kMaxL + y;
+        // P[x][y]: 3-paths j - w - r - i with phi_w = x, phi_r = y (slot i->j holds
+        // [type next to i][type next to j], slot j->i the reverse)
+        ws.Pm[z] = (int64_t)cv.A[(int64_t)(y * L + x) * g.nnz + slot_ij] + (int64_t)cv.A[(int64_t)(x * L + y) * g.nnz + slot_ji];
+        ws.taui[z] = tau_i[k];
+        ws.tauj[z] = tau_j[k];
+        ws.deli[z] = del_i[k];
+        ws.delj[z] = del_j[k];
+    }
+    bar();
+    derive_matrices(ws, L, gsize, gr, bar);
     const int P = L * (L + 1) / 2;
     // 3-node slots and 2-node / 3-node global blocks
     for (int t = gr; t < L; t += gsize) {
-        int64_t s3 = E.a[t] + E.b[t];
-        if (E.a[t] < 0 || E.b[t] < 0) set_status(cv.status, ST_INTERNAL);
+        const int64_t s3 = ws.a[t] + ws.b[t];
+        if (ws.a[t] < 0 || ws.b[t] < 0) set_status(cv.status, ST_INTERNAL);
         if (row) {
             row[t] = sat32(s3, cv.status);
-            row[L + t] = sat32(E.c[t], cv.status);
+            row[L + t] = sat32(ws.c[t], cv.status);
         }
-        int ms[3] = {E.p, E.q, t};
+        int ms[3] = {p, q, t};
         sort3(ms);
-        int r = multiset_rank_dev(L, 3, ms);
+        const int r = multiset_rank_dev(L, 3, ms);
         if (s3) atomicAdd(&hist[gblock_off(L, 1) + r], (unsigned long long)s3);
-        if (E.c[t]) atomicAdd(&hist[gblock_off(L, 2) + r], (unsigned long long)E.c[t]);
+        if (ws.c[t]) atomicAdd(&hist[gblock_off(L, 2) + r], (unsigned long long)ws.c[t]);
     }
     if (gr == 0) {
-        int ms[2] = {E.p < E.q ? E.p : E.q, E.p < E.q ? E.q : E.p};
+        int ms[2] = {p < q ? p : q, p < q ? q : p};
         atomicAdd(&hist[multiset_rank_dev(L, 2, ms)], 1ull);
     }
     for (int pi = gr; pi < P; pi += gsize) {
@@ -645,8 +782,8 @@ __device__ void edge_epilogue(const GraphView &g, const CountView &cv, int64_t e
         while (pair_idx(L, t, L - 1) < pi) ++t;
         const int u = t + (pi - pair_idx(L, t, t));
         int64_t gv[10];
-        if (!orbit_values(E, ws, t, u, gv)) set_status(cv.status, ST_INTERNAL);
-        int ms[4] = {E.p, E.q, t, u};
+        if (!orbit_values(ws, t, u, gv)) set_status(cv.status, ST_INTERNAL);
+        int ms[4] = {p, q, t, u};
         sort4(ms);
         const int r = multiset_rank_dev(L, 4, ms);
         for (int o = 3; o <= 12; ++o) {
@@ -679,16 +816,18 @@ struct Tile {
 
 // Light edges (min(d_i, d_j) <= light_max): one warp per edge, tiles of edge
 // ids that never cross a graph, a per-CTA histogram for global sums.
-__global__ void __launch_bounds__(kEdgeThreads) k_edge4_light(GraphView g, CountView cv, const Tile *__restrict__ tiles,
+// Dynamic shared memory: [histogram G u64][EdgeWs per warp][T list per warp].
+__global__ void __launch_bounds__(kEdgeThreads, 4) k_edge4_light(GraphView g, CountView cv, const Tile *__restrict__ tiles,
                                                              int64_t n_tiles, int64_t light_max, int64_t e_begin,
                                                              uint32_t *per_edge_out, unsigned long long *gacc) {
-    extern __shared__ unsigned long long hist[];
-    __shared__ EdgeWs wsa[kEdgeThreads / 32];
-    __shared__ int32_t tl[kEdgeThreads / 32][kTCapWarp];
+    extern __shared__ unsigned long long dsm[];
     const int L = g.L;
     const int G = (int)global_slots(L, 4);
     const int S = (int)per_edge_slots(L, 4);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long *hist = dsm;
+    EdgeWs *wsa = reinterpret_cast<EdgeWs *>(dsm + ((G + 1) & ~1));
+    int32_t *tl = reinterpret_cast<int32_t *>(wsa + kEdgeThreads / 32) + wid * kTCapWarp;
     EdgeWs &ws = wsa[wid];
     for (int s = threadIdx.x; s < G; s += blockDim.x) hist[s] = 0;
     __syncthreads();
@@ -707,8 +846,8 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge4_light(GraphView g, Count
             if ((di < dj ? di : dj) > light_max) continue;
             clear_ws(ws, 32, lane);
             __syncwarp();
-            enumerate_T(g, cv, i, j, ws, tl[wid], kTCapWarp, 32, lane, wbar);
-            count_K(g, ws, tl[wid], 32, lane, wbar);
+            enumerate_T(g, cv, e, i, j, ws, tl, kTCapWarp, 32, lane, wbar);
+            count_K(g, ws, tl, 32, lane, wbar);
             uint32_t *row = per_edge_out ? per_edge_out + (e - e_begin) * S : nullptr;
             edge_epilogue(g, cv, e, i, j, ws, row, hist, 32, lane, wbar);
         }
@@ -719,16 +858,17 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge4_light(GraphView g, Count
 
 // Heavy edges: one CTA per edge (the list is sorted by cost, largest first).
 // T lives in shared memory when it fits, else in this CTA's global slice.
-__global__ void __launch_bounds__(kHeavyThreads) k_edge4_heavy(GraphView g, CountView cv, const int32_t *__restrict__ list,
+__global__ void __launch_bounds__(kHeavyThreads, 2) k_edge4_heavy(GraphView g, CountView cv, const int32_t *__restrict__ list,
                                                               int64_t n_list, int64_t e_begin, int64_t e_end,
                                                               uint32_t *per_edge_out, unsigned long long *gacc,
                                                               int32_t *tscratch, int64_t tscratch_stride) {
-    extern __shared__ unsigned long long hist[];
-    __shared__ EdgeWs ws;
-    __shared__ int32_t tl_smem[kTCapSmemHeavy];
+    extern __shared__ unsigned long long dsm[];
     const int L = g.L;
     const int G = (int)global_slots(L, 4);
     const int S = (int)per_edge_slots(L, 4);
+    unsigned long long *hist = dsm;
+    EdgeWs &ws = *reinterpret_cast<EdgeWs *>(dsm + ((G + 1) & ~1));
+    int32_t *tl_smem = reinterpret_cast<int32_t *>(&ws + 1);
     for (int s = threadIdx.x; s < G; s += blockDim.x) hist[s] = 0;
     __syncthreads();
     auto bbar = []() { __syncthreads(); };
@@ -748,7 +888,7 @@ __global__ void __launch_bounds__(kHeavyThreads) k_edge4_heavy(GraphView g, Coun
         int32_t *tl = cap <= kTCapSmemHeavy ? tl_smem : tscratch + (int64_t)blockIdx.x * tscratch_stride;
         clear_ws(ws, blockDim.x, threadIdx.x);
         __syncthreads();
-        enumerate_T(g, cv, i, j, ws, tl, cap, blockDim.x, threadIdx.x, bbar);
+        enumerate_T(g, cv, e, i, j, ws, tl, cap, blockDim.x, threadIdx.x, bbar);
         count_K(g, ws, tl, blockDim.x, threadIdx.x, bbar);
         uint32_t *row = per_edge_out ? per_edge_out + (e - e_begin) * S : nullptr;
         edge_epilogue(g, cv, e, i, j, ws, row, hist, blockDim.x, threadIdx.x, bbar);
@@ -860,10 +1000,12 @@ int64_t launch_prepare(Graph &G, int k, cudaStream_t s) {
     const int sms = sm_count();
     int64_t launches = 0;
     if (G.m > 0) {
+        KernelTimer kt(G, s, "k_tri");
         k_tri<<<grid_for(G.m, 8, sms * 16), 256, 0, s>>>(gv, cv);
         ++launches;
     }
     if (G.n > 0) {
+        KernelTimer kt(G, s, "k_tau");
         k_tau<<<grid_for(G.n, 8, sms * 16), 256, 0, s>>>(gv, cv);
         ++launches;
     }
@@ -873,11 +1015,13 @@ int64_t launch_prepare(Graph &G, int k, cudaStream_t s) {
             int cap = 1;
             while (cap < 2 * G.opt.light_anchor_max_wedges) cap <<= 1;
             const size_t smem = (size_t)kLightAnchorWarps * cap * (1 + G.L) * sizeof(int32_t);
+            KernelTimer kt(G, s, "k_wedge_light");
             k_wedge_light<<<grid_for(G.n_anchors_light, kLightAnchorWarps, sms * 8), kLightAnchorWarps * 32, smem, s>>>(
                 gv, cv, G.anchors_light.as<int32_t>(), G.n_anchors_light, cap);
             ++launches;
         }
         if (G.n_anchors_heavy > 0) {
+            KernelTimer kt(G, s, "k_wedge_heavy");
             k_wedge_heavy<<<G.n_tables, kAnchorThreads, 0, s>>>(gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy);
             ++launches;
         }
@@ -918,12 +1062,16 @@ static const Tile *tiles_for(Graph &G, int64_t e_begin, int64_t e_end, int64_t &
 
 // Allocations and kernel attributes of the per-edge stage (done before any
 // capture).
+static size_t hist_bytes(int L, int k) { return (size_t)((global_slots(L, k) + 1) & ~1) * sizeof(unsigned long long); }
+static size_t light_smem(int L) {
+    return hist_bytes(L, 4) + (kEdgeThreads / 32) * (sizeof(EdgeWs) + kTCapWarp * sizeof(int32_t));
+}
+static size_t heavy_smem(int L) { return hist_bytes(L, 4) + sizeof(EdgeWs) + kTCapSmemHeavy * sizeof(int32_t); }
+
 void prepare_edges(Graph &G, int k, cudaStream_t s) {
-    const int Gs = (int)global_slots(G.L, k);
-    const int hbytes = (int)(Gs * sizeof(unsigned long long));
-    TG_CK(cudaFuncSetAttribute(k_edge3, cudaFuncAttributeMaxDynamicSharedMemorySize, hbytes));
-    TG_CK(cudaFuncSetAttribute(k_edge4_light, cudaFuncAttributeMaxDynamicSharedMemorySize, hbytes));
-    TG_CK(cudaFuncSetAttribute(k_edge4_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, hbytes));
+    TG_CK(cudaFuncSetAttribute(k_edge3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes(G.L, 3)));
+    TG_CK(cudaFuncSetAttribute(k_edge4_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)light_smem(G.L)));
+    TG_CK(cudaFuncSetAttribute(k_edge4_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem(G.L)));
     if (k == 4 && G.n_edges_heavy > 0 && !G.tscratch.p) {
         const int64_t nblk = std::min<int64_t>(G.n_edges_heavy, (int64_t)sm_count() * 2);
         const int64_t stride = std::max<int64_t>(G.max_degree, 1);
@@ -953,17 +1101,20 @@ int64_t launch_edges(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *
     int64_t n_tiles = 0;
     const Tile *tiles = tiles_for(G, e_begin, e_end, n_tiles, tmp, s);
     if (n_tiles == 0) return 0;
-    const int Gs = (int)global_slots(G.L, k);
-    const size_t hbytes = (size_t)Gs * sizeof(unsigned long long);
     if (k == 3) {
-        k_edge3<<<grid_for(n_tiles, 1, sms * 8), 256, hbytes, s>>>(gv, cv, tiles, n_tiles, e_begin, per_edge_out, gacc);
+        KernelTimer kt(G, s, "k_edge3");
+        k_edge3<<<grid_for(n_tiles, 1, sms * 8), 256, hist_bytes(G.L, 3), s>>>(gv, cv, tiles, n_tiles, e_begin, per_edge_out, gacc);
         ++launches;
     } else {
-        k_edge4_light<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), kEdgeThreads, hbytes, s>>>(
+        {
+        KernelTimer kt(G, s, "k_edge4_light");
+        k_edge4_light<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), kEdgeThreads, light_smem(G.L), s>>>(
             gv, cv, tiles, n_tiles, G.opt.light_edge_max_degree, e_begin, per_edge_out, gacc);
         ++launches;
+        }
         if (G.n_edges_heavy > 0) {
-            k_edge4_heavy<<<G.tscratch_blocks, kHeavyThreads, hbytes, s>>>(
+            KernelTimer kt(G, s, "k_edge4_heavy");
+            k_edge4_heavy<<<G.tscratch_blocks, kHeavyThreads, heavy_smem(G.L), s>>>(
                 gv, cv, G.edges_heavy.as<int32_t>(), G.n_edges_heavy, e_begin, e_end, per_edge_out, gacc,
                 G.tscratch.as<int32_t>(), G.tscratch_stride);
             ++launches;
@@ -976,6 +1127,7 @@ int64_t launch_edges(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *
 
 int64_t launch_finalize(Graph &G, int k, int64_t *global_out, cudaStream_t s) {
     const int64_t total = (int64_t)G.ngraphs * global_slots(G.L, k);
+    KernelTimer kt(G, s, "k_finalize");
     k_finalize<<<grid_for(total, 256, 1 << 20), 256, 0, s>>>(G.ngraphs, G.L, k, G.gacc.as<unsigned long long>(), global_out,
                                                               G.status.as<uint32_t>());
     TG_CK(cudaGetLastError());

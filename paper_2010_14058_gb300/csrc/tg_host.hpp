@@ -3,6 +3,8 @@
 
 #include <cstdint>
 #include <cstring>
+#include <string>
+#include <utility>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -80,7 +82,7 @@ struct Graph {
     tg_options opt;
 
     // graph (built once)
-    DBuf node_off, edge_off, rp, adj, toff, ty, old_of, slot_eid, e_lo, e_hi, e_slot_lo, e_slot_hi, delta;
+    DBuf node_off, edge_off, rp, adj, toff, pivot, ty, old_of, slot_eid, e_lo, e_hi, e_slot_lo, e_slot_hi, delta;
     // work lists
     DBuf anchors_light, anchors_heavy, edges_light, edges_heavy;
     int64_t n_anchors_light = 0, n_anchors_heavy = 0, n_edges_light = 0, n_edges_heavy = 0;
@@ -92,6 +94,12 @@ struct Graph {
     int32_t n_tables = 0;
     int32_t prepared_k = 0;             // 0: nothing, 3: C and tau, 4: C, tau and A
     int64_t last_launches = 0;
+    // per-kernel event timing (tg_set_timing)
+    bool timing = false;
+    struct TimerRec { const char *name; cudaEvent_t a, b; };
+    std::vector<TimerRec> timer_pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<std::pair<const char *, std::pair<double, int64_t>>> timer_totals;
     // CUDA graph of the last batched count
     cudaGraphExec_t batch_exec = nullptr;
     int32_t batch_k = 0;
@@ -106,6 +114,7 @@ struct Graph {
         v.rp = rp.as<int64_t>();
         v.adj = adj.as<int32_t>();
         v.toff = toff.as<int32_t>();
+        v.pivot = pivot.as<int32_t>();
         v.ty = ty.as<uint8_t>();
         v.slot_eid = slot_eid.as<int32_t>();
         v.e_lo = e_lo.as<int32_t>();
@@ -127,7 +136,7 @@ struct Graph {
         return c;
     }
     int64_t device_bytes() const {
-        const DBuf *all[] = {&node_off, &edge_off, &rp, &adj, &toff, &ty, &old_of, &slot_eid, &e_lo, &e_hi,
+        const DBuf *all[] = {&node_off, &edge_off, &rp, &adj, &toff, &pivot, &ty, &old_of, &slot_eid, &e_lo, &e_hi,
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &tscratch,
                              &stage_pe, &stage_gl};
@@ -137,6 +146,35 @@ struct Graph {
     }
     ~Graph() {
         if (batch_exec) cudaGraphExecDestroy(batch_exec);
+        for (auto &r : timer_pending) { event_pool.push_back(r.a); event_pool.push_back(r.b); }
+        for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+    }
+    cudaEvent_t take_event() {
+        if (!event_pool.empty()) { cudaEvent_t e = event_pool.back(); event_pool.pop_back(); return e; }
+        cudaEvent_t e;
+        TG_CK(cudaEventCreate(&e));
+        return e;
+    }
+};
+
+// Brackets one kernel launch with events when timing is on and the stream
+// is not being captured.
+struct KernelTimer {
+    Graph &G;
+    cudaStream_t s;
+    const char *name;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KernelTimer(Graph &g, cudaStream_t st, const char *nm) : G(g), s(st), name(nm) {
+        if (!G.timing) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        a = G.take_event();
+        b = G.take_event();
+        TG_CK(cudaEventRecord(a, s));
+    }
+    ~KernelTimer() {
+        if (!a) return;
+        if (cudaEventRecord(b, s) == cudaSuccess) G.timer_pending.push_back(Graph::TimerRec{name, a, b});
     }
 };
 

@@ -41,6 +41,7 @@ struct GraphView {
     const int64_t *rp;         // [n+1]
     const int32_t *adj;        // [nnz] internal ids, rows sorted by (type, id)
     const int32_t *toff;       // [n*(L+1)] type segment starts, relative to rp[x]
+    const int32_t *pivot;      // [n*L] first slot of segment (x,t) with id > x, relative to rp[x]
     const uint8_t *ty;         // [n] node type by internal id
     const int32_t *slot_eid;   // [nnz] edge id of each adjacency slot
     const int32_t *e_lo;       // [m] internal endpoint with the smaller id

@@ -63,6 +63,9 @@ SIGNATURES = {
     "tg_status_string": ([_i32], ctypes.c_char_p),
     "tg_last_launch_count": ([_vp], _i64),
     "tg_abi_version": ([], _i32),
+    "tg_set_timing": ([_vp, _i32], _i32),
+    "tg_get_timing": ([_vp, _i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], _i32),
 }
 
 
@@ -263,3 +266,17 @@ def tg_count_batch(g: Graph, k: int, per_edge_out=None, global_out=None, stream=
 
 def tg_query_status(g: Graph) -> int:
     return int(load().tg_query_status(g.handle))
+
+
+def tg_set_timing(g: Graph, on: bool = True) -> None:
+    _check(load().tg_set_timing(g.handle, 1 if on else 0), "tg_set_timing")
+
+
+def tg_get_timing(g: Graph, max_entries: int = 32) -> dict:
+    """{kernel name: (total ms, launches)} accumulated since the last call."""
+    names = (ctypes.c_char_p * max_entries)()
+    ms = (ctypes.c_double * max_entries)()
+    launches = (ctypes.c_int64 * max_entries)()
+    n = ctypes.c_int32(0)
+    _check(load().tg_get_timing(g.handle, max_entries, names, ms, launches, ctypes.byref(n)), "tg_get_timing")
+    return {names[i].decode(): (ms[i], int(launches[i])) for i in range(n.value)}
