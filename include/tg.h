@@ -234,6 +234,29 @@ tg_status tg_set_timing(tg_graph *g, int32_t on);
 tg_status tg_get_timing(tg_graph *g, int32_t max, const char **names, double *ms, int64_t *launches,
                         int32_t *n);
 
+/* Typed 3-node counts without any allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- services whose device memory is all owned by their own pool,
+ * code running while a CUDA graph is captured (plain cudaMalloc/cudaFree
+ * cannot be captured), loops that cannot afford cudaFree's implicit device
+ * synchronisation.  It computes what tg_count(k = 3) computes (per-edge rows
+ * of 2L uint32: typed 3-paths then typed triangles; global typed edge,
+ * 3-path and triangle totals, G(L, 3) int64) straight from a caller CSR, no
+ * tg_graph handle.  Arguments: device pointers only (TG_ERR_INVALID_ARG
+ * otherwise); rows must be sorted by neighbour id; per_edge_out,
+ * global_out and device_status may be NULL; device_status receives the
+ * device-detected error bits OR-ed in (non-zero: invalid graph or internal
+ * error), in stream order.
+ * Working memory: one file-scope device array of about 8 MB that every GPU
+ * which loads the library keeps until the process exits, shared by all
+ * calls; at most 1,048,576 nodes per call (TG_ERR_TOO_LARGE beyond).  The
+ * first call on a device looks up that array's device address (set-up); make
+ * it before any stream capture.  Calls that overlap on the GPU (other
+ * streams, other host threads) race on the shared array: serialise them. */
+tg_status tg_count3_static(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                           const uint8_t *node_types, int32_t L, uint32_t *per_edge_out, int64_t *global_out,
+                           uint32_t *device_status, void *stream);
+
 /* Library ABI version (TG_ABI_VERSION). */
 int32_t tg_abi_version(void);
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "tg_status_string": ([_i32], ctypes.c_char_p),
     "tg_last_launch_count": ([_vp], _i64),
     "tg_abi_version": ([], _i32),
+    "tg_count3_static": ([_i64, _i64, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
     "tg_set_timing": ([_vp, _i32], _i32),
     "tg_get_timing": ([_vp, _i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], _i32),
@@ -280,3 +281,13 @@ def tg_get_timing(g: Graph, max_entries: int = 32) -> dict:
     n = ctypes.c_int32(0)
     _check(load().tg_get_timing(g.handle, max_entries, names, ms, launches, ctypes.byref(n)), "tg_get_timing")
     return {names[i].decode(): (ms[i], int(launches[i])) for i in range(n.value)}
+
+
+def tg_count3_static(row_ptr, col, node_types, L: int, per_edge_out=None, global_out=None, device_status=None,
+                     stream=None) -> None:
+    """Allocation-free typed 3-node counts for callers that cannot call
+    cudaMalloc (see include/tg.h); device tensors only, rows sorted by id."""
+    n = int(row_ptr.shape[0]) - 1
+    nnz = int(col.shape[0])
+    _check(load().tg_count3_static(n, nnz, _ptr(row_ptr), _ptr(col), _ptr(node_types), L, _ptr(per_edge_out),
+                                   _ptr(global_out), _ptr(device_status), _stream(stream)), "tg_count3_static")
