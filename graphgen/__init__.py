@@ -33,7 +33,11 @@ def build(force: bool = False) -> str:
     """Compile graphgen.c into libgraphgen.so beside it (gcc, -O2)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:5] + ["-fopenmp"] + base[5:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -58,6 +62,8 @@ def _load():
             lib.gg_ego_network.restype = i64
             lib.gg_degree_proportional_node.argtypes = [i64, vp, u64]
             lib.gg_degree_proportional_node.restype = i32
+            lib.gg_ego_batch_sizes.argtypes = [i64, vp, vp, i64, i64, i64, i64, u64, vp, vp]
+            lib.gg_ego_batch_fill.argtypes = [i64, vp, vp, i64, i64, i64, i64, u64, i32, vp, vp, vp, vp, vp]
             lib.gg_unit_from_seed.argtypes = [u64]
             lib.gg_unit_from_seed.restype = dbl
             _lib = lib
@@ -191,3 +197,68 @@ def workload(name: str) -> dict:
         np.fill_diagonal(aff, 0.05)
         return sbm([500_000, 300_000, 150_000, 50_000], aff, 30_000_000, SEED_BASE + 3)
     raise KeyError(name)
+
+
+def ego_parent(seed: int = SEED_BASE + 4) -> dict:
+    """Parent graph of the batched workload: Chung-Lu n=4e6, average degree 20
+    (m = 4e7), gamma = 2.3, max weight 2e4, L = 6 uniform types."""
+    return chung_lu(4_000_000, 40_000_000, 2.3, 2.0e4, 6, seed)
+
+
+def ego_batch(count: int = 8192, seed: int = SEED_BASE + 4, parent: dict | None = None,
+              m_min: int = 100, m_max: int = 400_000, n_max: int = 20_000, L: int = 6) -> dict:
+    """The batched workload as one block-diagonal union (dict with node_off).
+
+    Graph g (seed + g): u ~ U(0,1), edge target round(m_min (m_max/m_min)^u)
+    (log-uniform), seed node drawn in proportion to degree, breadth-first
+    ball grown node by node until the induced subgraph reaches the edge
+    target or n_max nodes; L uniform types."""
+    lib = _load()
+    parent = parent if parent is not None else ego_parent(seed)
+    rp, col = parent["row_ptr"], parent["col"]
+    n_out = np.zeros(count, dtype=np.int64)
+    m_out = np.zeros(count, dtype=np.int64)
+    _check(lib.gg_ego_batch_sizes(parent["n"], _p(rp), _p(col), count, m_min, m_max, n_max, seed, _p(n_out),
+                                  _p(m_out)), "ego_batch_sizes")
+    node_off = np.concatenate([[0], np.cumsum(n_out)]).astype(np.int64)
+    nnz_off = np.concatenate([[0], np.cumsum(2 * m_out)]).astype(np.int64)
+    n, nnz = int(node_off[-1]), int(nnz_off[-1])
+    u_rp = np.empty(n + 1, dtype=np.int64)
+    u_col = np.empty(nnz, dtype=np.int32)
+    u_ty = np.empty(n, dtype=np.uint8)
+    _check(lib.gg_ego_batch_fill(parent["n"], _p(rp), _p(col), count, m_min, m_max, n_max, seed, L, _p(node_off),
+                                 _p(nnz_off), _p(u_rp), _p(u_col), _p(u_ty)), "ego_batch_fill")
+    u_rp[n] = nnz
+    return {"n": n, "m": nnz // 2, "L": L, "row_ptr": u_rp, "col": u_col, "types": u_ty, "node_off": node_off,
+            "graph_m": m_out, "graph_n": n_out, "name": f"ego batch of {count} (seed {seed})"}
+
+
+def split(union: dict, g: int) -> dict:
+    """Graph g of a union as a standalone graph (ids relative to its first node)."""
+    a, b = int(union["node_off"][g]), int(union["node_off"][g + 1])
+    rp = union["row_ptr"][a:b + 1] - union["row_ptr"][a]
+    col = union["col"][int(union["row_ptr"][a]):int(union["row_ptr"][b])] - a
+    return {"n": b - a, "m": int(rp[-1]) // 2, "L": union["L"], "row_ptr": rp.astype(np.int64),
+            "col": col.astype(np.int32), "types": union["types"][a:b].copy(), "name": f"graph {g}"}
+
+
+def concat(graphs: list) -> dict:
+    """Block-diagonal union of graphs with the same L: node_off marks each graph."""
+    node_off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        node_off[k + 1] = node_off[k] + g["n"]
+    nnz = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        nnz[k + 1] = nnz[k] + int(g["row_ptr"][-1])
+    rp = np.empty(int(node_off[-1]) + 1, dtype=np.int64)
+    col = np.empty(int(nnz[-1]), dtype=np.int32)
+    ty = np.empty(int(node_off[-1]), dtype=np.uint8)
+    for k, g in enumerate(graphs):
+        a, b = int(node_off[k]), int(node_off[k + 1])
+        rp[a:b] = g["row_ptr"][:-1] + nnz[k]
+        col[nnz[k]:nnz[k + 1]] = g["col"] + a
+        ty[a:b] = g["types"]
+    rp[-1] = nnz[-1]
+    L = graphs[0]["L"] if graphs else 1
+    return {"n": int(node_off[-1]), "m": int(nnz[-1]) // 2, "L": L, "row_ptr": rp, "col": col, "types": ty,
+            "node_off": node_off, "name": f"union of {len(graphs)} graphs"}

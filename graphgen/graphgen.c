@@ -28,6 +28,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------ RNG */
 
@@ -418,3 +421,107 @@ int32_t gg_degree_proportional_node(int64_t n, const int64_t *row_ptr, uint64_t 
 
 /* uniform double in [0,1) from a seed (for callers that need one draw) */
 double gg_unit_from_seed(uint64_t seed) { gg_rng r; rng_seed(&r, seed); return rng_unit(&r); }
+
+/* ------------------------------------------------------- ego-network batch */
+
+/* Ego network g of a parent CSR with an edge target: a breadth-first ball
+ * around `seed_node` (neighbours in CSR order) grows one node at a time until
+ * the induced subgraph holds at least m_target edges or n_max nodes.  Writes
+ * the ball's parent ids in visit order to nodes[] (capacity n_max) and
+ * returns the node count; *m_out receives the induced edge count.  `mark`
+ * (n_parent int32, all -1) is restored before return. */
+static int64_t ego_ball(const int64_t *rp, const int32_t *col, int32_t seed_node, int64_t m_target, int64_t n_max,
+                        int32_t *mark, int32_t *nodes, int64_t *m_out) {
+    int64_t nn = 0, head = 0, me = 0;
+    nodes[nn] = seed_node; mark[seed_node] = (int32_t)nn; ++nn;
+    while (head < nn && nn < n_max && me < m_target) {
+        int32_t v = nodes[head++];
+        for (int64_t k = rp[v]; k < rp[v + 1] && nn < n_max && me < m_target; ++k) {
+            int32_t w = col[k];
+            if (mark[w] >= 0) continue;
+            int64_t add = 0;                           /* edges from w into the ball */
+            for (int64_t q = rp[w]; q < rp[w + 1]; ++q) add += mark[col[q]] >= 0;
+            mark[w] = (int32_t)nn; nodes[nn++] = w; me += add;
+        }
+    }
+    *m_out = me;
+    return nn;
+}
+
+/* Sizes pass of a batch: for graph g (seed seed + g), u ~ U(0,1), edge target
+ * round(m_min * (m_max/m_min)^u), seed node drawn in proportion to degree.
+ * n_out[g], m_out[g] receive the ball's sizes.  OpenMP over graphs. */
+int gg_ego_batch_sizes(int64_t n_parent, const int64_t *rp, const int32_t *col, int64_t count, int64_t m_min,
+                       int64_t m_max, int64_t n_max, uint64_t seed, int64_t *n_out, int64_t *m_out) {
+    int bad = 0;
+#pragma omp parallel reduction(|:bad)
+    {
+        int32_t *mark = (int32_t *)malloc((size_t)n_parent * sizeof(int32_t));
+        int32_t *nodes = (int32_t *)malloc((size_t)n_max * sizeof(int32_t));
+        if (!mark || !nodes) bad = 1;
+        else {
+            for (int64_t v = 0; v < n_parent; ++v) mark[v] = -1;
+#pragma omp for schedule(dynamic, 4)
+            for (int64_t g = 0; g < count; ++g) {
+                uint64_t s = seed + (uint64_t)g;
+                double u = gg_unit_from_seed(s);
+                int64_t mt = (int64_t)llround((double)m_min * pow((double)m_max / (double)m_min, u));
+                int32_t sn = gg_degree_proportional_node(n_parent, rp, s ^ 0x5EEDull);
+                int64_t me = 0;
+                int64_t nn = ego_ball(rp, col, sn, mt, n_max, mark, nodes, &me);
+                for (int64_t q = 0; q < nn; ++q) mark[nodes[q]] = -1;
+                n_out[g] = nn; m_out[g] = me;
+            }
+        }
+        free(mark); free(nodes);
+    }
+    return bad ? -2 : 0;
+}
+
+/* Fill pass: the union CSR of the batch.  node_off[g] / nnz_off[g] are the
+ * prefix sums of n_out and 2*m_out.  Graph g's nodes are numbered
+ * node_off[g] + visit order; rows are sorted by neighbour id; types uniform
+ * over L from seed + g.  OpenMP over graphs. */
+int gg_ego_batch_fill(int64_t n_parent, const int64_t *rp, const int32_t *col, int64_t count, int64_t m_min,
+                      int64_t m_max, int64_t n_max, uint64_t seed, int32_t L, const int64_t *node_off,
+                      const int64_t *nnz_off, int64_t *u_rp, int32_t *u_col, uint8_t *u_ty) {
+    int bad = 0;
+#pragma omp parallel reduction(|:bad)
+    {
+        int32_t *mark = (int32_t *)malloc((size_t)n_parent * sizeof(int32_t));
+        int32_t *nodes = (int32_t *)malloc((size_t)n_max * sizeof(int32_t));
+        if (!mark || !nodes) bad = 1;
+        else {
+            for (int64_t v = 0; v < n_parent; ++v) mark[v] = -1;
+#pragma omp for schedule(dynamic, 4)
+            for (int64_t g = 0; g < count; ++g) {
+                uint64_t s = seed + (uint64_t)g;
+                double u = gg_unit_from_seed(s);
+                int64_t mt = (int64_t)llround((double)m_min * pow((double)m_max / (double)m_min, u));
+                int32_t sn = gg_degree_proportional_node(n_parent, rp, s ^ 0x5EEDull);
+                int64_t me = 0;
+                int64_t nn = ego_ball(rp, col, sn, mt, n_max, mark, nodes, &me);
+                if (nn != node_off[g + 1] - node_off[g] || 2 * me != nnz_off[g + 1] - nnz_off[g]) { bad = 1; }
+                else {
+                    /* rows: local ids in visit order, neighbours inside the ball */
+                    int64_t pos = nnz_off[g];
+                    for (int64_t a = 0; a < nn; ++a) {
+                        int32_t v = nodes[a];
+                        u_rp[node_off[g] + a] = pos;
+                        int64_t b0 = pos;
+                        for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+                            int32_t b = mark[col[k]];
+                            if (b >= 0) u_col[pos++] = (int32_t)(node_off[g] + b);
+                        }
+                        qsort(u_col + b0, (size_t)(pos - b0), sizeof(int32_t), cmp_i32);
+                    }
+                    gg_rng r; rng_seed(&r, s ^ 0x7E57ull);
+                    for (int64_t a = 0; a < nn; ++a) u_ty[node_off[g] + a] = (uint8_t)rng_below(&r, (uint64_t)L);
+                }
+                for (int64_t q = 0; q < nn; ++q) mark[nodes[q]] = -1;
+            }
+        }
+        free(mark); free(nodes);
+    }
+    return bad ? -2 : 0;
+}

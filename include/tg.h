@@ -118,7 +118,9 @@ typedef struct {
     int32_t light_anchor_max_wedges;  /* wedge anchors with at most this many wedges: warp per anchor */
     int32_t anchor_table_budget_mb;   /* device memory for per-CTA wedge tables */
     int32_t ctas_per_sm;              /* resident CTAs per SM for the per-edge kernels */
-    int32_t reserved[4];
+    int32_t cycle_budget_mb;          /* device memory for the per-slot 4-cycle array; a batch whose
+                                         array would exceed it is counted in chunks of whole graphs */
+    int32_t reserved[3];
 } tg_options;
 
 /* ---- layout ---------------------------------------------------------- */

@@ -60,6 +60,7 @@ void build_common(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t n
         if (opt->light_anchor_max_wedges > 0) o.light_anchor_max_wedges = opt->light_anchor_max_wedges;
         if (opt->anchor_table_budget_mb > 0) o.anchor_table_budget_mb = opt->anchor_table_budget_mb;
         if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
+        if (opt->cycle_budget_mb > 0) o.cycle_budget_mb = opt->cycle_budget_mb;
     }
     o.light_edge_max_degree = std::min(o.light_edge_max_degree, 256);     // warp T list capacity
     o.light_anchor_max_wedges = std::min(o.light_anchor_max_wedges, 2048);
@@ -189,8 +190,7 @@ tg_status tg_count(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_t *glo
         uint32_t *pe = device_out(per_edge_out, pe_bytes, G.stage_pe, pe_staged);
         int64_t *gl = device_out(global_out, gl_bytes, G.stage_gl, gl_staged);
         TG_CK(cudaMemsetAsync(G.gacc.p, 0, (size_t)G.ngraphs * tg::global_slots(G.L, 4) * sizeof(unsigned long long), s));
-        int64_t launches = tg::launch_prepare(G, k, s);
-        launches += tg::launch_edges(G, k, 0, G.m, pe, G.gacc.as<unsigned long long>(), s);
+        int64_t launches = tg::run_count(G, k, 0, G.m, pe, G.gacc.as<unsigned long long>(), true, s);
         if (gl) launches += tg::launch_finalize(G, k, gl, s);
         if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
         if (gl_staged) TG_CK(cudaMemcpyAsync(global_out, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
@@ -210,7 +210,6 @@ tg_status tg_count_range(tg_graph *gh, int32_t k, int64_t e_begin, int64_t e_end
         tg::prepare_counting(G, k, s);
         tg::prepare_edges(G, k, s);
         int64_t launches = 0;
-        if (!(G.prepared_k == k || (G.prepared_k == 4 && k == 3))) launches += tg::launch_prepare(G, k, s);
         const size_t pe_bytes = (size_t)(e_end - e_begin) * tg::per_edge_slots(G.L, k) * sizeof(uint32_t);
         const size_t gl_bytes = (size_t)G.ngraphs * tg::global_slots(G.L, k) * sizeof(int64_t);
         bool pe_staged = false, gl_staged = false;
@@ -224,7 +223,7 @@ tg_status tg_count_range(tg_graph *gh, int32_t k, int64_t e_begin, int64_t e_end
             TG_CK(cudaMemsetAsync(scratch.p, 0, gl_bytes, s));
             acc = scratch.as<unsigned long long>();
         }
-        launches += tg::launch_edges(G, k, e_begin, e_end, pe, acc, s);
+        launches += tg::run_count(G, k, e_begin, e_end, pe, acc, false, s);
         if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
         if (gl_staged) TG_CK(cudaMemcpyAsync(global_accum, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
         if (pe_staged || gl_staged || scratch.p) TG_CK(cudaStreamSynchronize(s));
@@ -273,8 +272,7 @@ tg_status tg_count_batch(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_
             int64_t launches = 0;
             try {
                 TG_CK(cudaMemsetAsync(G.gacc.p, 0, (size_t)G.ngraphs * tg::global_slots(G.L, 4) * sizeof(unsigned long long), s));
-                launches += tg::launch_prepare(G, k, s);
-                launches += tg::launch_edges(G, k, 0, G.m, per_edge_out, G.gacc.as<unsigned long long>(), s);
+                launches += tg::run_count(G, k, 0, G.m, per_edge_out, G.gacc.as<unsigned long long>(), true, s);
                 if (global_out) launches += tg::launch_finalize(G, k, global_out, s);
             } catch (...) {
                 cudaStreamEndCapture(s, &graph);

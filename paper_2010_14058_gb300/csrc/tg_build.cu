@@ -513,6 +513,8 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         // each graph holds half of its rows' entries
         for (int g = 0; g < ngraphs; ++g)
             G.h_edge_off[g + 1] = G.h_edge_off[g] + (h_rp[G.h_node_off[g + 1]] - h_rp[G.h_node_off[g]]) / 2;
+        G.h_slot_off.assign(ngraphs + 1, 0);
+        for (int g = 0; g <= ngraphs; ++g) G.h_slot_off[g] = h_rp[G.h_node_off[g]];
         G.max_degree = 0;
         for (int64_t v = 0; v < n; ++v) G.max_degree = std::max(G.max_degree, h_rp[v + 1] - h_rp[v]);
         if (G.h_edge_off[ngraphs] != m) throw Error{TG_ERR_INVALID_GRAPH, "edge count per graph"};

@@ -208,7 +208,8 @@ __device__ int hash_find(const int32_t *keys, int cap, int32_t w) {
 // Light anchors (few wedges): one warp per anchor, table in shared memory.
 __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphView g, CountView cv,
                                                                         const int32_t *__restrict__ anchors,
-                                                                        int64_t n_anchors, int cap) {
+                                                                        int64_t n_anchors, int cap, int64_t n0,
+                                                                        int64_t n1) {
     extern __shared__ int32_t smem[];
     const int L = g.L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -218,9 +219,11 @@ __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphVie
     for (int k = lane; k < cap * L; k += 32) cnt[k] = 0;
     __syncwarp();
     const int64_t nw = (int64_t)gridDim.x * kLightAnchorWarps;
-    const int64_t nnz = g.nnz;
+    const int64_t nnz = cv.a_stride;
+    uint32_t *A = cv.A - cv.a_base;                          // indexed by absolute slot
     for (int64_t a = (int64_t)blockIdx.x * kLightAnchorWarps + wid; a < n_anchors; a += nw) {
         const int32_t u = anchors[a];
+        if (u < n0 || u >= n1) continue;                    // anchor outside this chunk
         const int tu = g.ty[u];
         // phase 1
         for (int tv = 0; tv < L; ++tv) {
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphVie
                             if (t >= L) break;
                             unsigned c = cnt[h * L + t] - (t == tv ? 1u : 0u);
                             if (c) {
-                                atomicAdd(&cv.A[(int64_t)(tu * L + t) * nnz + k], c);
+                                atomicAdd(&A[(int64_t)(tu * L + t) * nnz + k], c);
                                 acc[t] += c;
                             }
                         }
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphVie
                     for (int t = 0; t < kMaxL; ++t) {
                         if (t >= L) break;
                         unsigned r = warp_sum_u32(acc[t]);
-                        if (lane == 0 && r) atomicAdd(&cv.A[(int64_t)(t * L + tw) * nnz + sv], r);
+                        if (lane == 0 && r) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + sv], r);
                     }
                 }
             }
@@ -285,14 +288,16 @@ __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphVie
 // indexed by (w - first node of u's graph).  Warps take the v in V_u.
 __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, CountView cv,
                                                                const int32_t *__restrict__ anchors,
-                                                               int64_t n_anchors) {
+                                                               int64_t n_anchors, int64_t n0, int64_t n1) {
     __shared__ int64_t s_b[kMaxL + 1], s_cnt[kMaxL + 1];
     const int L = g.L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     uint32_t *tbl = cv.tables + (int64_t)blockIdx.x * cv.table_stride;
-    const int64_t nnz = g.nnz;
+    const int64_t nnz = cv.a_stride;
+    uint32_t *A = cv.A - cv.a_base;                          // indexed by absolute slot
     for (int64_t a = blockIdx.x; a < n_anchors; a += gridDim.x) {
         const int32_t u = anchors[a];
+        if (u < n0 || u >= n1) continue;                    // anchor outside this chunk (uniform per CTA)
         const int tu = g.ty[u];
         const int64_t base = g.node_off[graph_of_node(g, u)];
         if (threadIdx.x == 0) {
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
                                 if (t >= L) break;
                                 unsigned c = h[t] - (t == tv ? 1u : 0u);
                                 if (c) {
-                                    atomicAdd(&cv.A[(int64_t)(tu * L + t) * nnz + k], c);
+                                    atomicAdd(&A[(int64_t)(tu * L + t) * nnz + k], c);
                                     acc[t] += c;
                                 }
                             }
@@ -340,7 +345,7 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
                         for (int t = 0; t < kMaxL; ++t) {
                             if (t >= L) break;
                             unsigned r = warp_sum_u32(acc[t]);
-                            if (lane == 0 && r) atomicAdd(&cv.A[(int64_t)(t * L + tw) * nnz + sv], r);
+                            if (lane == 0 && r) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + sv], r);
                         }
                     } else {
                         for (int64_t k = vb + lane; k < vcut; k += 32) {
@@ -750,7 +755,8 @@ __device__ void edge_epilogue(const GraphView &g, const CountView &cv, int64_t e
         const int z = x * kMaxL + y;
         // P[x][y]: 3-paths j - w - r - i with phi_w = x, phi_r = y (slot i->j holds
         // [type next to i][type next to j], slot j->i the reverse)
-        ws.Pm[z] = (int64_t)cv.A[(int64_t)(y * L + x) * g.nnz + slot_ij] + (int64_t)cv.A[(int64_t)(x * L + y) * g.nnz + slot_ji];
+        const uint32_t *A = cv.A - cv.a_base;
+        ws.Pm[z] = (int64_t)A[(int64_t)(y * L + x) * cv.a_stride + slot_ij] + (int64_t)A[(int64_t)(x * L + y) * cv.a_stride + slot_ji];
         ws.taui[z] = tau_i[k];
         ws.tauj[z] = tau_j[k];
         ws.deli[z] = del_i[k];
@@ -860,8 +866,9 @@ __global__ void __launch_bounds__(kEdgeThreads, 4) k_edge4_light(GraphView g, Co
 // T lives in shared memory when it fits, else in this CTA's global slice.
 __global__ void __launch_bounds__(kHeavyThreads, 2) k_edge4_heavy(GraphView g, CountView cv, const int32_t *__restrict__ list,
                                                               int64_t n_list, int64_t e_begin, int64_t e_end,
-                                                              uint32_t *per_edge_out, unsigned long long *gacc,
-                                                              int32_t *tscratch, int64_t tscratch_stride) {
+                                                              int64_t row_base, uint32_t *per_edge_out,
+                                                              unsigned long long *gacc, int32_t *tscratch,
+                                                              int64_t tscratch_stride) {
     extern __shared__ unsigned long long dsm[];
     const int L = g.L;
     const int G = (int)global_slots(L, 4);
@@ -890,7 +897,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 2) k_edge4_heavy(GraphView g, C
         __syncthreads();
         enumerate_T(g, cv, e, i, j, ws, tl, cap, blockDim.x, threadIdx.x, bbar);
         count_K(g, ws, tl, blockDim.x, threadIdx.x, bbar);
-        uint32_t *row = per_edge_out ? per_edge_out + (e - e_begin) * S : nullptr;
+        uint32_t *row = per_edge_out ? per_edge_out + (e - row_base) * S : nullptr;
         edge_epilogue(g, cv, e, i, j, ws, row, hist, blockDim.x, threadIdx.x, bbar);
     }
     __syncthreads();
@@ -968,6 +975,44 @@ int grid_for(int64_t items, int per_block, int cap) {
 
 }  // namespace
 
+static std::vector<Tile> make_tiles(const Graph &G, int64_t e_begin, int64_t e_end) {
+    std::vector<Tile> tiles;
+    for (int gi = 0; gi < G.ngraphs; ++gi) {
+        int64_t b = std::max(e_begin, G.h_edge_off[gi]), e = std::min(e_end, G.h_edge_off[gi + 1]);
+        for (int64_t x = b; x < e; x += kTile) tiles.push_back(Tile{x, std::min(e, x + kTile), gi, 0});
+    }
+    return tiles;
+}
+
+// Splits the graphs into consecutive chunks whose adjacency slots fit the
+// 4-cycle array budget (a single graph larger than the budget is a chunk of
+// its own), and sizes the array for the largest chunk.
+static void plan_chunks(Graph &G) {
+    G.chunks.clear();
+    const int64_t per_slot = (int64_t)G.L * G.L * (int64_t)sizeof(uint32_t);
+    const int64_t max_slots = std::max<int64_t>(((int64_t)G.opt.cycle_budget_mb << 20) / per_slot, 1);
+    // tile index ranges follow graph boundaries (make_tiles emits graph after graph)
+    std::vector<int64_t> tile_off(G.ngraphs + 1, 0);
+    for (int gi = 0; gi < G.ngraphs; ++gi)
+        tile_off[gi + 1] = tile_off[gi] + (G.h_edge_off[gi + 1] - G.h_edge_off[gi] + kTile - 1) / kTile;
+    int g0 = 0;
+    int64_t widest = 0;
+    while (g0 < G.ngraphs) {
+        int g1 = g0 + 1;
+        while (g1 < G.ngraphs && G.h_slot_off[g1 + 1] - G.h_slot_off[g0] <= max_slots) ++g1;
+        Graph::Chunk c;
+        c.g0 = g0; c.g1 = g1;
+        c.n0 = G.h_node_off[g0]; c.n1 = G.h_node_off[g1];
+        c.s0 = G.h_slot_off[g0]; c.s1 = G.h_slot_off[g1];
+        c.e0 = G.h_edge_off[g0]; c.e1 = G.h_edge_off[g1];
+        c.t0 = tile_off[g0]; c.t1 = tile_off[g1];
+        widest = std::max(widest, c.s1 - c.s0);
+        G.chunks.push_back(c);
+        g0 = g1;
+    }
+    G.a_stride = std::max<int64_t>(widest, 1);
+}
+
 // Allocates the working arrays of a count with this k (kept by the handle).
 void prepare_counting(Graph &G, int k, cudaStream_t s) {
     const int L = G.L;
@@ -977,7 +1022,8 @@ void prepare_counting(Graph &G, int k, cudaStream_t s) {
     const size_t gbytes = (size_t)G.ngraphs * global_slots(L, 4) * sizeof(unsigned long long);
     if (G.gacc.bytes < gbytes) G.gacc.alloc(gbytes);
     if (k == 4) {
-        const size_t ab = (size_t)std::max<int64_t>(G.nnz, 1) * L * L * sizeof(uint32_t);
+        if (G.chunks.empty()) plan_chunks(G);
+        const size_t ab = (size_t)G.a_stride * L * L * sizeof(uint32_t);
         if (G.A.bytes < ab) G.A.alloc(ab);
         if (G.n_anchors_heavy > 0 && G.n_tables == 0) {
             const int64_t stride = std::max<int64_t>(G.max_graph_nodes, 1) * L;
@@ -990,55 +1036,13 @@ void prepare_counting(Graph &G, int k, cudaStream_t s) {
             G.n_tables = (int32_t)nt;
         }
     }
-    (void)s;
 }
 
-// typed triangles, tau, and (k = 4) the wedge pass: whole graph
-int64_t launch_prepare(Graph &G, int k, cudaStream_t s) {
-    const GraphView gv = G.view();
-    const CountView cv = G.cview();
-    const int sms = sm_count();
-    int64_t launches = 0;
-    if (G.m > 0) {
-        KernelTimer kt(G, s, "k_tri");
-        k_tri<<<grid_for(G.m, 8, sms * 16), 256, 0, s>>>(gv, cv);
-        ++launches;
-    }
-    if (G.n > 0) {
-        KernelTimer kt(G, s, "k_tau");
-        k_tau<<<grid_for(G.n, 8, sms * 16), 256, 0, s>>>(gv, cv);
-        ++launches;
-    }
-    if (k == 4) {
-        TG_CK(cudaMemsetAsync(G.A.p, 0, (size_t)std::max<int64_t>(G.nnz, 1) * G.L * G.L * sizeof(uint32_t), s));
-        if (G.n_anchors_light > 0) {
-            int cap = 1;
-            while (cap < 2 * G.opt.light_anchor_max_wedges) cap <<= 1;
-            const size_t smem = (size_t)kLightAnchorWarps * cap * (1 + G.L) * sizeof(int32_t);
-            KernelTimer kt(G, s, "k_wedge_light");
-            k_wedge_light<<<grid_for(G.n_anchors_light, kLightAnchorWarps, sms * 8), kLightAnchorWarps * 32, smem, s>>>(
-                gv, cv, G.anchors_light.as<int32_t>(), G.n_anchors_light, cap);
-            ++launches;
-        }
-        if (G.n_anchors_heavy > 0) {
-            KernelTimer kt(G, s, "k_wedge_heavy");
-            k_wedge_heavy<<<G.n_tables, kAnchorThreads, 0, s>>>(gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy);
-            ++launches;
-        }
-    }
-    TG_CK(cudaGetLastError());
-    G.prepared_k = k;
-    return launches;
+static size_t hist_bytes(int L, int k) { return (size_t)((global_slots(L, k) + 1) & ~1) * sizeof(unsigned long long); }
+static size_t light_smem(int L) {
+    return hist_bytes(L, 4) + (kEdgeThreads / 32) * (sizeof(EdgeWs) + kTCapWarp * sizeof(int32_t));
 }
-
-static std::vector<Tile> make_tiles(const Graph &G, int64_t e_begin, int64_t e_end) {
-    std::vector<Tile> tiles;
-    for (int gi = 0; gi < G.ngraphs; ++gi) {
-        int64_t b = std::max(e_begin, G.h_edge_off[gi]), e = std::min(e_end, G.h_edge_off[gi + 1]);
-        for (int64_t x = b; x < e; x += kTile) tiles.push_back(Tile{x, std::min(e, x + kTile), gi, 0});
-    }
-    return tiles;
-}
+static size_t heavy_smem(int L) { return hist_bytes(L, 4) + sizeof(EdgeWs) + kTCapSmemHeavy * sizeof(int32_t); }
 
 // Device tile list of [e_begin, e_end); the full range is cached by the
 // handle (so that a captured CUDA graph never copies from host memory).
@@ -1062,12 +1066,6 @@ static const Tile *tiles_for(Graph &G, int64_t e_begin, int64_t e_end, int64_t &
 
 // Allocations and kernel attributes of the per-edge stage (done before any
 // capture).
-static size_t hist_bytes(int L, int k) { return (size_t)((global_slots(L, k) + 1) & ~1) * sizeof(unsigned long long); }
-static size_t light_smem(int L) {
-    return hist_bytes(L, 4) + (kEdgeThreads / 32) * (sizeof(EdgeWs) + kTCapWarp * sizeof(int32_t));
-}
-static size_t heavy_smem(int L) { return hist_bytes(L, 4) + sizeof(EdgeWs) + kTCapSmemHeavy * sizeof(int32_t); }
-
 void prepare_edges(Graph &G, int k, cudaStream_t s) {
     TG_CK(cudaFuncSetAttribute(k_edge3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes(G.L, 3)));
     TG_CK(cudaFuncSetAttribute(k_edge4_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)light_smem(G.L)));
@@ -1090,38 +1088,130 @@ void prepare_edges(Graph &G, int k, cudaStream_t s) {
     }
 }
 
-// per-edge stage over [e_begin, e_end): rows and raw global sums into gacc
-int64_t launch_edges(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out,
-                     unsigned long long *gacc, cudaStream_t s) {
+// typed triangles per edge and per-node typed triangle sums: whole graph
+static int64_t launch_triangles(Graph &G, cudaStream_t s) {
     const GraphView gv = G.view();
     const CountView cv = G.cview();
     const int sms = sm_count();
     int64_t launches = 0;
-    DBuf tmp;
-    int64_t n_tiles = 0;
-    const Tile *tiles = tiles_for(G, e_begin, e_end, n_tiles, tmp, s);
-    if (n_tiles == 0) return 0;
+    if (G.m > 0) {
+        KernelTimer kt(G, s, "k_tri");
+        k_tri<<<grid_for(G.m, 8, sms * 16), 256, 0, s>>>(gv, cv);
+        ++launches;
+    }
+    if (G.n > 0) {
+        KernelTimer kt(G, s, "k_tau");
+        k_tau<<<grid_for(G.n, 8, sms * 16), 256, 0, s>>>(gv, cv);
+        ++launches;
+    }
+    TG_CK(cudaGetLastError());
+    return launches;
+}
+
+// degree-priority wedges of the anchors of one chunk into A
+static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
+    G.a_base = c.s0;
+    const GraphView gv = G.view();
+    const CountView cv = G.cview();
+    const int sms = sm_count();
+    int64_t launches = 0;
+    const int L = G.L;
+    if (c.s1 > c.s0)
+        TG_CK(cudaMemset2DAsync(G.A.p, (size_t)G.a_stride * sizeof(uint32_t), 0, (size_t)(c.s1 - c.s0) * sizeof(uint32_t),
+                                (size_t)L * L, s));
+    if (G.n_anchors_light > 0) {
+        int cap = 1;
+        while (cap < 2 * G.opt.light_anchor_max_wedges) cap <<= 1;
+        const size_t smem = (size_t)kLightAnchorWarps * cap * (1 + L) * sizeof(int32_t);
+        KernelTimer kt(G, s, "k_wedge_light");
+        k_wedge_light<<<grid_for(G.n_anchors_light, kLightAnchorWarps, sms * 8), kLightAnchorWarps * 32, smem, s>>>(
+            gv, cv, G.anchors_light.as<int32_t>(), G.n_anchors_light, cap, c.n0, c.n1);
+        ++launches;
+    }
+    if (G.n_anchors_heavy > 0) {
+        KernelTimer kt(G, s, "k_wedge_heavy");
+        k_wedge_heavy<<<G.n_tables, kAnchorThreads, 0, s>>>(gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy,
+                                                             c.n0, c.n1);
+        ++launches;
+    }
+    TG_CK(cudaGetLastError());
+    return launches;
+}
+
+// per-edge stage of edges [e_begin, e_end) given as tiles (inside one chunk for k = 4)
+static int64_t launch_edge_tiles(Graph &G, int k, const Tile *tiles, int64_t n_tiles, int64_t e_begin, int64_t e_end,
+                                 int64_t row_base, uint32_t *per_edge_out, unsigned long long *gacc, cudaStream_t s) {
+    if (n_tiles <= 0) return 0;
+    const GraphView gv = G.view();
+    const CountView cv = G.cview();
+    const int sms = sm_count();
+    int64_t launches = 0;
     if (k == 3) {
         KernelTimer kt(G, s, "k_edge3");
-        k_edge3<<<grid_for(n_tiles, 1, sms * 8), 256, hist_bytes(G.L, 3), s>>>(gv, cv, tiles, n_tiles, e_begin, per_edge_out, gacc);
+        k_edge3<<<grid_for(n_tiles, 1, sms * 8), 256, hist_bytes(G.L, 3), s>>>(gv, cv, tiles, n_tiles, row_base,
+                                                                                per_edge_out, gacc);
         ++launches;
     } else {
         {
-        KernelTimer kt(G, s, "k_edge4_light");
-        k_edge4_light<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), kEdgeThreads, light_smem(G.L), s>>>(
-            gv, cv, tiles, n_tiles, G.opt.light_edge_max_degree, e_begin, per_edge_out, gacc);
-        ++launches;
+            KernelTimer kt(G, s, "k_edge4_light");
+            k_edge4_light<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), kEdgeThreads, light_smem(G.L), s>>>(
+                gv, cv, tiles, n_tiles, G.opt.light_edge_max_degree, row_base, per_edge_out, gacc);
+            ++launches;
         }
         if (G.n_edges_heavy > 0) {
             KernelTimer kt(G, s, "k_edge4_heavy");
             k_edge4_heavy<<<G.tscratch_blocks, kHeavyThreads, heavy_smem(G.L), s>>>(
-                gv, cv, G.edges_heavy.as<int32_t>(), G.n_edges_heavy, e_begin, e_end, per_edge_out, gacc,
+                gv, cv, G.edges_heavy.as<int32_t>(), G.n_edges_heavy, e_begin, e_end, row_base, per_edge_out, gacc,
                 G.tscratch.as<int32_t>(), G.tscratch_stride);
             ++launches;
         }
     }
     TG_CK(cudaGetLastError());
-    if (tmp.p) TG_CK(cudaStreamSynchronize(s));   // tmp tiles freed on return
+    return launches;
+}
+
+int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out, unsigned long long *gacc,
+                  bool full, cudaStream_t s) {
+    int64_t launches = 0;
+    if (full || G.prepared_k < 3) {
+        launches += launch_triangles(G, s);
+        G.prepared_k = 3;
+    }
+    DBuf tmp;
+    int64_t n_tiles = 0;
+    const Tile *tiles = tiles_for(G, e_begin, e_end, n_tiles, tmp, s);
+    if (k == 3) {
+        launches += launch_edge_tiles(G, 3, tiles, n_tiles, e_begin, e_end, e_begin, per_edge_out, gacc, s);
+    } else {
+        const bool whole = e_begin == 0 && e_end == G.m;
+        for (const Graph::Chunk &c : G.chunks) {
+            const int64_t b = std::max(e_begin, c.e0), e = std::min(e_end, c.e1);
+            if (b >= e) continue;
+            // the wedge pass of a single-chunk handle is reused by later range calls
+            if (full || G.chunks.size() > 1 || G.prepared_k != 4) {
+                launches += launch_wedges(G, c, s);
+                if (G.chunks.size() == 1) G.prepared_k = 4;
+            }
+            G.a_base = c.s0;
+            const Tile *ct = tiles;
+            int64_t nct = n_tiles;
+            if (whole) {
+                ct = tiles + c.t0;
+                nct = c.t1 - c.t0;
+            } else {
+                // tiles of an arbitrary range: the kernel skips none; pick this chunk's part
+                int64_t a = 0, z = n_tiles;
+                std::vector<Tile> host = make_tiles(G, e_begin, e_end);
+                while (a < z && host[a].end <= b) ++a;
+                int64_t y = a;
+                while (y < z && host[y].begin < e) ++y;
+                ct = tiles + a;
+                nct = y - a;
+            }
+            launches += launch_edge_tiles(G, 4, ct, nct, b, e, e_begin, per_edge_out, gacc, s);
+        }
+    }
+    if (tmp.p) TG_CK(cudaStreamSynchronize(s));
     return launches;
 }
 

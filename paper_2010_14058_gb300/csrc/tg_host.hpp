@@ -78,7 +78,11 @@ struct Graph {
     int64_t n = 0, nnz = 0, m = 0;
     int64_t max_graph_nodes = 0;
     int64_t max_degree = 0;
-    std::vector<int64_t> h_node_off, h_edge_off;
+    std::vector<int64_t> h_node_off, h_edge_off, h_slot_off;
+    // chunks of whole graphs counted one after another (bounds the 4-cycle array)
+    struct Chunk { int32_t g0, g1; int64_t n0, n1, s0, s1, e0, e1, t0, t1; };
+    std::vector<Chunk> chunks;
+    int64_t a_stride = 0, a_base = 0;
     tg_options opt;
 
     // graph (built once)
@@ -129,6 +133,8 @@ struct Graph {
         c.C = C.as<uint32_t>();
         c.tau = tau.as<int64_t>();
         c.A = A.as<uint32_t>();
+        c.a_base = a_base;
+        c.a_stride = a_stride;
         c.tables = tables.as<uint32_t>();
         c.table_stride = table_stride;
         c.gacc = gacc.as<unsigned long long>();
@@ -184,6 +190,7 @@ inline void fill_defaults(tg_options *o) {
     o->light_anchor_max_wedges = 256;
     o->anchor_table_budget_mb = 4096;
     o->ctas_per_sm = 4;
+    o->cycle_budget_mb = 16384;
 }
 
 // number of SMs of the current device
@@ -197,9 +204,11 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
 // count entries (tg_count.cu)
 void prepare_counting(Graph &G, int k, cudaStream_t s);
 void prepare_edges(Graph &G, int k, cudaStream_t s);
-int64_t launch_prepare(Graph &G, int k, cudaStream_t s);
-int64_t launch_edges(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out,
-                     unsigned long long *gacc, cudaStream_t s);
+// Runs the counting stages for edges [e_begin, e_end) into per_edge_out
+// (row 0 = e_begin) and the raw sums gacc.  full: the whole graph, every
+// stage recomputed (no cached state).  Returns the kernel launches.
+int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out,
+                  unsigned long long *gacc, bool full, cudaStream_t s);
 int64_t launch_finalize(Graph &G, int k, int64_t *global_out, cudaStream_t s);
 
 }  // namespace tg

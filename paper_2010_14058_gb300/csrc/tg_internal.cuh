@@ -55,7 +55,9 @@ struct GraphView {
 struct CountView {
     uint32_t *C;                // [m*L]   typed triangle counts c_e^t
     int64_t *tau;               // [n*L*L] ordered typed edges inside Gamma_x
-    uint32_t *A;                // [L*L*nnz] 4-cycle contributions per slot (SoA by type pair)
+    uint32_t *A;                // [L*L][a_stride] 4-cycle contributions per slot of the current chunk
+    int64_t a_base;             // first adjacency slot of the current chunk
+    int64_t a_stride;           // slots per type-pair row of A
     uint32_t *tables;           // dense per-CTA wedge tables
     int64_t table_stride;       // entries (uint32) per CTA table
     unsigned long long *gacc;   // [ngraphs*G] raw per-graphlet edge sums

@@ -139,15 +139,18 @@ def test_edge_endpoints_and_ranges():
     h.free()
 
 
-def test_batch_equals_separate_graphs():
+@pytest.mark.parametrize("options", [None, {"cycle_budget_mb": 1}])
+def test_batch_equals_separate_graphs(options):
+    # cycle_budget_mb = 1 splits the batch into many chunks of whole graphs
     graphs = [graphgen.erdos_renyi(50 + 30 * x, 200 + 150 * x, 3, 400 + x) for x in range(7)]
     graphs.append(graphgen.chung_lu(2000, 9000, 2.1, 500.0, 3, 9))
     graphs.insert(3, graph_from_edges(5, [], [0, 1, 2, 0, 1], 3))      # an empty graph inside the batch
+    graphs += [graphgen.erdos_renyi(300, 1500, 3, 600 + x) for x in range(12)]
     node_off, rp, col, ty = concat_graphs(graphs)
     L = 3
     lay = tg.tg_layout(L, 4)
     h = tg.tg_build_batch(node_off, torch.as_tensor(rp, device="cuda"), torch.as_tensor(col, device="cuda"),
-                          torch.as_tensor(ty, device="cuda"), L)
+                          torch.as_tensor(ty, device="cuda"), L, options=options)
     assert h.ngraphs == len(graphs)
     eoff = tg.tg_edge_offsets(h)
     pe = torch.zeros((h.m, lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
@@ -171,6 +174,16 @@ def test_batch_equals_separate_graphs():
     gl2 = torch.zeros_like(gl)
     tg.tg_count(h, 4, None, gl2)
     assert torch.equal(gl2, gl)
+    # ranges that cut across graphs (and chunks) give the same rows and sums
+    raw = torch.zeros_like(gl)
+    cuts = [0, 7, int(eoff[4]) + 3, int(eoff[9]) - 1, int(eoff[15]), h.m]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        part = torch.zeros((b - a, lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
+        tg.tg_count_range(h, 4, a, b, part, raw)
+        assert torch.equal(part, pe[a:b])
+    np.testing.assert_array_equal(tg.tg_finalize_global(L, 4, len(graphs), raw.cpu().numpy().ravel()),
+                                  gl.cpu().numpy().ravel())
+    assert tg.tg_query_status(h) == 0
     h.free()
 
 
