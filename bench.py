@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched"],
+                    help="plain: one graph (the headline line); batched: the ego-network batch vs per-graph launches")
+    ap.add_argument("--graphs", type=int, default=8192, help="graphs in the batched workload")
     return ap.parse_args()
 
 
@@ -340,9 +343,105 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ batched form
+
+def run_batched(args):
+    """Batched form: the ego-network batch (graphs with log-uniform edge
+    counts 100..400,000, L = 6) as one batch handle counted by one captured
+    CUDA graph (tg_count_batch), against plain launches of the same graphs
+    one at a time (tg_build + tg_count per graph).  Both produce per-graph
+    global totals, which must be identical.  value = edges / time of the
+    counting calls (handles built beforehand); build times reported apart."""
+    import torch
+
+    import graphgen
+    import paper_2010_14058_gb300 as tg
+    from paper_2010_14058_gb300 import build as tgbuild
+    torch.cuda.set_device(0)
+    tgbuild.build()
+    def log(msg):
+        print(f"[batched] {msg}", file=sys.stderr, flush=True)
+
+    t = time.perf_counter()
+    u = graphgen.ego_batch(args.graphs)
+    gen_s = time.perf_counter() - t
+    log(f"generated {args.graphs} graphs, {u['m']} edges in {gen_s:.1f} s")
+    L, m, ng = u["L"], u["m"], args.graphs
+    lay = tg.tg_layout(L, 4)
+    G = lay["global_slots"]
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda")
+    rp = torch.as_tensor(u["row_ptr"], device=dev)
+    col = torch.as_tensor(u["col"], device=dev)
+    ty = torch.as_tensor(u["types"], device=dev)
+    torch.cuda.synchronize()
+    # batched: one handle, one captured graph
+    t = time.perf_counter()
+    h = tg.tg_build_batch(u["node_off"], rp, col, ty, L, stream=stream)
+    torch.cuda.synchronize()
+    build_batch_s = time.perf_counter() - t
+    gl_b = torch.zeros((ng, G), dtype=torch.int64, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            tg.tg_count_batch(h, 4, None, gl_b, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            tg.tg_count_batch(h, 4, None, gl_b, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    batch_ms = e0.elapsed_time(e1) / args.steps
+    log(f"batched: build {build_batch_s:.2f} s, count {batch_ms:.1f} ms")
+    launches_batch = h.last_launch_count
+    status_b = tg.tg_query_status(h)
+    h.free()
+    # plain: graph by graph
+    gl_p = torch.zeros((ng, G), dtype=torch.int64, device=dev)
+    plain_ms, build_plain_s = 0.0, 0.0
+    node_off = u["node_off"]
+    rp_h = u["row_ptr"]
+    status_p = 0
+    with torch.cuda.stream(stream):
+        for x in range(ng):
+            a, b = int(node_off[x]), int(node_off[x + 1])
+            s0, s1 = int(rp_h[a]), int(rp_h[b])
+            t = time.perf_counter()
+            hx = tg.tg_build(rp[a:b + 1] - s0, col[s0:s1] - a, ty[a:b], L, stream=stream)
+            stream.synchronize()
+            build_plain_s += time.perf_counter() - t
+            e0.record(stream)
+            tg.tg_count(hx, 4, None, gl_p[x], stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+            status_p = status_p or tg.tg_query_status(hx)
+            hx.free()
+            if x % 512 == 511:
+                log(f"plain: {x + 1} graphs, build {build_plain_s:.1f} s, count {plain_ms:.0f} ms")
+    identical = bool(torch.equal(gl_b, gl_p))
+    line = {"metric": METRIC + ", batched form", "value": round(m / (batch_ms / 1e3), 1), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(batch_ms, 3), "higher_is_better": True,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"ego_batch({ng})", "graphs": ng, "edges": m, "nodes": u["n"], "types": L,
+                       "graph_edges_median": float(np.median(u["graph_m"])), "graph_edges_max": int(u["graph_m"].max()),
+                       "parent": "Chung-Lu n=4e6 m=4e7 gamma=2.3 max weight 2e4", "generation_s": round(gen_s, 1)},
+            "batched": {"count_ms": round(batch_ms, 3), "edges_per_s": round(m / (batch_ms / 1e3), 1),
+                        "build_s": round(build_batch_s, 3), "launches_per_count": launches_batch,
+                        "status": tg.STATUS[status_b]},
+            "plain_per_graph": {"count_ms": round(plain_ms, 3), "edges_per_s": round(m / (plain_ms / 1e3), 1),
+                                "build_s": round(build_plain_s, 3), "status": tg.STATUS[status_p]},
+            "speedup_count": round(plain_ms / batch_ms, 2),
+            "speedup_build_plus_count": round((build_plain_s + plain_ms / 1e3) / (build_batch_s + batch_ms / 1e3), 2),
+            "totals_identical": identical}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode == "batched":
+        run_batched(a)
     else:
         run_ours(a)
