@@ -266,6 +266,7 @@ tg_status tg_count_batch(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_
             }
             tg::prepare_counting(G, k, s);
             tg::prepare_edges(G, k, s);
+            tg::prepare_capture(G, k, s);
             TG_CK(cudaStreamSynchronize(s));
             cudaGraph_t graph = nullptr;
             TG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

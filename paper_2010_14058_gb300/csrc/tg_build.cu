@@ -117,7 +117,7 @@ __global__ void k_gather_types(int64_t n, const int32_t *__restrict__ old_of, co
 
 // warp per internal row x: adjacency ids, self-loop / repeat checks, type offsets
 __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const unsigned long long *__restrict__ keys,
-                       int32_t *adj, int32_t *toff, int32_t *pivot, uint32_t *status) {
+                       int32_t *adj, int32_t *toff, int32_t *pivot, int32_t *nplus, uint32_t *status) {
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
     int lane = threadIdx.x & (kWarp - 1);
     if (warp >= n) return;
@@ -150,6 +150,7 @@ __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const u
     __syncwarp();
     const int32_t sb = lane < L ? toff[x * (L + 1) + lane] : 0;
     const int32_t se = lane < L ? toff[x * (L + 1) + lane + 1] : 0;
+    int32_t up = 0;                      // higher-priority neighbours of this type segment
     if (lane < L) {
         int64_t lo = b + sb, hi = b + se;
         while (lo < hi) {
@@ -157,7 +158,10 @@ __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const u
             if (adj[mid] < (int32_t)x + 1) lo = mid + 1; else hi = mid;
         }
         pivot[x * L + lane] = (int32_t)(lo - b);
+        up = se - (int32_t)(lo - b);
     }
+    for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(0xffffffffu, up, o);
+    if (lane == 0) nplus[x] = up;
 }
 
 // warp per internal row x: forward slots (caller id of x < caller id of y) become edges
@@ -434,6 +438,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
     G.adj.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
     G.toff.alloc(sizeof(int32_t) * std::max<int64_t>(n * (L + 1), 1));
     G.pivot.alloc(sizeof(int32_t) * std::max<int64_t>(n * L, 1));
+    G.nplus.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1));
     G.ty.alloc(std::max<int64_t>(n, 1));
     {
         TBuf keys(sizeof(unsigned long long) * std::max<int64_t>(nnz, 1), s), keys2(sizeof(unsigned long long) * std::max<int64_t>(nnz, 1), s);
@@ -455,7 +460,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
             ++G.last_launches;
             k_rows<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(n, L, G.rp.as<int64_t>(), keys2.as<unsigned long long>(),
                                                                        G.adj.as<int32_t>(), G.toff.as<int32_t>(),
-                                                                       G.pivot.as<int32_t>(), status);
+                                                                       G.pivot.as<int32_t>(), G.nplus.as<int32_t>(), status);
             TG_CK(cudaGetLastError());
         }
     }

@@ -39,19 +39,17 @@
 #include <algorithm>
 #include <vector>
 
+#include <cub/device/device_scan.cuh>
+
 #include "tg_host.hpp"
 
 namespace tg {
 
 namespace {
 
-constexpr int kEdgeThreads = 256;           // k_edge4_light: 8 warps, one edge each
-constexpr int kHeavyThreads = 512;          // k_edge4_heavy: one edge per CTA
 constexpr int kAnchorThreads = 512;         // k_wedge_heavy: one anchor per CTA
 constexpr int kLightAnchorWarps = 4;        // k_wedge_light: one anchor per warp
-constexpr int kTCapWarp = 256;              // T list capacity of a warp (light edges: |T| <= 256)
-constexpr int kTCapSmemHeavy = 8192;        // T list capacity in shared memory for a heavy edge
-constexpr int kTile = 2048;                 // edges per tile of k_edge4_light
+constexpr int kTile = 2048;                 // edges per tile of k_epi4 and k_edge3
 
 __device__ __forceinline__ unsigned warp_sum_u32(unsigned v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -361,354 +359,16 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
 }
 
 // ------------------------------------------------------------ per-edge 4-node
-// Shared workspace of one edge.
-struct EdgeWs {
-    unsigned long long TCi[kMaxL * kMaxL], TCj[kMaxL * kMaxL], DT[kMaxL * kMaxL], K[kMaxL * kMaxL];
-    int64_t Pm[kMaxL * kMaxL];                  // 3-paths j - w - r - i by (type w, type r); then Q
-    int64_t Ks[kMaxL * kMaxL];                  // ordered adjacent pairs in T (K + K^T)
-    int64_t taui[kMaxL * kMaxL], tauj[kMaxL * kMaxL], deli[kMaxL * kMaxL], delj[kMaxL * kMaxL];
-    int64_t c[kMaxL], a[kMaxL], b[kMaxL], di[kMaxL], dj[kMaxL];
-    int32_t tstart[kMaxL + 1];   // T list offsets per type
-    int32_t nT;
-    int32_t p, q;                // types of the endpoints
-    int32_t wcount[32];          // per-warp compaction counts (CTA variant)
-};
-
-// Enumerates T_ij (typed intersection), appends it to Tlist in (type, id)
-// order and accumulates TCi, TCj, DT.  `gsize` threads of the group, thread
-// rank `gr`; the group has gsize/32 warps.  bar() is the group barrier.
-template <class Bar>
-__device__ void enumerate_T(const GraphView &g, const CountView &cv, int64_t e, int32_t i, int32_t j, EdgeWs &ws,
-                            int32_t *Tlist, int64_t Tcap, int gsize, int gr, Bar bar) {
-    const int L = g.L;
-    const int lane = gr & 31, wid = gr >> 5, nwarp = gsize >> 5;
-    int32_t base = 0;
-    for (int t = 0; t < L; ++t) {
-        if (gr == 0) ws.tstart[t] = base;
-        const uint32_t ct = cv.C[e * L + t];      // |T_ij^t| from k_tri: nothing to find when 0
-        if (ct == 0) continue;
-        int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
-        int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
-        bool swapped = false;
-        if (ei - bi > ej - bj) {
-            int64_t x = bi; bi = bj; bj = x;
-            x = ei; ei = ej; ej = x;
-            swapped = true;
-        }
-        // per-thread sums over this type segment, reduced per warp at its end
-        unsigned long long a_ci[kMaxL], a_cj[kMaxL], a_dt[kMaxL];
-#pragma unroll
-        for (int q = 0; q < kMaxL; ++q) { a_ci[q] = 0; a_cj[q] = 0; a_dt[q] = 0; }
-        for (int64_t r0 = bi; r0 < ei; r0 += gsize) {
-            const int64_t s = r0 + gr;
-            bool found = false;
-            int64_t r = -1;
-            int32_t w = 0;
-            if (s < ei) {
-                w = g.adj[s];
-                r = lower_bound_i32(g.adj, bj, ej, w);
-                found = r < ej && g.adj[r] == w;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, found);
-            if (nwarp > 1) {
-                if (lane == 0) ws.wcount[wid] = __popc(bal);
-                bar();
-            }
-            int32_t off = base;
-            int32_t total = __popc(bal);
-            if (nwarp > 1) {
-                total = 0;
-                for (int q = 0; q < nwarp; ++q) {
-                    if (q < wid) off += ws.wcount[q];
-                    total += ws.wcount[q];
-                }
-            }
-            if (found) {
-                const int32_t pos = off + __popc(bal & ((1u << lane) - 1u));
-                if (pos < Tcap) Tlist[pos] = w;
-                else set_status(cv.status, ST_INTERNAL);
-                const int64_t si = swapped ? r : s, sj = swapped ? s : r;   // slots of w in rows i and j
-                const uint32_t *ci = cv.C + (int64_t)g.slot_eid[si] * L;
-                const uint32_t *cj = cv.C + (int64_t)g.slot_eid[sj] * L;
-                const int32_t *o = g.toff + (int64_t)w * (L + 1);
-#pragma unroll
-                for (int q = 0; q < kMaxL; ++q) {
-                    if (q < L) {
-                        a_ci[q] += ci[q];
-                        a_cj[q] += cj[q];
-                        a_dt[q] += (unsigned)(o[q + 1] - o[q]);
-                    }
-                }
-            }
-            base += total;
-            if (nwarp > 1) bar();
-        }
-        if (bi < ei) {
-#pragma unroll
-            for (int q = 0; q < kMaxL; ++q) {
-                if (q >= L) break;
-                const unsigned long long x1 = warp_sum_u64(a_ci[q]), x2 = warp_sum_u64(a_cj[q]), x3 = warp_sum_u64(a_dt[q]);
-                if (lane == 0) {
-                    if (x1) atomicAdd(&ws.TCi[t * kMaxL + q], x1);
-                    if (x2) atomicAdd(&ws.TCj[t * kMaxL + q], x2);
-                    if (x3) atomicAdd(&ws.DT[t * kMaxL + q], x3);
-                }
-            }
-        }
-    }
-    if (gr == 0) {
-        ws.tstart[L] = base;
-        ws.nT = base;
-    }
-    bar();
-}
-
-// K: adjacent pairs (w, x) of T with w < x, by type.  For each w, either
-// scan N+(w) = {x in Gamma_w : x > w} (all types, flattened over the warp's
-// lanes, each x looked up in T's sorted segment of its type), or take each
-// x > w of T and look it up in Gamma_w -- whichever touches fewer entries.
-template <class Bar>
-__device__ void count_K(const GraphView &g, EdgeWs &ws, const int32_t *Tlist, int gsize, int gr, Bar bar) {
-    const int L = g.L;
-    const int lane = gr & 31, wid = gr >> 5, nwarp = gsize >> 5;
-    const int32_t nT = ws.nT;
-    if (nT < 2) {
-        bar();
-        return;
-    }
-    int32_t ts[kMaxL + 1];
-#pragma unroll
-    for (int q = 0; q <= kMaxL; ++q) ts[q] = q <= L ? ws.tstart[q] : nT;
-    const int32_t npair = nT * (nT - 1) / 2;
-    if (npair <= 2 * gsize) {
-        // few pairs: one pair {T[a], T[b]} per thread, adjacency by binary search
-        // of the larger id in the smaller id's typed segment; each adjacent pair
-        // is counted once, as (smaller id, larger id)
-        for (int32_t pk = gr; pk < npair; pk += gsize) {
-            int32_t a = 0, rem = pk;
-            while (rem >= nT - 1 - a) { rem -= nT - 1 - a; ++a; }
-            const int32_t b = a + 1 + rem;
-            int ta = 0, tb = 0;
-#pragma unroll
-            for (int qq = 1; qq < kMaxL; ++qq) {
-                ta += (qq < L && ts[qq] <= a) ? 1 : 0;
-                tb += (qq < L && ts[qq] <= b) ? 1 : 0;
-            }
-            int32_t w = Tlist[a], x = Tlist[b];
-            int tw = ta, tx = tb;
-            if (x < w) { int32_t y = w; w = x; x = y; int ty = tw; tw = tx; tx = ty; }
-            const int64_t sb = seg_begin(g, w, tx), se = seg_end(g, w, tx);
-            const int64_t r = lower_bound_i32(g.adj, sb, se, x);
-            if (r < se && g.adj[r] == x) atomicAdd(&ws.K[tw * kMaxL + tx], 1ull);
-        }
-        bar();
-        return;
-    }
-    for (int32_t kw = wid; kw < nT; kw += nwarp) {
-        const int32_t w = Tlist[kw];
-        int tw = 0;
-#pragma unroll
-        for (int q = 1; q < kMaxL; ++q) tw += (q < L && ts[q] <= kw) ? 1 : 0;
-        // N+(w) per type: [pb_q, pb_q + cnt_q)
-        int64_t pb = 0;
-        int32_t cnt = 0;
-        const int64_t rw = g.rp[w];
-        if (lane < L) {
-            pb = rw + g.pivot[(int64_t)w * L + lane];
-            cnt = (int32_t)(rw + g.toff[(int64_t)w * (L + 1) + lane + 1] - pb);
-        }
-        int32_t pre = cnt;                                   // inclusive prefix over lanes < L
-#pragma unroll
-        for (int o = 1; o < kMaxL; o <<= 1) {
-            int32_t v = __shfl_up_sync(0xffffffffu, pre, o);
-            if (lane >= o) pre += v;
-        }
-        int64_t pbq[kMaxL];
-        int32_t preq[kMaxL];
-#pragma unroll
-        for (int q = 0; q < kMaxL; ++q) {
-            pbq[q] = __shfl_sync(0xffffffffu, pb, q);
-            preq[q] = q < L ? __shfl_sync(0xffffffffu, pre, q) : 0x7fffffff;
-        }
-        const int32_t dplus = preq[L - 1];
-        if (dplus == 0) continue;
-        unsigned cq[kMaxL];
-#pragma unroll
-        for (int q = 0; q < kMaxL; ++q) cq[q] = 0;
-        int lgT = 1;
-        while ((1 << lgT) < nT + 1) ++lgT;
-        const int64_t dw = g.rp[w + 1] - rw;
-        int lgd = 1;
-        while ((1ll << lgd) < dw + 1) ++lgd;
-        // members of T above w, per type: [tg_q, ts_{q+1}) (each T segment is id-sorted)
-        int32_t tgt = 0;
-        if (lane < L) {
-            int32_t lo = ts[0], hi = ts[0];
-#pragma unroll
-            for (int qq = 0; qq < kMaxL; ++qq)
-                if (qq == lane) { lo = ts[qq]; hi = ts[qq + 1]; }
-            while (lo < hi) {
-                int32_t mid = (lo + hi) >> 1;
-                if (Tlist[mid] <= w) lo = mid + 1; else hi = mid;
-            }
-            tgt = lo;
-        }
-        int32_t above = 0;
-        if (lane < L) {
-            int32_t te = 0;
-#pragma unroll
-            for (int qq = 0; qq < kMaxL; ++qq)
-                if (qq == lane) te = ts[qq + 1];
-            above = te - tgt;
-        }
-        int32_t nabove = above;
-        for (int o = 16; o > 0; o >>= 1) nabove += __shfl_xor_sync(0xffffffffu, nabove, o);
-        if (nabove == 0) continue;
-        if ((int64_t)dplus * lgT <= (int64_t)nabove * lgd) {
-            for (int32_t f = lane; f < dplus; f += 32) {
-                int q = 0;
-#pragma unroll
-                for (int qq = 0; qq < kMaxL - 1; ++qq) q += (f >= preq[qq]) ? 1 : 0;
-                int64_t slot = 0;
-#pragma unroll
-                for (int qq = 0; qq < kMaxL; ++qq)
-                    if (qq == q) slot = pbq[qq] + (f - (qq ? preq[qq - 1] : 0));
-                const int32_t x = g.adj[slot];
-                int32_t lo = 0, hi = 0;
-#pragma unroll
-                for (int qq = 0; qq < kMaxL; ++qq)
-                    if (qq == q) { lo = ts[qq]; hi = ts[qq + 1]; }
-                const int32_t te = hi;
-                while (lo < hi) {
-                    int32_t mid = (lo + hi) >> 1;
-                    if (Tlist[mid] < x) lo = mid + 1; else hi = mid;
-                }
-                if (lo < te && Tlist[lo] == x) {
-#pragma unroll
-                    for (int qq = 0; qq < kMaxL; ++qq) cq[qq] += (qq == q) ? 1u : 0u;
-                }
-            }
-        } else {
-            for (int q = 0; q < L; ++q) {
-                const int32_t kb = __shfl_sync(0xffffffffu, tgt, q);
-                const int32_t ke = ts[q + 1 <= kMaxL ? q + 1 : kMaxL];
-                if (kb >= ke) continue;
-                const int64_t b = seg_begin(g, w, q), e = seg_end(g, w, q);
-                if (b == e) continue;
-                unsigned c = 0;
-                for (int32_t k = kb + lane; k < ke; k += 32) {
-                    const int32_t x = Tlist[k];
-                    const int64_t r = lower_bound_i32(g.adj, b, e, x);
-                    c += (r < e && g.adj[r] == x) ? 1u : 0u;
-                }
-#pragma unroll
-                for (int qq = 0; qq < kMaxL; ++qq) cq[qq] += (qq == q) ? c : 0u;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kMaxL; ++q) {
-            if (q >= L) break;
-            unsigned v = warp_sum_u32(cq[q]);
-            if (lane == 0 && v) atomicAdd(&ws.K[tw * kMaxL + q], (unsigned long long)v);
-        }
-    }
-    bar();
-}
-
-// Derived typed counts of one edge, each matrix entry computed once, in
-// place, in dependency order (x, y index types; z = x * kMaxL + y):
-//   Ks  = K + K^T                       ordered adjacent pairs in T
-//   TCi -> CTi = TCi - Ks - [y=q] c_x   (w in T^x, r in S_i^y adjacent)
-//   TCj -> CTj = TCj - Ks - [y=p] c_x
-//   taui -> Wi = tau_i - CTi - CTi^T - Ks - [x=q] c_y - [y=q] c_x
-//   tauj -> Wj = tau_j - CTj - CTj^T - Ks - [x=p] c_y - [y=p] c_x
-//   Pm  -> Q   = P - CTj^T - CTi - Ks  (w in S_j^x, r in S_i^y: 4-cycles)
-//   deli -> Ri = delta_i - DT - [x=q] d_j^y - [y=p] a_x - Wi - CTi^T - Q^T
-//   delj -> Rj = delta_j - DT - [x=p] d_i^y - [y=q] b_x - Wj - CTj^T - Q
-//   DT  -> G8  = DT - ([y=p]+[y=q]) c_x - Ks - CTi - CTj
-template <class Bar>
-__device__ void derive_matrices(EdgeWs &ws, int L, int gsize, int gr, Bar bar) {
-    const int p = ws.p, q = ws.q;
-    const int n2 = L * L;
-    for (int k = gr; k < n2; k += gsize) {
-        const int x = k / L, y = k % L, z = x * kMaxL + y, zt = y * kMaxL + x;
-        ws.Ks[z] = (int64_t)ws.K[z] + (int64_t)ws.K[zt];
-    }
-    bar();
-    for (int k = gr; k < n2; k += gsize) {
-        const int x = k / L, y = k % L, z = x * kMaxL + y;
-        ws.TCi[z] = (unsigned long long)((int64_t)ws.TCi[z] - ws.Ks[z] - (y == q ? ws.c[x] : 0));
-        ws.TCj[z] = (unsigned long long)((int64_t)ws.TCj[z] - ws.Ks[z] - (y == p ? ws.c[x] : 0));
-    }
-    bar();
-    const long long *CTi = reinterpret_cast<const long long *>(ws.TCi);
-    const long long *CTj = reinterpret_cast<const long long *>(ws.TCj);
-    for (int k = gr; k < n2; k += gsize) {
-        const int x = k / L, y = k % L, z = x * kMaxL + y, zt = y * kMaxL + x;
-        ws.taui[z] = ws.taui[z] - CTi[z] - CTi[zt] - ws.Ks[z] - (x == q ? ws.c[y] : 0) - (y == q ? ws.c[x] : 0);
-        ws.tauj[z] = ws.tauj[z] - CTj[z] - CTj[zt] - ws.Ks[z] - (x == p ? ws.c[y] : 0) - (y == p ? ws.c[x] : 0);
-        ws.Pm[z] = ws.Pm[z] - CTj[zt] - CTi[z] - ws.Ks[z];
-    }
-    bar();
-    for (int k = gr; k < n2; k += gsize) {
-        const int x = k / L, y = k % L, z = x * kMaxL + y, zt = y * kMaxL + x;
-        const int64_t dt = (int64_t)ws.DT[z];
-        ws.deli[z] = ws.deli[z] - dt - (x == q ? ws.dj[y] : 0) - (y == p ? ws.a[x] : 0) - ws.taui[z] - CTi[zt] - ws.Pm[zt];
-        ws.delj[z] = ws.delj[z] - dt - (x == p ? ws.di[y] : 0) - (y == q ? ws.b[x] : 0) - ws.tauj[z] - CTj[zt] - ws.Pm[z];
-    }
-    bar();
-    for (int k = gr; k < n2; k += gsize) {
-        const int x = k / L, y = k % L, z = x * kMaxL + y;
-        ws.DT[z] = (unsigned long long)((int64_t)ws.DT[z] - ((y == p ? 1 : 0) + (y == q ? 1 : 0)) * ws.c[x] - ws.Ks[z] -
-                                        CTi[z] - CTj[z]);
-    }
-    bar();
-}
-
-// Orbit values of one type pair (t <= u) from the derived matrices;
-// returns false if an internal identity fails (negative count, odd diagonal).
-__device__ __noinline__ bool orbit_values(const EdgeWs &ws, int t, int u, int64_t *gv /*[10]: g3..g12*/) {
-    const long long *CTi = reinterpret_cast<const long long *>(ws.TCi);
-    const long long *CTj = reinterpret_cast<const long long *>(ws.TCj);
-    const long long *G8 = reinterpret_cast<const long long *>(ws.DT);
-    const int tu = t * kMaxL + u, ut = u * kMaxL + t, tt = t * kMaxL + t;
-    bool ok = true;
-    int64_t g3, g6, g7, g8, g10, g12;
-    if (t != u) {
-        g3 = ws.deli[tu] + ws.delj[tu] + ws.deli[ut] + ws.delj[ut];   // Ri + Rj, both orders
-        g6 = ws.Pm[tu] + ws.Pm[ut];                                   // Q
-        g7 = ws.taui[tu] + ws.tauj[tu];                               // Wi + Wj
-        g8 = G8[tu] + G8[ut];
-        g10 = CTi[tu] + CTj[tu] + CTi[ut] + CTj[ut];
-        g12 = ws.Ks[tu];
-    } else {
-        g3 = ws.deli[tt] + ws.delj[tt];
-        g6 = ws.Pm[tt];
-        const int64_t w2 = ws.taui[tt] + ws.tauj[tt], k2 = ws.Ks[tt];
-        ok = !(w2 & 1) && !(k2 & 1);
-        g7 = w2 / 2;
-        g8 = G8[tt];
-        g10 = CTi[tt] + CTj[tt];
-        g12 = k2 / 2;
-    }
-    const int64_t at = ws.a[t], au = ws.a[u], bt = ws.b[t], bu = ws.b[u], ct = ws.c[t], cu = ws.c[u];
-    int64_t g4, g5, g9, g11;
-    if (t == u) {
-        g4 = at * bt - g6;                                   // Lemma 1
-        g5 = at * (at - 1) / 2 + bt * (bt - 1) / 2 - g7;     // Lemma 2
-        g9 = ct * (at + bt) - g10;                           // Lemma 3
-        g11 = ct * (ct - 1) / 2 - g12;                       // Lemma 4
-    } else {
-        g4 = at * bu + au * bt - g6;
-        g5 = at * au + bt * bu - g7;
-        g9 = ct * (au + bu) + cu * (at + bt) - g10;
-        g11 = ct * cu - g12;
-    }
-    gv[0] = g3; gv[1] = g4; gv[2] = g5; gv[3] = g6; gv[4] = g7;
-    gv[5] = g8; gv[6] = g9; gv[7] = g10; gv[8] = g11; gv[9] = g12;
-    for (int k = 0; k < 10; ++k) ok = ok && gv[k] >= 0;
-    return ok;
-}
+// The per-edge stage runs as three lean warp-per-edge kernels with the
+// per-edge intermediates in HBM (all indexed relative to the chunk's first
+// edge e_base):
+//   k_tsum    T list of the edge (sorted by (type, id)) and the sums TCi, TCj,
+//             DT over its triangle nodes;
+//   k_clique  K: adjacent pairs inside T (warp per edge; CTA per edge for
+//             the edges with |T| above a threshold, collected on the device);
+//   k_epi4    every orbit of Table 3 from the gathered sums, one warp per
+//             edge with the L x L matrices held one entry per lane and
+//             transposed by shuffles; writes the row and the CTA histogram.
 
 __device__ __forceinline__ uint32_t sat32(int64_t v, uint32_t *status) {
     if (v > 0xffffffffll) {
@@ -730,83 +390,6 @@ __device__ __forceinline__ int graphlet_block(int o) {
     }
 }
 
-// Epilogue of one edge: stages the per-edge inputs in shared memory, then
-// writes the row and adds to the CTA histogram.
-template <class Bar>
-__device__ void edge_epilogue(const GraphView &g, const CountView &cv, int64_t e, int32_t i, int32_t j, EdgeWs &ws,
-                              uint32_t *row, unsigned long long *hist, int gsize, int gr, Bar bar) {
-    const int L = g.L;
-    const int p = g.ty[i], q = g.ty[j];
-    if (gr == 0) { ws.p = p; ws.q = q; }
-    for (int t = gr; t < L; t += gsize) {
-        const int64_t c = cv.C[e * L + t];
-        const int64_t di = typed_degree(g, i, t), dj = typed_degree(g, j, t);
-        ws.c[t] = c;
-        ws.di[t] = di;
-        ws.dj[t] = dj;
-        ws.a[t] = di - c - (q == t ? 1 : 0);
-        ws.b[t] = dj - c - (p == t ? 1 : 0);
-    }
-    const int64_t slot_ij = g.e_slot_lo[e], slot_ji = g.e_slot_hi[e];
-    const int64_t *tau_i = cv.tau + (int64_t)i * L * L, *tau_j = cv.tau + (int64_t)j * L * L;
-    const int64_t *del_i = g.delta + (int64_t)i * L * L, *del_j = g.delta + (int64_t)j * L * L;
-    for (int k = gr; k < L * L; k += gsize) {
-        const int x = k / L, y = k % L;
-        const int z = x * kMaxL + y;
-        // P[x][y]: 3-paths j - w - r - i with phi_w = x, phi_r = y (slot i->j holds
-        // [type next to i][type next to j], slot j->i the reverse)
-        const uint32_t *A = cv.A - cv.a_base;
-        ws.Pm[z] = (int64_t)A[(int64_t)(y * L + x) * cv.a_stride + slot_ij] + (int64_t)A[(int64_t)(x * L + y) * cv.a_stride + slot_ji];
-        ws.taui[z] = tau_i[k];
-        ws.tauj[z] = tau_j[k];
-        ws.deli[z] = del_i[k];
-        ws.delj[z] = del_j[k];
-    }
-    bar();
-    derive_matrices(ws, L, gsize, gr, bar);
-    const int P = L * (L + 1) / 2;
-    // 3-node slots and 2-node / 3-node global blocks
-    for (int t = gr; t < L; t += gsize) {
-        const int64_t s3 = ws.a[t] + ws.b[t];
-        if (ws.a[t] < 0 || ws.b[t] < 0) set_status(cv.status, ST_INTERNAL);
-        if (row) {
-            row[t] = sat32(s3, cv.status);
-            row[L + t] = sat32(ws.c[t], cv.status);
-        }
-        int ms[3] = {p, q, t};
-        sort3(ms);
-        const int r = multiset_rank_dev(L, 3, ms);
-        if (s3) atomicAdd(&hist[gblock_off(L, 1) + r], (unsigned long long)s3);
-        if (ws.c[t]) atomicAdd(&hist[gblock_off(L, 2) + r], (unsigned long long)ws.c[t]);
-    }
-    if (gr == 0) {
-        int ms[2] = {p < q ? p : q, p < q ? q : p};
-        atomicAdd(&hist[multiset_rank_dev(L, 2, ms)], 1ull);
-    }
-    for (int pi = gr; pi < P; pi += gsize) {
-        int t = 0;
-        while (pair_idx(L, t, L - 1) < pi) ++t;
-        const int u = t + (pi - pair_idx(L, t, t));
-        int64_t gv[10];
-        if (!orbit_values(ws, t, u, gv)) set_status(cv.status, ST_INTERNAL);
-        int ms[4] = {p, q, t, u};
-        sort4(ms);
-        const int r = multiset_rank_dev(L, 4, ms);
-        for (int o = 3; o <= 12; ++o) {
-            const int64_t v = gv[o - 3];
-            if (row) row[2 * L + (o - 3) * P + pi] = sat32(v, cv.status);
-            if (v > 0) atomicAdd(&hist[gblock_off(L, graphlet_block(o)) + r], (unsigned long long)v);
-        }
-    }
-    bar();
-}
-
-__device__ void clear_ws(EdgeWs &ws, int gsize, int gr) {
-    for (int k = gr; k < kMaxL * kMaxL; k += gsize) {
-        ws.TCi[k] = 0; ws.TCj[k] = 0; ws.DT[k] = 0; ws.K[k] = 0;
-    }
-}
-
 __device__ void flush_hist(unsigned long long *hist, int G, unsigned long long *gacc, int graph, int gsize, int gr) {
     for (int s = gr; s < G; s += gsize) {
         unsigned long long v = hist[s];
@@ -820,85 +403,470 @@ struct Tile {
     int32_t graph, pad;
 };
 
-// Light edges (min(d_i, d_j) <= light_max): one warp per edge, tiles of edge
-// ids that never cross a graph, a per-CTA histogram for global sums.
-// Dynamic shared memory: [histogram G u64][EdgeWs per warp][T list per warp].
-__global__ void __launch_bounds__(kEdgeThreads, 4) k_edge4_light(GraphView g, CountView cv, const Tile *__restrict__ tiles,
-                                                             int64_t n_tiles, int64_t light_max, int64_t e_begin,
-                                                             uint32_t *per_edge_out, unsigned long long *gacc) {
-    extern __shared__ unsigned long long dsm[];
+__device__ __forceinline__ unsigned long long warp_allsum_u64(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// |T_e| per edge of the chunk (input of the offset scan), and the device
+// list of edges whose T is too large for one warp's 4-clique pass.
+__global__ void k_tcount(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t, int64_t *tcount,
+                         int32_t *big_list, unsigned long long *big_count) {
+    const int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e > e1) return;
+    if (e == e1) { tcount[e1 - e0] = 0; return; }
+    int64_t c = 0;
+    for (int t = 0; t < g.L; ++t) c += cv.C[e * g.L + t];
+    tcount[e - e0] = c;
+    if (c > big_t) {
+        const unsigned long long k = atomicAdd(big_count, 1ull);
+        big_list[k] = (int32_t)e;
+    }
+}
+
+// Warp per edge: T list and the triangle-node sums (Cor. 1; gathers of the
+// typed triangle counts of the edges (i,w), (j,w) and of d_w^t').
+__global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int64_t e0, int64_t e1) {
+    const int L = g.L, LL = L * L;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
+        const int64_t er = e - e0;
+        const int32_t i = g.e_lo[e], j = g.e_hi[e];
+        int32_t *tl = cv.tlist + cv.toffs[er];
+        unsigned long long *sum = cv.tsum + er * 3 * LL;
+        int32_t pos = 0;
+        for (int t = 0; t < L; ++t) {
+            unsigned long long a1[kMaxL], a2[kMaxL], a3[kMaxL];
+#pragma unroll
+            for (int q = 0; q < kMaxL; ++q) { a1[q] = 0; a2[q] = 0; a3[q] = 0; }
+            if (cv.C[e * L + t] != 0) {
+                int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
+                int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
+                bool swapped = false;
+                if (ei - bi > ej - bj) {
+                    int64_t x = bi; bi = bj; bj = x;
+                    x = ei; ei = ej; ej = x;
+                    swapped = true;
+                }
+                for (int64_t r0 = bi; r0 < ei; r0 += 32) {
+                    const int64_t s = r0 + lane;
+                    bool found = false;
+                    int64_t r = 0;
+                    int32_t w = 0;
+                    if (s < ei) {
+                        w = g.adj[s];
+                        r = lower_bound_i32(g.adj, bj, ej, w);
+                        found = r < ej && g.adj[r] == w;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, found);
+                    if (found) {
+                        tl[pos + __popc(bal & ((1u << lane) - 1u))] = w;
+                        const uint32_t *ci = cv.C + (int64_t)g.slot_eid[swapped ? r : s] * L;
+                        const uint32_t *cj = cv.C + (int64_t)g.slot_eid[swapped ? s : r] * L;
+                        const int32_t *o = g.toff + (int64_t)w * (L + 1);
+#pragma unroll
+                        for (int q = 0; q < kMaxL; ++q)
+                            if (q < L) {
+                                a1[q] += ci[q];
+                                a2[q] += cj[q];
+                                a3[q] += (unsigned)(o[q + 1] - o[q]);
+                            }
+                    }
+                    pos += __popc(bal);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kMaxL; ++q) {
+                if (q >= L) break;
+                const unsigned long long v1 = warp_allsum_u64(a1[q]), v2 = warp_allsum_u64(a2[q]), v3 = warp_allsum_u64(a3[q]);
+                if (lane == q) {
+                    sum[t * L + q] = v1;
+                    sum[LL + t * L + q] = v2;
+                    sum[2 * LL + t * L + q] = v3;
+                }
+            }
+        }
+    }
+}
+
+// type boundaries of an edge's T list, from its typed triangle counts
+__device__ __forceinline__ void t_bounds(const CountView &cv, int L, int64_t e, int32_t *ts) {
+    int32_t acc = 0;
+    for (int q = 0; q < L; ++q) { ts[q] = acc; acc += (int32_t)cv.C[e * L + q]; }
+    for (int q = L; q <= kMaxL; ++q) ts[q] = acc;
+}
+
+__device__ __forceinline__ int type_of_index(const int32_t *ts, int L, int32_t k) {
+    int t = 0;
+    for (int q = 1; q < L; ++q) t += ts[q] <= k ? 1 : 0;
+    return t;
+}
+
+// 4-clique pairs of one edge by a group of `gsize` threads (whole warps):
+// adjacent pairs (w, x) of T, each counted once as (smaller id, larger id),
+// into sK[type of smaller][type of larger].  Either every pair is checked by
+// a binary search in the smaller id's typed row, or every w scans its
+// higher-priority neighbours N+(w) and looks them up in T -- whichever
+// touches fewer entries.
+__device__ __forceinline__ uint32_t t_hash(int32_t x, int lgcap) {
+    return ((uint32_t)x * 2654435761u) >> (32 - lgcap);
+}
+
+// T as an open-addressing set (capacity 2^lgcap >= 2|T|, entries -1 when
+// empty), built by the group.
+__device__ void t_set_build(const int32_t *T, int32_t nT, int32_t *set, int lgcap, int gsize, int gr) {
+    const int cap = 1 << lgcap;
+    for (int k = gr; k < cap; k += gsize) set[k] = -1;
+    if (gsize > 32) __syncthreads(); else __syncwarp();
+    for (int32_t k = gr; k < nT; k += gsize) {
+        const int32_t x = T[k];
+        uint32_t h = t_hash(x, lgcap);
+        for (int probe = 0; probe < cap; ++probe) {
+            if (atomicCAS(&set[h], -1, x) == -1) break;
+            h = (h + 1) & (cap - 1);
+        }
+    }
+    if (gsize > 32) __syncthreads(); else __syncwarp();
+}
+
+__device__ __forceinline__ bool t_set_has(const int32_t *set, int lgcap, int32_t x) {
+    const int cap = 1 << lgcap;
+    uint32_t h = t_hash(x, lgcap);
+    for (int probe = 0; probe < cap; ++probe) {
+        const int32_t v = set[h];
+        if (v == x) return true;
+        if (v == -1) return false;
+        h = (h + 1) & (cap - 1);
+    }
+    return false;
+}
+
+// 4-clique pairs of one edge by a group of `gsize` threads (whole warps):
+// adjacent pairs (w, x) of T, each counted once as (smaller id, larger id),
+// into sK[type of smaller][type of larger].  Few pairs: every pair checked
+// by a binary search in the smaller id's typed row.  Otherwise each warp
+// takes members w of T and its lanes scan N+(w) = the neighbours of higher
+// priority (all types flattened), looking each up in the set of T.
+__device__ void clique_pairs(const GraphView &g, const int32_t *T, int32_t nT, const int32_t *ts, unsigned *sK,
+                             int32_t *set, int lgcap, int gsize, int gr) {
     const int L = g.L;
+    const int lane = gr & 31, wid = gr >> 5, nwarp = gsize >> 5;
+    const long long npair = (long long)nT * (nT - 1) / 2;
+    if (npair <= 2 * (long long)gsize) {
+        for (long long pk = gr; pk < npair; pk += gsize) {
+            int32_t a = 0;
+            long long rem = pk;
+            while (rem >= nT - 1 - a) { rem -= nT - 1 - a; ++a; }
+            const int32_t b = a + 1 + (int32_t)rem;
+            int32_t w = T[a], x = T[b];
+            int tw = type_of_index(ts, L, a), tx = type_of_index(ts, L, b);
+            if (x < w) { int32_t y = w; w = x; x = y; int ty = tw; tw = tx; tx = ty; }
+            const int64_t sb = seg_begin(g, w, tx), se = seg_end(g, w, tx);
+            const int64_t r = lower_bound_i32(g.adj, sb, se, x);
+            if (r < se && g.adj[r] == x) atomicAdd(&sK[tw * kMaxL + tx], 1u);
+        }
+        return;
+    }
+    t_set_build(T, nT, set, lgcap, gsize, gr);
+    // members in blocks of 32 per warp: each lane scans N+ of its own member
+    // when it is short (type segment by type segment, 4 loads in flight);
+    // long ones are scanned by the whole warp
+    constexpr int32_t kShort = 64;
+    for (int32_t base = wid * 32; base < nT; base += nwarp * 32) {
+        const int32_t k = base + lane;
+        const bool valid = k < nT;
+        const int32_t w = valid ? T[k] : 0;
+        const int32_t dplus = valid ? g.nplus[w] : 0;
+        if (valid && dplus <= kShort && dplus > 0) {
+            const int tw = type_of_index(ts, L, k);
+            const int64_t rw = g.rp[w];
+            for (int q = 0; q < L; ++q) {
+                int64_t sx = rw + g.pivot[(int64_t)w * L + q];
+                const int64_t se = rw + g.toff[(int64_t)w * (L + 1) + q + 1];
+                unsigned c = 0;
+                for (; sx + 4 <= se; sx += 4) {
+                    const int32_t x0 = g.adj[sx], x1 = g.adj[sx + 1], x2 = g.adj[sx + 2], x3 = g.adj[sx + 3];
+                    c += t_set_has(set, lgcap, x0) + t_set_has(set, lgcap, x1) + t_set_has(set, lgcap, x2) +
+                         t_set_has(set, lgcap, x3);
+                }
+                for (; sx < se; ++sx) c += t_set_has(set, lgcap, g.adj[sx]) ? 1u : 0u;
+                if (c) atomicAdd(&sK[tw * kMaxL + q], c);
+            }
+        }
+        unsigned longs = __ballot_sync(0xffffffffu, valid && dplus > kShort);
+        while (longs) {
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int32_t lw = __shfl_sync(0xffffffffu, w, src);
+            const int ltw = type_of_index(ts, L, base + src);
+            const int64_t rw = g.rp[lw];
+            for (int q = 0; q < L; ++q) {
+                const int64_t sb = rw + g.pivot[(int64_t)lw * L + q];
+                const int64_t se = rw + g.toff[(int64_t)lw * (L + 1) + q + 1];
+                unsigned c = 0;
+                for (int64_t sx = sb + lane; sx < se; sx += 32) c += t_set_has(set, lgcap, g.adj[sx]) ? 1u : 0u;
+                c = warp_sum_u32(c);
+                if (lane == 0 && c) atomicAdd(&sK[ltw * kMaxL + q], c);
+            }
+        }
+    }
+}
+
+// Warp per edge (edges with |T| <= big_t): K into kmat.
+__global__ void __launch_bounds__(256) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
+    __shared__ unsigned sKw[8][kMaxL * kMaxL];
+    __shared__ int32_t setw[8][512];
+    const int L = g.L, LL = L * L;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned *sK = sKw[wid];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
+        const int64_t er = e - e0;
+        const int32_t nT = (int32_t)(cv.toffs[er + 1] - cv.toffs[er]);
+        if (nT > big_t) continue;                           // done by k_clique_big
+        unsigned long long *km = cv.kmat + er * LL;
+        if (nT < 2) {
+            for (int k = lane; k < LL; k += 32) km[k] = 0;
+            continue;
+        }
+        for (int k = lane; k < kMaxL * kMaxL; k += 32) sK[k] = 0;
+        __syncwarp();
+        int32_t ts[kMaxL + 1];
+        t_bounds(cv, L, e, ts);
+        int lg = 1;
+        while ((1 << lg) < 2 * nT) ++lg;
+        clique_pairs(g, cv.tlist + cv.toffs[er], nT, ts, sK, setw[wid], lg, 32, lane);
+        __syncwarp();
+        for (int k = lane; k < LL; k += 32) km[k] = sK[(k / L) * kMaxL + (k % L)];
+        __syncwarp();
+    }
+}
+
+// CTA per edge for the listed edges with a large T; the set of T lives in
+// shared memory up to kBigSetSmem entries, else in this CTA's global slice.
+constexpr int kBigSetSmem = 1 << 12;
+__global__ void __launch_bounds__(256) k_clique_big(GraphView g, CountView cv, int64_t e0,
+                                                   const int32_t *__restrict__ big_list,
+                                                   const unsigned long long *__restrict__ big_count,
+                                                   int32_t *set_scratch, int64_t set_stride) {
+    __shared__ unsigned sK[kMaxL * kMaxL];
+    extern __shared__ int32_t set_smem[];
+    const int L = g.L, LL = L * L;
+    const int64_t nb = (int64_t)*big_count;
+    for (int64_t k = blockIdx.x; k < nb; k += gridDim.x) {
+        const int64_t e = big_list[k];
+        const int64_t er = e - e0;
+        const int32_t nT = (int32_t)(cv.toffs[er + 1] - cv.toffs[er]);
+        for (int x = threadIdx.x; x < kMaxL * kMaxL; x += blockDim.x) sK[x] = 0;
+        __syncthreads();
+        int32_t ts[kMaxL + 1];
+        t_bounds(cv, L, e, ts);
+        int lg = 1;
+        while ((1 << lg) < 2 * nT) ++lg;
+        int32_t *set = (1 << lg) <= kBigSetSmem ? set_smem : set_scratch + (int64_t)blockIdx.x * set_stride;
+        clique_pairs(g, cv.tlist + cv.toffs[er], nT, ts, sK, set, lg, blockDim.x, threadIdx.x);
+        __syncthreads();
+        for (int x = threadIdx.x; x < LL; x += blockDim.x) cv.kmat[er * LL + x] = sK[(x / L) * kMaxL + (x % L)];
+        __syncthreads();
+    }
+}
+
+// value of matrix entry k (0 <= k < L*L) held as (r0 on lane k, or r1 on lane k-32)
+__device__ __forceinline__ long long mat_get(long long r0, long long r1, int k) {
+    const long long v0 = __shfl_sync(0xffffffffu, r0, k & 31);
+    const long long v1 = __shfl_sync(0xffffffffu, r1, k & 31);
+    return k < 32 ? v0 : v1;
+}
+__device__ __forceinline__ long long lane_get(long long v, int t) { return __shfl_sync(0xffffffffu, v, t); }
+
+// Warp per edge: all orbits of Table 3 from the gathered sums (the
+// inclusion-exclusion of Thm. 1 over S_i, S_j, T, I; then Lemmas 1-4).
+// Lane l holds entry k = l (and k = l + 32 when L*L > 32) of each L x L
+// matrix, (x, y) = (k / L, k % L); transposed entries come by shuffle.
+__global__ void __launch_bounds__(256, 3) k_epi4(GraphView g, CountView cv, const Tile *__restrict__ tiles,
+                                             int64_t n_tiles, int64_t row_base, uint32_t *per_edge_out,
+                                             unsigned long long *gacc) {
+    extern __shared__ unsigned long long hist[];
+    const int L = g.L, LL = L * L, P = L * (L + 1) / 2;
     const int G = (int)global_slots(L, 4);
     const int S = (int)per_edge_slots(L, 4);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long *hist = dsm;
-    EdgeWs *wsa = reinterpret_cast<EdgeWs *>(dsm + ((G + 1) & ~1));
-    int32_t *tl = reinterpret_cast<int32_t *>(wsa + kEdgeThreads / 32) + wid * kTCapWarp;
-    EdgeWs &ws = wsa[wid];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int s = threadIdx.x; s < G; s += blockDim.x) hist[s] = 0;
     __syncthreads();
     int cur_graph = -1;
-    auto wbar = []() { __syncwarp(); };
+    const int kA = lane, kB = lane + 32;                     // this lane's matrix entries
+    const int xA = kA / L, yA = kA % L, xB = kB / L, yB = kB % L;
+    const bool hasA = kA < LL, hasB = kB < LL;
+    const int tA = yA * L + xA, tB = yB * L + xB;            // transposed entries
     for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
         const Tile tile = tiles[ti];
         if (tile.graph != cur_graph) {
+            __syncthreads();
             if (cur_graph >= 0) flush_hist(hist, G, gacc, cur_graph, blockDim.x, threadIdx.x);
             __syncthreads();
             cur_graph = tile.graph;
         }
-        for (int64_t e = tile.begin + wid; e < tile.end; e += kEdgeThreads / 32) {
+        for (int64_t e = tile.begin + wid; e < tile.end; e += nwarp) {
+            const int64_t er = e - cv.e_base;
             const int32_t i = g.e_lo[e], j = g.e_hi[e];
-            const int64_t di = g.rp[i + 1] - g.rp[i], dj = g.rp[j + 1] - g.rp[j];
-            if ((di < dj ? di : dj) > light_max) continue;
-            clear_ws(ws, 32, lane);
-            __syncwarp();
-            enumerate_T(g, cv, e, i, j, ws, tl, kTCapWarp, 32, lane, wbar);
-            count_K(g, ws, tl, 32, lane, wbar);
-            uint32_t *row = per_edge_out ? per_edge_out + (e - e_begin) * S : nullptr;
-            edge_epilogue(g, cv, e, i, j, ws, row, hist, 32, lane, wbar);
+            const int p = g.ty[i], q = g.ty[j];
+            // per-type scalars, lane t < L
+            long long c = 0, di = 0, dj = 0;
+            if (lane < L) {
+                c = cv.C[e * L + lane];
+                di = typed_degree(g, i, lane);
+                dj = typed_degree(g, j, lane);
+            }
+            const long long a = di - c - (q == lane ? 1 : 0);  // |S_i^t|
+            const long long b = dj - c - (p == lane ? 1 : 0);  // |S_j^t|
+            // gathered matrices
+            const unsigned long long *sum = cv.tsum + er * 3 * LL;
+            const unsigned long long *km = cv.kmat + er * LL;
+            const int64_t *tau_i = cv.tau + (int64_t)i * LL, *tau_j = cv.tau + (int64_t)j * LL;
+            const int64_t *del_i = g.delta + (int64_t)i * LL, *del_j = g.delta + (int64_t)j * LL;
+            const uint32_t *A = cv.A - cv.a_base;
+            const int64_t sij = g.e_slot_lo[e], sji = g.e_slot_hi[e];
+            long long TCi[2] = {0, 0}, TCj[2] = {0, 0}, DT[2] = {0, 0}, Kd[2] = {0, 0}, Pm[2] = {0, 0};
+            long long ti_[2] = {0, 0}, tj_[2] = {0, 0}, dI[2] = {0, 0}, dJ[2] = {0, 0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool has = h ? hasB : hasA;
+                const int k = h ? kB : kA, x = h ? xB : xA, y = h ? yB : yA;
+                if (has) {
+                    TCi[h] = (long long)sum[k];
+                    TCj[h] = (long long)sum[LL + k];
+                    DT[h] = (long long)sum[2 * LL + k];
+                    Kd[h] = (long long)km[k];
+                    // P[x][y]: slot i->j holds [type next to i][type next to j], slot j->i the reverse
+                    Pm[h] = (long long)A[(int64_t)(y * L + x) * cv.a_stride + sij] +
+                            (long long)A[(int64_t)(x * L + y) * cv.a_stride + sji];
+                    ti_[h] = tau_i[k];
+                    tj_[h] = tau_j[k];
+                    dI[h] = del_i[k];
+                    dJ[h] = del_j[k];
+                }
+            }
+            // Ks = K + K^T
+            long long Ks[2];
+            Ks[0] = Kd[0] + mat_get(Kd[0], Kd[1], hasA ? tA : 0);
+            Ks[1] = Kd[1] + mat_get(Kd[0], Kd[1], hasB ? tB : 0);
+            // CTi, CTj
+            long long CTi[2], CTj[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = h ? xB : xA, y = h ? yB : yA;
+                const long long cx = lane_get(c, x < L ? x : 0);
+                CTi[h] = TCi[h] - Ks[h] - (y == q ? cx : 0);
+                CTj[h] = TCj[h] - Ks[h] - (y == p ? cx : 0);
+            }
+            long long CTiT[2], CTjT[2];
+            CTiT[0] = mat_get(CTi[0], CTi[1], hasA ? tA : 0);
+            CTiT[1] = mat_get(CTi[0], CTi[1], hasB ? tB : 0);
+            CTjT[0] = mat_get(CTj[0], CTj[1], hasA ? tA : 0);
+            CTjT[1] = mat_get(CTj[0], CTj[1], hasB ? tB : 0);
+            // W, Q
+            long long Wi[2], Wj[2], Q[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = h ? xB : xA, y = h ? yB : yA;
+                const long long cx = lane_get(c, x < L ? x : 0), cy = lane_get(c, y < L ? y : 0);
+                Wi[h] = ti_[h] - CTi[h] - CTiT[h] - Ks[h] - (x == q ? cy : 0) - (y == q ? cx : 0);
+                Wj[h] = tj_[h] - CTj[h] - CTjT[h] - Ks[h] - (x == p ? cy : 0) - (y == p ? cx : 0);
+                Q[h] = Pm[h] - CTjT[h] - CTi[h] - Ks[h];
+            }
+            long long QT[2];
+            QT[0] = mat_get(Q[0], Q[1], hasA ? tA : 0);
+            QT[1] = mat_get(Q[0], Q[1], hasB ? tB : 0);
+            // R = Ri + Rj, G8, W = Wi + Wj, CT = CTi + CTj
+            long long R[2], G8[2], W[2], CT[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = h ? xB : xA, y = h ? yB : yA;
+                const long long cx = lane_get(c, x < L ? x : 0);
+                const long long ax = lane_get(a, x < L ? x : 0), bx = lane_get(b, x < L ? x : 0);
+                const long long djy = lane_get(dj, y < L ? y : 0), diy = lane_get(di, y < L ? y : 0);
+                const long long Ri = dI[h] - DT[h] - (x == q ? djy : 0) - (y == p ? ax : 0) - Wi[h] - CTiT[h] - QT[h];
+                const long long Rj = dJ[h] - DT[h] - (x == p ? diy : 0) - (y == q ? bx : 0) - Wj[h] - CTjT[h] - Q[h];
+                R[h] = Ri + Rj;
+                G8[h] = DT[h] - ((y == p ? 1 : 0) + (y == q ? 1 : 0)) * cx - Ks[h] - CTi[h] - CTj[h];
+                W[h] = Wi[h] + Wj[h];
+                CT[h] = CTi[h] + CTj[h];
+            }
+            uint32_t *row = per_edge_out ? per_edge_out + (e - row_base) * S : nullptr;
+            // 3-node slots, typed edge and 3-node global blocks
+            if (lane < L) {
+                const long long s3 = a + b;
+                if (a < 0 || b < 0) set_status(cv.status, ST_INTERNAL);
+                if (row) {
+                    row[lane] = sat32(s3, cv.status);
+                    row[L + lane] = sat32(c, cv.status);
+                }
+                int ms[3] = {p, q, lane};
+                sort3(ms);
+                const int r = multiset_rank_dev(L, 3, ms);
+                if (s3) atomicAdd(&hist[gblock_off(L, 1) + r], (unsigned long long)s3);
+                if (c) atomicAdd(&hist[gblock_off(L, 2) + r], (unsigned long long)c);
+            }
+            if (lane == 0) {
+                int ms[2] = {p < q ? p : q, p < q ? q : p};
+                atomicAdd(&hist[multiset_rank_dev(L, 2, ms)], 1ull);
+            }
+            // orbits, one type pair (t <= u) per lane (two rounds when P > 32)
+            for (int base = 0; base < P; base += 32) {
+                const int pi = base + lane;
+                int t = 0;
+                if (pi < P)
+                    while (pair_idx(L, t, L - 1) < pi) ++t;
+                const int u = pi < P ? t + (pi - pair_idx(L, t, t)) : 0;
+                const int ktu = t * L + u, kut = u * L + t;
+                const long long Rtu = mat_get(R[0], R[1], ktu), Rut = mat_get(R[0], R[1], kut);
+                const long long Qtu = mat_get(Q[0], Q[1], ktu), Qut = mat_get(Q[0], Q[1], kut);
+                const long long Wtu = mat_get(W[0], W[1], ktu);
+                const long long Gtu = mat_get(G8[0], G8[1], ktu), Gut = mat_get(G8[0], G8[1], kut);
+                const long long CTtu = mat_get(CT[0], CT[1], ktu), CTut = mat_get(CT[0], CT[1], kut);
+                const long long Ktu = mat_get(Ks[0], Ks[1], ktu);
+                const long long at = lane_get(a, t), au = lane_get(a, u), bt = lane_get(b, t), bu = lane_get(b, u);
+                const long long ct = lane_get(c, t), cu = lane_get(c, u);
+                if (pi >= P) continue;
+                long long gv[10];
+                bool ok = true;
+                if (t != u) {
+                    gv[0] = Rtu + Rut;                                 // g3
+                    gv[3] = Qtu + Qut;                                 // g6
+                    gv[4] = Wtu;                                       // g7
+                    gv[5] = Gtu + Gut;                                 // g8
+                    gv[7] = CTtu + CTut;                               // g10
+                    gv[9] = Ktu;                                       // g12
+                    gv[1] = at * bu + au * bt - gv[3];                 // Lemma 1
+                    gv[2] = at * au + bt * bu - gv[4];                 // Lemma 2
+                    gv[6] = ct * (au + bu) + cu * (at + bt) - gv[7];   // Lemma 3
+                    gv[8] = ct * cu - gv[9];                           // Lemma 4
+                } else {
+                    ok = !(Wtu & 1) && !(Ktu & 1);
+                    gv[0] = Rtu;
+                    gv[3] = Qtu;
+                    gv[4] = Wtu / 2;
+                    gv[5] = Gtu;
+                    gv[7] = CTtu;
+                    gv[9] = Ktu / 2;
+                    gv[1] = at * bt - gv[3];
+                    gv[2] = at * (at - 1) / 2 + bt * (bt - 1) / 2 - gv[4];
+                    gv[6] = ct * (at + bt) - gv[7];
+                    gv[8] = ct * (ct - 1) / 2 - gv[9];
+                }
+                int ms[4] = {p, q, t, u};
+                sort4(ms);
+                const int r = multiset_rank_dev(L, 4, ms);
+                for (int o = 3; o <= 12; ++o) {
+                    const long long v = gv[o - 3];
+                    ok = ok && v >= 0;
+                    if (row) row[2 * L + (o - 3) * P + pi] = sat32(v, cv.status);
+                    if (v > 0) atomicAdd(&hist[gblock_off(L, graphlet_block(o)) + r], (unsigned long long)v);
+                }
+                if (!ok) set_status(cv.status, ST_INTERNAL);
+            }
         }
-        __syncthreads();
-    }
-    if (cur_graph >= 0) flush_hist(hist, G, gacc, cur_graph, blockDim.x, threadIdx.x);
-}
-
-// Heavy edges: one CTA per edge (the list is sorted by cost, largest first).
-// T lives in shared memory when it fits, else in this CTA's global slice.
-__global__ void __launch_bounds__(kHeavyThreads, 2) k_edge4_heavy(GraphView g, CountView cv, const int32_t *__restrict__ list,
-                                                              int64_t n_list, int64_t e_begin, int64_t e_end,
-                                                              int64_t row_base, uint32_t *per_edge_out,
-                                                              unsigned long long *gacc, int32_t *tscratch,
-                                                              int64_t tscratch_stride) {
-    extern __shared__ unsigned long long dsm[];
-    const int L = g.L;
-    const int G = (int)global_slots(L, 4);
-    const int S = (int)per_edge_slots(L, 4);
-    unsigned long long *hist = dsm;
-    EdgeWs &ws = *reinterpret_cast<EdgeWs *>(dsm + ((G + 1) & ~1));
-    int32_t *tl_smem = reinterpret_cast<int32_t *>(&ws + 1);
-    for (int s = threadIdx.x; s < G; s += blockDim.x) hist[s] = 0;
-    __syncthreads();
-    auto bbar = []() { __syncthreads(); };
-    int cur_graph = -1;
-    for (int64_t k = blockIdx.x; k < n_list; k += gridDim.x) {
-        const int64_t e = list[k];
-        if (e < e_begin || e >= e_end) continue;
-        const int graph = graph_of_edge(g, e);
-        if (graph != cur_graph) {
-            if (cur_graph >= 0) flush_hist(hist, G, gacc, cur_graph, blockDim.x, threadIdx.x);
-            __syncthreads();
-            cur_graph = graph;
-        }
-        const int32_t i = g.e_lo[e], j = g.e_hi[e];
-        const int64_t di = g.rp[i + 1] - g.rp[i], dj = g.rp[j + 1] - g.rp[j];
-        const int64_t cap = di < dj ? di : dj;
-        int32_t *tl = cap <= kTCapSmemHeavy ? tl_smem : tscratch + (int64_t)blockIdx.x * tscratch_stride;
-        clear_ws(ws, blockDim.x, threadIdx.x);
-        __syncthreads();
-        enumerate_T(g, cv, e, i, j, ws, tl, cap, blockDim.x, threadIdx.x, bbar);
-        count_K(g, ws, tl, blockDim.x, threadIdx.x, bbar);
-        uint32_t *row = per_edge_out ? per_edge_out + (e - row_base) * S : nullptr;
-        edge_epilogue(g, cv, e, i, j, ws, row, hist, blockDim.x, threadIdx.x, bbar);
     }
     __syncthreads();
     if (cur_graph >= 0) flush_hist(hist, G, gacc, cur_graph, blockDim.x, threadIdx.x);
@@ -989,8 +957,13 @@ static std::vector<Tile> make_tiles(const Graph &G, int64_t e_begin, int64_t e_e
 // its own), and sizes the array for the largest chunk.
 static void plan_chunks(Graph &G) {
     G.chunks.clear();
-    const int64_t per_slot = (int64_t)G.L * G.L * (int64_t)sizeof(uint32_t);
-    const int64_t max_slots = std::max<int64_t>(((int64_t)G.opt.cycle_budget_mb << 20) / per_slot, 1);
+    // working bytes of a chunk: the 4-cycle array (4 L^2 per slot) and the
+    // per-edge sums, K and offsets (32 L^2 + 28 per edge)
+    const int64_t LL = (int64_t)G.L * G.L;
+    const int64_t budget = std::max<int64_t>((int64_t)G.opt.cycle_budget_mb << 20, 1);
+    auto bytes_of = [&](int a, int b) {
+        return (G.h_slot_off[b] - G.h_slot_off[a]) * 4 * LL + (G.h_edge_off[b] - G.h_edge_off[a]) * (32 * LL + 28);
+    };
     // tile index ranges follow graph boundaries (make_tiles emits graph after graph)
     std::vector<int64_t> tile_off(G.ngraphs + 1, 0);
     for (int gi = 0; gi < G.ngraphs; ++gi)
@@ -999,7 +972,7 @@ static void plan_chunks(Graph &G) {
     int64_t widest = 0;
     while (g0 < G.ngraphs) {
         int g1 = g0 + 1;
-        while (g1 < G.ngraphs && G.h_slot_off[g1 + 1] - G.h_slot_off[g0] <= max_slots) ++g1;
+        while (g1 < G.ngraphs && bytes_of(g0, g1 + 1) <= budget) ++g1;
         Graph::Chunk c;
         c.g0 = g0; c.g1 = g1;
         c.n0 = G.h_node_off[g0]; c.n1 = G.h_node_off[g1];
@@ -1007,42 +980,14 @@ static void plan_chunks(Graph &G) {
         c.e0 = G.h_edge_off[g0]; c.e1 = G.h_edge_off[g1];
         c.t0 = tile_off[g0]; c.t1 = tile_off[g1];
         widest = std::max(widest, c.s1 - c.s0);
+        G.max_chunk_edges = std::max(G.max_chunk_edges, c.e1 - c.e0);
         G.chunks.push_back(c);
         g0 = g1;
     }
     G.a_stride = std::max<int64_t>(widest, 1);
 }
 
-// Allocates the working arrays of a count with this k (kept by the handle).
-void prepare_counting(Graph &G, int k, cudaStream_t s) {
-    const int L = G.L;
-    const size_t m = (size_t)std::max<int64_t>(G.m, 1), n = (size_t)std::max<int64_t>(G.n, 1);
-    if (G.C.bytes < m * L * sizeof(uint32_t)) G.C.alloc(m * L * sizeof(uint32_t));
-    if (G.tau.bytes < n * L * L * sizeof(int64_t)) G.tau.alloc(n * L * L * sizeof(int64_t));
-    const size_t gbytes = (size_t)G.ngraphs * global_slots(L, 4) * sizeof(unsigned long long);
-    if (G.gacc.bytes < gbytes) G.gacc.alloc(gbytes);
-    if (k == 4) {
-        if (G.chunks.empty()) plan_chunks(G);
-        const size_t ab = (size_t)G.a_stride * L * L * sizeof(uint32_t);
-        if (G.A.bytes < ab) G.A.alloc(ab);
-        if (G.n_anchors_heavy > 0 && G.n_tables == 0) {
-            const int64_t stride = std::max<int64_t>(G.max_graph_nodes, 1) * L;
-            const int64_t per = stride * (int64_t)sizeof(uint32_t);
-            int64_t budget = (int64_t)G.opt.anchor_table_budget_mb << 20;
-            int64_t nt = std::min<int64_t>({(int64_t)2 * sm_count(), G.n_anchors_heavy, std::max<int64_t>(budget / per, 1)});
-            G.tables.alloc((size_t)(nt * per));
-            TG_CK(cudaMemsetAsync(G.tables.p, 0, (size_t)(nt * per), s));
-            G.table_stride = stride;
-            G.n_tables = (int32_t)nt;
-        }
-    }
-}
-
 static size_t hist_bytes(int L, int k) { return (size_t)((global_slots(L, k) + 1) & ~1) * sizeof(unsigned long long); }
-static size_t light_smem(int L) {
-    return hist_bytes(L, 4) + (kEdgeThreads / 32) * (sizeof(EdgeWs) + kTCapWarp * sizeof(int32_t));
-}
-static size_t heavy_smem(int L) { return hist_bytes(L, 4) + sizeof(EdgeWs) + kTCapSmemHeavy * sizeof(int32_t); }
 
 // Device tile list of [e_begin, e_end); the full range is cached by the
 // handle (so that a captured CUDA graph never copies from host memory).
@@ -1064,18 +1009,29 @@ static const Tile *tiles_for(Graph &G, int64_t e_begin, int64_t e_end, int64_t &
     return dst.as<Tile>();
 }
 
+// |T_e| summed over the edges of each chunk (from c_e^t)
+__global__ void k_chunk_t(GraphView g, CountView cv, int64_t e0, int64_t e1, unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x)
+        for (int t = 0; t < g.L; ++t) acc += cv.C[e * g.L + t];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
 // Allocations and kernel attributes of the per-edge stage (done before any
 // capture).
 void prepare_edges(Graph &G, int k, cudaStream_t s) {
     TG_CK(cudaFuncSetAttribute(k_edge3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes(G.L, 3)));
-    TG_CK(cudaFuncSetAttribute(k_edge4_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)light_smem(G.L)));
-    TG_CK(cudaFuncSetAttribute(k_edge4_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heavy_smem(G.L)));
-    if (k == 4 && G.n_edges_heavy > 0 && !G.tscratch.p) {
-        const int64_t nblk = std::min<int64_t>(G.n_edges_heavy, (int64_t)sm_count() * 2);
-        const int64_t stride = std::max<int64_t>(G.max_degree, 1);
-        G.tscratch.alloc(sizeof(int32_t) * (size_t)(stride * nblk));
-        G.tscratch_stride = stride;
-        G.tscratch_blocks = (int32_t)nblk;
+    TG_CK(cudaFuncSetAttribute(k_epi4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes(G.L, 4)));
+    TG_CK(cudaFuncSetAttribute(k_clique_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kBigSetSmem * sizeof(int32_t))));
+    if (k == 4 && !G.set_scratch.p) {
+        // a set of capacity >= 2 max degree per CTA, for edges whose T exceeds shared memory
+        int64_t cap = 1;
+        while (cap < 2 * std::max<int64_t>(G.max_degree, 1)) cap <<= 1;
+        G.big_blocks = sm_count() * 8;
+        G.set_stride = cap > kBigSetSmem ? cap : 1;
+        G.set_scratch.alloc(sizeof(int32_t) * (size_t)(G.set_stride * G.big_blocks));
     }
     DBuf unused;
     int64_t nt = 0;
@@ -1108,6 +1064,33 @@ static int64_t launch_triangles(Graph &G, cudaStream_t s) {
     return launches;
 }
 
+// Triangle-node entries of every chunk (a graph invariant, computed once
+// after the first k_tri; synchronises) and the T list buffer sized for the
+// largest chunk.
+static void ensure_t_sizes(Graph &G, cudaStream_t s) {
+    if (!G.chunk_t.empty()) return;
+    TBuf cnt(sizeof(unsigned long long) * G.chunks.size(), s);
+    TG_CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * G.chunks.size(), s));
+    const GraphView gv = G.view();
+    const CountView cv = G.cview();
+    for (size_t x = 0; x < G.chunks.size(); ++x) {
+        const Graph::Chunk &c = G.chunks[x];
+        if (c.e1 > c.e0)
+            k_chunk_t<<<grid_for(c.e1 - c.e0, 256, sm_count() * 8), 256, 0, s>>>(gv, cv, c.e0, c.e1,
+                                                                               cnt.as<unsigned long long>() + x);
+    }
+    TG_CK(cudaGetLastError());
+    std::vector<unsigned long long> h(G.chunks.size());
+    TG_CK(cudaMemcpyAsync(h.data(), cnt.p, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaStreamSynchronize(s));
+    G.chunk_t.assign(h.begin(), h.end());
+    const int64_t cap = std::max<int64_t>(*std::max_element(G.chunk_t.begin(), G.chunk_t.end()), 1);
+    if (G.tlist_cap < cap) {
+        G.tlist.alloc(sizeof(int32_t) * (size_t)cap);
+        G.tlist_cap = cap;
+    }
+}
+
 // degree-priority wedges of the anchors of one chunk into A
 static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
     G.a_base = c.s0;
@@ -1138,36 +1121,101 @@ static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
     return launches;
 }
 
-// per-edge stage of edges [e_begin, e_end) given as tiles (inside one chunk for k = 4)
-static int64_t launch_edge_tiles(Graph &G, int k, const Tile *tiles, int64_t n_tiles, int64_t e_begin, int64_t e_end,
-                                 int64_t row_base, uint32_t *per_edge_out, unsigned long long *gacc, cudaStream_t s) {
-    if (n_tiles <= 0) return 0;
+// per-edge 4-node stage of edges [b, e) (inside one chunk, whose wedge pass
+// is in A): T offsets, T lists and sums, K, orbits
+static int64_t launch_edges4(Graph &G, int64_t b, int64_t e, const Tile *tiles, int64_t n_tiles, int64_t row_base,
+                             uint32_t *per_edge_out, unsigned long long *gacc, cudaStream_t s) {
+    if (e <= b) return 0;
+    G.e_base = b;
     const GraphView gv = G.view();
     const CountView cv = G.cview();
     const int sms = sm_count();
+    const int64_t ne = e - b;
+    const int64_t big_t = std::max<int64_t>(G.opt.light_edge_max_degree, 32);
     int64_t launches = 0;
-    if (k == 3) {
-        KernelTimer kt(G, s, "k_edge3");
-        k_edge3<<<grid_for(n_tiles, 1, sms * 8), 256, hist_bytes(G.L, 3), s>>>(gv, cv, tiles, n_tiles, row_base,
-                                                                                per_edge_out, gacc);
+    TG_CK(cudaMemsetAsync(G.big_count.p, 0, sizeof(unsigned long long), s));
+    {
+        KernelTimer kt(G, s, "k_tcount");
+        k_tcount<<<grid_for(ne + 1, 256, 1 << 30), 256, 0, s>>>(gv, cv, b, e, big_t, G.tcount.as<int64_t>(),
+                                                                G.big_list.as<int32_t>(),
+                                                                G.big_count.as<unsigned long long>());
         ++launches;
-    } else {
-        {
-            KernelTimer kt(G, s, "k_edge4_light");
-            k_edge4_light<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), kEdgeThreads, light_smem(G.L), s>>>(
-                gv, cv, tiles, n_tiles, G.opt.light_edge_max_degree, row_base, per_edge_out, gacc);
-            ++launches;
-        }
-        if (G.n_edges_heavy > 0) {
-            KernelTimer kt(G, s, "k_edge4_heavy");
-            k_edge4_heavy<<<G.tscratch_blocks, kHeavyThreads, heavy_smem(G.L), s>>>(
-                gv, cv, G.edges_heavy.as<int32_t>(), G.n_edges_heavy, e_begin, e_end, row_base, per_edge_out, gacc,
-                G.tscratch.as<int32_t>(), G.tscratch_stride);
-            ++launches;
-        }
+    }
+    size_t tmp_bytes = G.scan_tmp_bytes;
+    TG_CK(cub::DeviceScan::ExclusiveSum(G.scan_tmp.p, tmp_bytes, G.tcount.as<int64_t>(), G.toffs.as<int64_t>(),
+                                        ne + 1, s));
+    {
+        KernelTimer kt(G, s, "k_tsum");
+        k_tsum<<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e);
+        ++launches;
+    }
+    {
+        KernelTimer kt(G, s, "k_clique");
+        k_clique<<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e, big_t);
+        ++launches;
+    }
+    {
+        KernelTimer kt(G, s, "k_clique_big");
+        k_clique_big<<<G.big_blocks, 256, kBigSetSmem * sizeof(int32_t), s>>>(
+            gv, cv, b, G.big_list.as<int32_t>(), G.big_count.as<unsigned long long>(), G.set_scratch.as<int32_t>(),
+            G.set_stride);
+        ++launches;
+    }
+    if (n_tiles > 0) {
+        KernelTimer kt(G, s, "k_epi4");
+        k_epi4<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), 256, hist_bytes(G.L, 4), s>>>(
+            gv, cv, tiles, n_tiles, row_base, per_edge_out, gacc);
+        ++launches;
     }
     TG_CK(cudaGetLastError());
     return launches;
+}
+
+// Allocates the working arrays of a count with this k (kept by the handle).
+void prepare_counting(Graph &G, int k, cudaStream_t s) {
+    const int L = G.L;
+    const size_t m = (size_t)std::max<int64_t>(G.m, 1), n = (size_t)std::max<int64_t>(G.n, 1);
+    if (G.C.bytes < m * L * sizeof(uint32_t)) G.C.alloc(m * L * sizeof(uint32_t));
+    if (G.tau.bytes < n * L * L * sizeof(int64_t)) G.tau.alloc(n * L * L * sizeof(int64_t));
+    const size_t gbytes = (size_t)G.ngraphs * global_slots(L, 4) * sizeof(unsigned long long);
+    if (G.gacc.bytes < gbytes) G.gacc.alloc(gbytes);
+    if (k == 4) {
+        if (G.chunks.empty()) plan_chunks(G);
+        const size_t ab = (size_t)G.a_stride * L * L * sizeof(uint32_t);
+        if (G.A.bytes < ab) G.A.alloc(ab);
+        const size_t me = (size_t)std::max<int64_t>(G.max_chunk_edges, 1);
+        if (G.tcount.bytes < (me + 1) * sizeof(int64_t)) {
+            G.tcount.alloc((me + 1) * sizeof(int64_t));
+            G.toffs.alloc((me + 1) * sizeof(int64_t));
+            G.tsum.alloc(me * 3 * L * L * sizeof(unsigned long long));
+            G.kmat.alloc(me * L * L * sizeof(unsigned long long));
+            G.big_list.alloc(me * sizeof(int32_t));
+            G.big_count.alloc(sizeof(unsigned long long));
+            size_t tb = 0;
+            TG_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, G.tcount.as<int64_t>(), G.toffs.as<int64_t>(),
+                                                (int64_t)me + 1, s));
+            G.scan_tmp.alloc(tb);
+            G.scan_tmp_bytes = tb;
+        }
+        if (G.n_anchors_heavy > 0 && G.n_tables == 0) {
+            const int64_t stride = std::max<int64_t>(G.max_graph_nodes, 1) * L;
+            const int64_t per = stride * (int64_t)sizeof(uint32_t);
+            int64_t budget = (int64_t)G.opt.anchor_table_budget_mb << 20;
+            int64_t nt = std::min<int64_t>({(int64_t)2 * sm_count(), G.n_anchors_heavy, std::max<int64_t>(budget / per, 1)});
+            G.tables.alloc((size_t)(nt * per));
+            TG_CK(cudaMemsetAsync(G.tables.p, 0, (size_t)(nt * per), s));
+            G.table_stride = stride;
+            G.n_tables = (int32_t)nt;
+        }
+    }
+}
+
+// For a captured count: the T list size needs one k_tri before capture.
+void prepare_capture(Graph &G, int k, cudaStream_t s) {
+    if (k == 4 && G.chunk_t.empty()) {
+        launch_triangles(G, s);
+        ensure_t_sizes(G, s);
+    }
 }
 
 int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out, unsigned long long *gacc,
@@ -1175,15 +1223,26 @@ int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per
     int64_t launches = 0;
     if (full || G.prepared_k < 3) {
         launches += launch_triangles(G, s);
-        G.prepared_k = 3;
+        G.prepared_k = std::max(G.prepared_k, 3);
     }
     DBuf tmp;
     int64_t n_tiles = 0;
     const Tile *tiles = tiles_for(G, e_begin, e_end, n_tiles, tmp, s);
     if (k == 3) {
-        launches += launch_edge_tiles(G, 3, tiles, n_tiles, e_begin, e_end, e_begin, per_edge_out, gacc, s);
+        if (n_tiles > 0) {
+            const GraphView gv = G.view();
+            const CountView cv = G.cview();
+            KernelTimer kt(G, s, "k_edge3");
+            k_edge3<<<grid_for(n_tiles, 1, sm_count() * 8), 256, hist_bytes(G.L, 3), s>>>(gv, cv, tiles, n_tiles, e_begin,
+                                                                                       per_edge_out, gacc);
+            ++launches;
+            TG_CK(cudaGetLastError());
+        }
     } else {
+        ensure_t_sizes(G, s);
         const bool whole = e_begin == 0 && e_end == G.m;
+        std::vector<Tile> host;
+        if (!whole) host = make_tiles(G, e_begin, e_end);
         for (const Graph::Chunk &c : G.chunks) {
             const int64_t b = std::max(e_begin, c.e0), e = std::min(e_end, c.e1);
             if (b >= e) continue;
@@ -1199,16 +1258,14 @@ int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per
                 ct = tiles + c.t0;
                 nct = c.t1 - c.t0;
             } else {
-                // tiles of an arbitrary range: the kernel skips none; pick this chunk's part
-                int64_t a = 0, z = n_tiles;
-                std::vector<Tile> host = make_tiles(G, e_begin, e_end);
-                while (a < z && host[a].end <= b) ++a;
+                int64_t a = 0;
+                while (a < n_tiles && host[a].end <= b) ++a;
                 int64_t y = a;
-                while (y < z && host[y].begin < e) ++y;
+                while (y < n_tiles && host[y].begin < e) ++y;
                 ct = tiles + a;
                 nct = y - a;
             }
-            launches += launch_edge_tiles(G, 4, ct, nct, b, e, e_begin, per_edge_out, gacc, s);
+            launches += launch_edges4(G, b, e, ct, nct, e_begin, per_edge_out, gacc, s);
         }
     }
     if (tmp.p) TG_CK(cudaStreamSynchronize(s));

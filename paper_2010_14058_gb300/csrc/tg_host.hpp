@@ -86,14 +86,19 @@ struct Graph {
     tg_options opt;
 
     // graph (built once)
-    DBuf node_off, edge_off, rp, adj, toff, pivot, ty, old_of, slot_eid, e_lo, e_hi, e_slot_lo, e_slot_hi, delta;
+    DBuf node_off, edge_off, rp, adj, toff, pivot, nplus, ty, old_of, slot_eid, e_lo, e_hi, e_slot_lo, e_slot_hi, delta;
     // work lists
     DBuf anchors_light, anchors_heavy, edges_light, edges_heavy;
     int64_t n_anchors_light = 0, n_anchors_heavy = 0, n_edges_light = 0, n_edges_heavy = 0;
     // counting state
-    DBuf C, tau, A, tables, gacc, status, tiles_full, tscratch, stage_pe, stage_gl;
-    int64_t n_tiles_full = 0, tscratch_stride = 0;
-    int32_t tscratch_blocks = 0;
+    DBuf C, tau, A, tables, gacc, status, tiles_full, stage_pe, stage_gl;
+    DBuf tcount, toffs, tlist, tsum, kmat, big_list, big_count, scan_tmp, set_scratch;
+    int64_t set_stride = 1;
+    int32_t big_blocks = 1;
+    int64_t n_tiles_full = 0, max_chunk_edges = 0, tlist_cap = 0;
+    size_t scan_tmp_bytes = 0;
+    std::vector<int64_t> chunk_t;       // triangle-node entries per chunk (graph invariant)
+    int64_t e_base = 0;
     int64_t table_stride = 0;
     int32_t n_tables = 0;
     int32_t prepared_k = 0;             // 0: nothing, 3: C and tau, 4: C, tau and A
@@ -119,6 +124,7 @@ struct Graph {
         v.adj = adj.as<int32_t>();
         v.toff = toff.as<int32_t>();
         v.pivot = pivot.as<int32_t>();
+        v.nplus = nplus.as<int32_t>();
         v.ty = ty.as<uint8_t>();
         v.slot_eid = slot_eid.as<int32_t>();
         v.e_lo = e_lo.as<int32_t>();
@@ -135,6 +141,11 @@ struct Graph {
         c.A = A.as<uint32_t>();
         c.a_base = a_base;
         c.a_stride = a_stride;
+        c.e_base = e_base;
+        c.toffs = toffs.as<int64_t>();
+        c.tlist = tlist.as<int32_t>();
+        c.tsum = tsum.as<unsigned long long>();
+        c.kmat = kmat.as<unsigned long long>();
         c.tables = tables.as<uint32_t>();
         c.table_stride = table_stride;
         c.gacc = gacc.as<unsigned long long>();
@@ -142,10 +153,11 @@ struct Graph {
         return c;
     }
     int64_t device_bytes() const {
-        const DBuf *all[] = {&node_off, &edge_off, &rp, &adj, &toff, &pivot, &ty, &old_of, &slot_eid, &e_lo, &e_hi,
+        const DBuf *all[] = {&node_off, &edge_off, &rp, &adj, &toff, &pivot, &nplus, &ty, &old_of, &slot_eid, &e_lo, &e_hi,
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
-                             &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &tscratch,
-                             &stage_pe, &stage_gl};
+                             &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
+                             &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
+                             &set_scratch};
         int64_t s = 0;
         for (const DBuf *b : all) s += (int64_t)b->bytes;
         return s;
@@ -204,6 +216,7 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
 // count entries (tg_count.cu)
 void prepare_counting(Graph &G, int k, cudaStream_t s);
 void prepare_edges(Graph &G, int k, cudaStream_t s);
+void prepare_capture(Graph &G, int k, cudaStream_t s);
 // Runs the counting stages for edges [e_begin, e_end) into per_edge_out
 // (row 0 = e_begin) and the raw sums gacc.  full: the whole graph, every
 // stage recomputed (no cached state).  Returns the kernel launches.

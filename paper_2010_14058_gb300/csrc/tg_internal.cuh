@@ -42,6 +42,7 @@ struct GraphView {
     const int32_t *adj;        // [nnz] internal ids, rows sorted by (type, id)
     const int32_t *toff;       // [n*(L+1)] type segment starts, relative to rp[x]
     const int32_t *pivot;      // [n*L] first slot of segment (x,t) with id > x, relative to rp[x]
+    const int32_t *nplus;      // [n] neighbours of higher priority (id > x)
     const uint8_t *ty;         // [n] node type by internal id
     const int32_t *slot_eid;   // [nnz] edge id of each adjacency slot
     const int32_t *e_lo;       // [m] internal endpoint with the smaller id
@@ -58,6 +59,11 @@ struct CountView {
     uint32_t *A;                // [L*L][a_stride] 4-cycle contributions per slot of the current chunk
     int64_t a_base;             // first adjacency slot of the current chunk
     int64_t a_stride;           // slots per type-pair row of A
+    int64_t e_base;             // first edge of the current range (per-edge arrays are relative to it)
+    int64_t *toffs;             // [edges + 1] T list offsets of the range
+    int32_t *tlist;             // T lists of the range, each sorted by (type, id)
+    unsigned long long *tsum;   // [edges][3][L*L] TCi, TCj, DT
+    unsigned long long *kmat;   // [edges][L*L] adjacent pairs inside T, (smaller id type, larger id type)
     uint32_t *tables;           // dense per-CTA wedge tables
     int64_t table_stride;       // entries (uint32) per CTA table
     unsigned long long *gacc;   // [ngraphs*G] raw per-graphlet edge sums
