@@ -218,6 +218,13 @@ tg_status tg_query_status(tg_graph *g);
 /* Static description of a status code. */
 const char *tg_status_string(tg_status s);
 
+/* Text of the calling host thread's most recent failed call into this
+ * library: the failing step and, for TG_ERR_CUDA / TG_ERR_OOM, the CUDA
+ * runtime's error string.  Thread-local storage owned by the library; valid
+ * until the thread's next failed call; "" if none failed yet.  Diagnostic
+ * only (the paper has no counterpart). */
+const char *tg_last_error(void);
+
 /* Number of this library's own kernel launches (not counting the CUB
  * primitives the build sorts with) issued by the last tg_build /
  * tg_build_batch, tg_count, tg_count_range or tg_count_batch call on this

@@ -20,10 +20,15 @@ tg_status guarded(F f) {
         f();
         return TG_OK;
     } catch (const Error &e) {
+        if (!e.from_cuda)
+            std::snprintf(tg::tl_last_error, sizeof tg::tl_last_error, "%s: %s", e.what ? e.what : "",
+                          tg_status_string(e.status));
         return e.status;
     } catch (const std::bad_alloc &) {
+        std::snprintf(tg::tl_last_error, sizeof tg::tl_last_error, "host allocation failed");
         return TG_ERR_OOM;
     } catch (...) {
+        std::snprintf(tg::tl_last_error, sizeof tg::tl_last_error, "unexpected exception");
         return TG_ERR_INTERNAL;
     }
 }
@@ -70,6 +75,7 @@ void build_common(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t n
         tg::build_graph(h->g, ngraphs, node_off, n, nnz, row_ptr, col, types, L, o, (cudaStream_t)stream);
     } catch (...) {
         cudaStreamSynchronize((cudaStream_t)stream);
+        h->g.stream = nullptr;
         delete h;
         throw;
     }
@@ -138,6 +144,7 @@ tg_status tg_build_batch(int32_t ngraphs, const int64_t *node_off, int64_t n, in
 void tg_free(tg_graph *g) {
     if (!g) return;
     cudaStreamSynchronize(g->g.stream);
+    g->g.stream = nullptr;          // release on the legacy stream: the caller's may be gone later
     delete g;
 }
 
@@ -348,6 +355,8 @@ tg_status tg_query_status(tg_graph *gh) {
     if (v & tg::ST_OVERFLOW) return TG_ERR_OVERFLOW;
     return TG_OK;
 }
+
+const char *tg_last_error(void) { return tg::tl_last_error; }
 
 const char *tg_status_string(tg_status s) {
     switch (s) {

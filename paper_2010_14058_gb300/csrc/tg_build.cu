@@ -13,6 +13,8 @@
 //   * work lists: wedge anchors by wedge count, edges by min endpoint degree.
 // Sorting and compaction use CUB device primitives.
 #include <algorithm>
+#include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include <cub/device/device_radix_sort.cuh>
@@ -348,6 +350,26 @@ uint32_t read_status(const DBuf &st, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaMemPool_t device_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    TG_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error{TG_ERR_INVALID_ARG, "device index"};
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        TG_CK(cudaMemPoolCreate(&pools[dev], &props));
+        uint64_t keep = UINT64_MAX;
+        TG_CK(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    return pools[dev];
+}
 
 int sm_count() {
     static int cached = 0;

@@ -41,6 +41,8 @@
 
 #include <cub/device/device_scan.cuh>
 
+#include <mutex>
+
 #include "tg_host.hpp"
 
 namespace tg {
@@ -1018,13 +1020,28 @@ __global__ void k_chunk_t(GraphView g, CountView cv, int64_t e0, int64_t e1, uns
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
+void raise_smem_limit(const void *func, size_t bytes) {
+    struct Limit { const void *func; int dev; size_t bytes; };
+    static std::mutex mu;
+    static std::vector<Limit> set;
+    int dev = 0;
+    TG_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    Limit *hit = nullptr;
+    for (auto &l : set)
+        if (l.func == func && l.dev == dev) hit = &l;
+    if (hit && hit->bytes >= bytes) return;
+    TG_CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (hit) hit->bytes = bytes;
+    else set.push_back({func, dev, bytes});
+}
+
 // Allocations and kernel attributes of the per-edge stage (done before any
 // capture).
 void prepare_edges(Graph &G, int k, cudaStream_t s) {
-    TG_CK(cudaFuncSetAttribute(k_edge3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes(G.L, 3)));
-    TG_CK(cudaFuncSetAttribute(k_epi4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes(G.L, 4)));
-    TG_CK(cudaFuncSetAttribute(k_clique_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kBigSetSmem * sizeof(int32_t))));
+    raise_smem_limit((const void *)k_edge3, hist_bytes(G.L, 3));
+    raise_smem_limit((const void *)k_epi4, hist_bytes(G.L, 4));
+    raise_smem_limit((const void *)k_clique_big, kBigSetSmem * sizeof(int32_t));
     if (k == 4 && !G.set_scratch.p) {
         // a set of capacity >= 2 max degree per CTA, for edges whose T exceeds shared memory
         int64_t cap = 1;
@@ -1040,7 +1057,7 @@ void prepare_edges(Graph &G, int k, cudaStream_t s) {
         int cap = 1;
         while (cap < 2 * G.opt.light_anchor_max_wedges) cap <<= 1;
         const size_t smem = (size_t)kLightAnchorWarps * cap * (1 + G.L) * sizeof(int32_t);
-        TG_CK(cudaFuncSetAttribute(k_wedge_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        raise_smem_limit((const void *)k_wedge_light, smem);
     }
 }
 

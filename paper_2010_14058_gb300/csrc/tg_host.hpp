@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -17,20 +18,40 @@ namespace tg {
 struct Error {
     tg_status status;
     const char *what;
+    bool from_cuda = false;     // message already recorded by throw_cuda
 };
+
+// Text of the calling thread's last failed entry (tg_last_error).
+inline thread_local char tl_last_error[256] = "";
 
 inline void throw_cuda(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return;
     (void)cudaGetLastError();   // clear the sticky-free error state
-    throw Error{e == cudaErrorMemoryAllocation ? TG_ERR_OOM : TG_ERR_CUDA, what};
+    std::snprintf(tl_last_error, sizeof tl_last_error, "%s: %s", what, cudaGetErrorString(e));
+    throw Error{e == cudaErrorMemoryAllocation ? TG_ERR_OOM : TG_ERR_CUDA, what, true};
 }
+
+// Raises (never lowers) a kernel's dynamic shared-memory limit.  The limit
+// is a process-wide attribute of the function, so handles counted
+// concurrently on several host threads must not shrink it under one another.
+// Defined in tg_count.cu.
+void raise_smem_limit(const void *func, size_t bytes);
 
 #define TG_CK(call) ::tg::throw_cuda((call), #call)
 
+// Stream-ordered memory pool of the current device, owned by the library
+// (release threshold kept at its maximum, so freed blocks are reused instead
+// of returned to the driver).  Defined in tg_build.cu.
+cudaMemPool_t device_pool();
+
 // Device buffer owned by a handle; freed by release() or the destructor.
+// With an owner stream (the handle's stream) it is allocated and freed
+// stream-ordered from the library pool, so no call synchronises the device;
+// without one it falls back to cudaMalloc / cudaFree.
 struct DBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    const cudaStream_t *owner = nullptr;
     DBuf() = default;
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
@@ -38,11 +59,15 @@ struct DBuf {
     void alloc(size_t b) {
         release();
         if (b == 0) b = 16;
-        TG_CK(cudaMalloc(&p, b));
+        if (owner) TG_CK(cudaMallocFromPoolAsync(&p, b, device_pool(), *owner));
+        else TG_CK(cudaMalloc(&p, b));
         bytes = b;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (owner) cudaFreeAsync(p, *owner);
+            else cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
     }
@@ -152,14 +177,24 @@ struct Graph {
         c.status = status.as<uint32_t>();
         return c;
     }
-    int64_t device_bytes() const {
-        const DBuf *all[] = {&node_off, &edge_off, &rp, &adj, &toff, &pivot, &nplus, &ty, &old_of, &slot_eid, &e_lo, &e_hi,
+    Graph() {
+        for (DBuf *b : buffers()) b->owner = &stream;
+    }
+    std::vector<DBuf *> buffers() {
+        std::vector<DBuf *> v;
+        for (const DBuf *b : cbuffers()) v.push_back(const_cast<DBuf *>(b));
+        return v;
+    }
+    std::vector<const DBuf *> cbuffers() const {
+        return {&node_off, &edge_off, &rp, &adj, &toff, &pivot, &nplus, &ty, &old_of, &slot_eid, &e_lo, &e_hi,
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
                              &set_scratch};
+    }
+    int64_t device_bytes() const {
         int64_t s = 0;
-        for (const DBuf *b : all) s += (int64_t)b->bytes;
+        for (const DBuf *b : cbuffers()) s += (int64_t)b->bytes;
         return s;
     }
     ~Graph() {

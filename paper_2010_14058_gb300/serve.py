@@ -1,0 +1,275 @@
+"""Continuous-batching request server for typed-graphlet counting.
+
+Requests (typed graphs with an arrival time) are admitted while the
+device-memory budget allows; requests of the same number of types L whose
+size is below `small_edges` are grouped into one batch handle (one build,
+one kernel sequence for the whole group); larger requests run alone.  Each
+admitted group runs on a worker thread with its own CUDA stream, so the
+groups' copies and kernels overlap on the GPU while the scheduler keeps
+admitting.  A request's latency is its completion time minus its arrival
+time.  Results are the global typed-graphlet totals of each request
+(Problem 2), identical to a standalone tg_count of the same graph.
+
+All counting runs in libtg through the binding; this module only moves
+host arrays, streams and bookkeeping.
+"""
+from __future__ import annotations
+
+import queue
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import tg
+
+# device bytes a request needs while it is counted, per edge and per node
+# (handle arrays plus per-edge intermediates of the 4-node stage, L = 8 bound)
+BYTES_PER_EDGE = 40 * 64 + 96
+BYTES_PER_NODE = 2 * 8 * 64 + 64
+
+
+@dataclass
+class Request:
+    rid: int
+    L: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    types: np.ndarray
+    arrival: float = 0.0                  # seconds after the start of the run
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.shape[0]) - 1
+
+    @property
+    def m(self) -> int:
+        return int(self.col.shape[0]) // 2
+
+    def bytes_needed(self) -> int:
+        return BYTES_PER_EDGE * self.m + BYTES_PER_NODE * self.n + (1 << 20)
+
+
+@dataclass
+class Result:
+    rid: int
+    totals: np.ndarray
+    arrival: float
+    started: float
+    done: float
+    status: int
+    group_size: int
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+@dataclass
+class _Group:
+    reqs: list
+    nbytes: int
+    started: float = 0.0
+
+
+def _union(reqs: list):
+    """Block-diagonal union of the requests' CSRs: node_off, row_ptr, col, types."""
+    n_off = np.zeros(len(reqs) + 1, dtype=np.int64)
+    z_off = np.zeros(len(reqs) + 1, dtype=np.int64)
+    for k, r in enumerate(reqs):
+        n_off[k + 1] = n_off[k] + r.n
+        z_off[k + 1] = z_off[k] + int(r.row_ptr[-1])
+    rp = np.empty(int(n_off[-1]) + 1, dtype=np.int64)
+    col = np.empty(int(z_off[-1]), dtype=np.int32)
+    ty = np.empty(int(n_off[-1]), dtype=np.uint8)
+    for k, r in enumerate(reqs):
+        a, b = int(n_off[k]), int(n_off[k + 1])
+        rp[a:b] = r.row_ptr[:-1] + z_off[k]
+        col[z_off[k]:z_off[k + 1]] = r.col + a
+        ty[a:b] = r.types
+    rp[-1] = z_off[-1]
+    return n_off, rp, col, ty
+
+
+class Server:
+    """Admission by device-memory budget, micro-batching, overlapped workers."""
+
+    def __init__(self, budget_bytes: int = 40 << 30, workers: int = 4, small_edges: int = 100_000,
+                 batch_edges: int = 4_000_000, batch_graphs: int = 512, batching: bool = True, device: int = 0):
+        import torch
+        self.torch = torch
+        self.budget = int(budget_bytes)
+        self.workers = max(1, int(workers))
+        self.small_edges = small_edges
+        self.batch_edges = batch_edges
+        self.batch_graphs = batch_graphs
+        self.batching = batching
+        self.device = device
+        self._in_use = 0
+        self._lock = threading.Lock()
+        self._freed = threading.Condition(self._lock)
+
+    # ------------------------------------------------------------ groups
+    def _take_group(self, pending: list) -> _Group | None:
+        """Next admissible group from the arrived requests (FIFO by arrival)."""
+        if not pending:
+            return None
+        head = pending[0]
+        need = head.bytes_needed()
+        if need > self.budget:
+            raise ValueError(f"request {head.rid} needs {need} bytes, more than the budget")
+        with self._lock:
+            if self._in_use + need > self.budget:
+                return None
+            group = [pending.pop(0)]
+            total_m, total_b = head.m, need
+            if self.batching and head.m <= self.small_edges:
+                k = 0
+                while k < len(pending) and len(group) < self.batch_graphs:
+                    r = pending[k]
+                    nb = r.bytes_needed()
+                    if (r.L == head.L and r.m <= self.small_edges and total_m + r.m <= self.batch_edges
+                            and self._in_use + total_b + nb <= self.budget):
+                        group.append(pending.pop(k))
+                        total_m += r.m
+                        total_b += nb
+                    else:
+                        k += 1
+            self._in_use += total_b
+        return _Group(group, total_b)
+
+    def _release(self, nbytes: int) -> None:
+        with self._lock:
+            self._in_use -= nbytes
+            self._freed.notify_all()
+
+    # ------------------------------------------------------------ worker
+    def _run_group(self, grp: _Group, stream, t0: float) -> list:
+        torch = self.torch
+        reqs = grp.reqs
+        L = reqs[0].L
+        lay = tg.tg_layout(L, 4)
+        G = lay["global_slots"]
+        with torch.cuda.stream(stream):
+            if len(reqs) == 1:
+                r = reqs[0]
+                h = tg.tg_build(torch.from_numpy(r.row_ptr).to("cuda", non_blocking=False),
+                                torch.from_numpy(r.col).to("cuda"), torch.from_numpy(r.types).to("cuda"), L,
+                                stream=stream)
+            else:
+                n_off, rp, col, ty = _union(reqs)
+                h = tg.tg_build_batch(n_off, torch.from_numpy(rp).to("cuda"), torch.from_numpy(col).to("cuda"),
+                                      torch.from_numpy(ty).to("cuda"), L, stream=stream)
+            out = torch.empty((len(reqs), G), dtype=torch.int64, device="cuda")
+            tg.tg_count(h, 4, None, out, stream=stream)
+            host = out.to("cpu", non_blocking=False)
+            status = tg.tg_query_status(h)
+            h.free()
+        done = time.perf_counter() - t0
+        res = [Result(r.rid, host[k].numpy().copy(), r.arrival, grp.started, done, status, len(reqs))
+               for k, r in enumerate(reqs)]
+        return res
+
+    # ------------------------------------------------------------ run
+    def run(self, requests: list, realtime: bool = True) -> list:
+        """Serves `requests` (sorted by arrival).  realtime: requests become
+        visible at their arrival times (open loop); otherwise all at once."""
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        work: queue.Queue = queue.Queue(maxsize=self.workers)
+        results: list = []
+        res_lock = threading.Lock()
+        errors: list = []
+        t0 = time.perf_counter()
+
+        def worker():
+            torch.cuda.set_device(self.device)
+            stream = torch.cuda.Stream()
+            while True:
+                grp = work.get()
+                if grp is None:
+                    return
+                try:
+                    out = self._run_group(grp, stream, t0)
+                    with res_lock:
+                        results.extend(out)
+                except Exception as exc:  # reported after the run
+                    errors.append(exc)
+                finally:
+                    self._release(grp.nbytes)
+
+        threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.workers)]
+        for th in threads:
+            th.start()
+        pending: list = []
+        nxt = 0
+        while nxt < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
+                pending.append(reqs[nxt])
+                nxt += 1
+            grp = self._take_group(pending)
+            if grp is not None:
+                grp.started = time.perf_counter() - t0
+                work.put(grp)                          # blocks while every worker is busy
+                continue
+            if pending:
+                with self._lock:
+                    self._freed.wait(timeout=0.002)    # wait for memory to free up
+            elif nxt < len(reqs):
+                time.sleep(min(0.001, max(0.0, reqs[nxt].arrival - now)))
+        for _ in threads:
+            work.put(None)
+        for th in threads:
+            th.join()
+        if errors:
+            raise errors[0]
+        return sorted(results, key=lambda r: r.rid)
+
+
+def summarize(results: list, requests: list) -> dict:
+    """Latency percentiles and throughput of a served trace."""
+    m_of = {r.rid: r.m for r in requests}
+    lat = np.array([r.latency for r in results])
+    edges = sum(m_of[r.rid] for r in results)
+    span = max(r.done for r in results) - min(r.arrival for r in results)
+    return {"requests": len(results), "edges": int(edges), "span_s": round(float(span), 3),
+            "edges_per_s": round(edges / span, 1), "p50_ms": round(float(np.percentile(lat, 50) * 1e3), 3),
+            "p99_ms": round(float(np.percentile(lat, 99) * 1e3), 3), "mean_ms": round(float(lat.mean() * 1e3), 3),
+            "mean_group": round(float(np.mean([r.group_size for r in results])), 2)}
+
+
+def request_pool(count: int, seed: int, m_min: int = 100, m_max: int = 1_000_000, gamma: float = 2.2,
+                 L_range=(3, 8)) -> list:
+    """Seeded pool of request graphs: Chung-Lu, edges log-uniform in
+    [m_min, m_max], n = max(10, ceil(m / 5)), L uniform in L_range, uniform
+    types (the request mix of the serving workload)."""
+    import graphgen
+    rng = np.random.default_rng(seed)
+    pool = []
+    for k in range(count):
+        m = int(round(m_min * (m_max / m_min) ** rng.random()))
+        n = max(10, -(-m // 5))
+        m = min(m, n * (n - 1) // 2 // 2)
+        L = int(rng.integers(L_range[0], L_range[1] + 1))
+        wmax = max(2.0, min(0.5 * n, 2.0 * m / n * 40))
+        g = graphgen.chung_lu(n, m, gamma, wmax, L, seed * 1000 + k)
+        pool.append(g)
+    return pool
+
+
+def poisson_trace(pool: list, rate_per_s: float, duration_s: float, seed: int) -> list:
+    """Open-loop Poisson arrivals over `duration_s`, each request a seeded
+    draw from the pool."""
+    rng = np.random.default_rng(seed)
+    t, rid, out = 0.0, 0, []
+    while True:
+        t += rng.exponential(1.0 / rate_per_s)
+        if t > duration_s:
+            break
+        g = pool[int(rng.integers(len(pool)))]
+        out.append(Request(rid, g["L"], g["row_ptr"], g["col"], g["types"], t))
+        rid += 1
+    return out

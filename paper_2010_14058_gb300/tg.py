@@ -61,6 +61,7 @@ SIGNATURES = {
     "tg_count_batch": ([_vp, _i32, _vp, _vp, _vp], _i32),
     "tg_query_status": ([_vp], _i32),
     "tg_status_string": ([_i32], ctypes.c_char_p),
+    "tg_last_error": ([], ctypes.c_char_p),
     "tg_last_launch_count": ([_vp], _i64),
     "tg_abi_version": ([], _i32),
     "tg_count3_static": ([_i64, _i64, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
@@ -75,10 +76,11 @@ class LibraryMissing(RuntimeError):
 
 
 class TGError(RuntimeError):
-    def __init__(self, code: int, where: str):
+    def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
         self.name = STATUS.get(code, f"status {code}")
-        super().__init__(f"{where}: {self.name}")
+        self.detail = detail
+        super().__init__(f"{where}: {self.name}" + (f" ({detail})" if detail else ""))
 
 
 _lib = None
@@ -106,7 +108,7 @@ def load(path: str = LIB_PATH):
 
 def _check(code: int, where: str) -> None:
     if code != 0:
-        raise TGError(code, where)
+        raise TGError(code, where, tg_last_error())
 
 
 def _ptr(a) -> int | None:
@@ -156,6 +158,11 @@ def tg_abi_version() -> int:
 
 def tg_status_string(code: int) -> str:
     return load().tg_status_string(code).decode()
+
+
+def tg_last_error() -> str:
+    """The calling thread's most recent failure text ("" if none)."""
+    return load().tg_last_error().decode(errors="replace")
 
 
 def tg_layout(L: int, k: int = 4) -> dict:

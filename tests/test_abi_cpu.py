@@ -59,6 +59,7 @@ def test_layout_rejects_bad_arguments(lib):
     with pytest.raises(tg.TGError) as e:
         tg.tg_layout(9, 4)
     assert e.value.name == "TG_ERR_TOO_MANY_TYPES"
+    assert tg.tg_status_string(3) in e.value.detail == tg.tg_last_error()   # thread's last failure text
     with pytest.raises(tg.TGError) as e:
         tg.tg_layout(3, 5)
     assert e.value.name == "TG_ERR_INVALID_ARG"
