@@ -43,6 +43,7 @@ WORKLOADS = {
     "cl_large": "Chung-Lu n=2,000,000 m=20,000,000 gamma=2.1 max weight 5e4, L=5 Zipf(1.2) types",
     "sbm_typed": "SBM 500k/300k/150k/50k nodes, L=4 types, m=30,000,000, affinity 1 between / 0.05 within",
     "er_small": "Erdos-Renyi n=2,000 m=10,000, L=3 uniform types",
+    "cl_mid": "Chung-Lu n=200,000 m=2,000,000 gamma=2.1 max weight 1.2e4, L=5 Zipf(1.2) types (profiling size)",
 }
 
 
@@ -128,24 +129,70 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def edge_bytes_per_kernel(g: dict, L: int, light_max: int = 256) -> dict:
-    """Algorithmic bytes of the per-edge kernels (what each edge must touch
-    in this formulation): its output row, its own triangle counts, the
-    typed-triangle and typed-degree sums of both endpoints, its two 4-cycle
-    slots, its edge record and the shorter side of each typed intersection."""
-    rp = g["row_ptr"]
+# DRAM bytes (read + write) per launch of a kernel, from the ncu capture
+# summarised under profiles/ for that workload; removed when the kernel changes.
+TRAFFIC = {}
+
+
+def kernel_units(g: dict, light_anchor_max: int = 256, hub_min: int = 1 << 16) -> dict:
+    """Work units of the count kernels, computed on the host from the graph:
+    degree-priority wedges (the search for the 4-cycles behind P) split
+    by the anchor class the build assigns (light: at most light_anchor_max
+    wedges; hub: more than hub_min), oriented (anchor, neighbour) pairs per
+    class, and the shorter
+    side of every typed intersection, sum_e sum_t min(d_i^t, d_j^t)."""
+    rp, col, ty, n, L = g["row_ptr"], g["col"].astype(np.int64), g["types"], g["n"], g["L"]
     deg = np.diff(rp)
-    n = g["n"]
+    rank = np.empty(n, np.int64)
+    rank[np.lexsort((np.arange(n), deg))] = np.arange(n)     # priority = (degree, id)
     rows = np.repeat(np.arange(n, dtype=np.int64), deg)
-    col = g["col"]
-    up = col > rows
-    mn = np.minimum(deg[rows[up]], deg[col[up]]).astype(np.int64)
-    S = 2 * L + 10 * L * (L + 1) // 2
-    per_edge = 4 * S + 4 * L + 2 * 8 * L * L + 2 * 8 * L * L + 2 * 4 * L * L + 24
-    light = mn <= light_max
-    return {"k_edge4_light": float(per_edge * light.sum() + 4 * mn[light].sum()),
-            "k_edge4_heavy": float(per_edge * (~light).sum() + 4 * mn[~light].sum()),
-            "k_tri": float((4 * L + 24) * len(mn) + 4 * mn.sum())}
+    key = np.sort(rows * n + rank[col])                       # each row by neighbour priority
+    up = rank[col] < rank[rows]                               # (anchor x, lower-priority neighbour v)
+    x, v = rows[up], col[up]
+    cnt = np.searchsorted(key, v * n + rank[x]) - rp[v]       # wedges x - v - w with w below x
+    W = np.bincount(x, weights=cnt, minlength=n)
+    light = (W > 0) & (W <= light_anchor_max)
+    heavy = (W > light_anchor_max) & (W <= hub_min)
+    hub = W > hub_min
+    pairs = np.bincount(x, minlength=n)
+    tdeg = np.zeros((n, L), np.int64)
+    np.add.at(tdeg, (rows, ty[col].astype(np.int64)), 1)
+    lo = col > rows
+    mins = np.minimum(tdeg[rows[lo]], tdeg[col[lo]]).sum()
+    return {"wedges_light": float(W[light].sum()), "wedges_heavy": float(W[heavy].sum()),
+            "wedges_hub": float(W[hub].sum()), "pairs_light": float(pairs[light].sum()),
+            "pairs_heavy": float(pairs[heavy].sum()), "pairs_hub": float(pairs[hub].sum()), "hubs": int(hub.sum()),
+            "typed_min_sum": float(mins)}
+
+
+def algorithmic_bytes(u: dict, m: int, L: int, S: int, t_nodes: int) -> dict:
+    """Bytes each count kernel must move at least once in this formulation
+    (reads of its inputs and writes of its outputs, intermediates included),
+    per launch over the whole graph:
+      k_tri       per edge: endpoints 8, the shorter side of each typed
+                  intersection 4 B/entry, its typed triangle row 4L;
+      k_wedge_*   per wedge: the far node's id 4 + its 4-cycle slot 4 read +
+                  4 written; per (anchor, neighbour) pair: L slots 8 B each;
+      k_tsum      per edge: endpoints 8, shorter sides as k_tri, C row 4L,
+                  the three L x L sums 24 L^2; per triangle node: its id
+                  written 4, two edge ids 8, two typed-triangle rows 8L,
+                  its type offsets 4(L+1);
+      k_clique*   per triangle node: its id read 4; per edge: K written 8L^2
+                  (a lower bound: the N+ scans are not counted);
+      k_epi4      per edge: endpoints and slots 24, C row 4L, two type
+                  offset rows 8(L+1), tsum 24L^2, K 8L^2, the two 4-cycle
+                  slot columns 8L^2, tau and delta of both endpoints 32L^2,
+                  its output row 4S."""
+    LL = L * L
+    return {
+        "k_tri": 8.0 * m + 4.0 * u["typed_min_sum"] + 4.0 * L * m,
+        "k_wedge_light": 12.0 * u["wedges_light"] + 8.0 * L * u["pairs_light"],
+        "k_wedge_heavy": 12.0 * u["wedges_heavy"] + 8.0 * L * u["pairs_heavy"],
+        "k_wedge_hub": 12.0 * u["wedges_hub"] + 8.0 * L * u["pairs_hub"],
+        "k_tsum": (8.0 + 4 * L + 24 * LL) * m + 4.0 * u["typed_min_sum"] + (12.0 + 12 * L + 4) * t_nodes,
+        "k_clique": 4.0 * t_nodes + 8.0 * LL * m,
+        "k_epi4": (24.0 + 4 * L + 8 * (L + 1) + 72 * LL + 4 * S) * m,
+    }
 
 
 # ------------------------------------------------------------- our arm
@@ -174,6 +221,7 @@ def run_ours(args):
     L, m = g["L"], g["m"]
     lay = tg.tg_layout(L, 4)
     S, G = lay["per_edge_slots"], lay["global_slots"]
+    units = kernel_units(g) if rank == 0 else None
     rp, col, ty = tg.to_device(g, dev)
     pe = torch.empty((m, S), dtype=torch.int32, device=dev)
     gl = torch.empty(G, dtype=torch.int64, device=dev)
@@ -228,18 +276,39 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     value = world * m * args.steps / (ms_max / 1e3)
 
-    # roofline of the dominant kernel (largest share of the timed device time)
+    # roofline: algorithmic bytes of each count kernel per step over its
+    # CUDA-event time per step (k_clique and k_clique_big share one bound)
     peak, peak_kind = load_peaks()
-    top = max(kernel_ms.items(), key=lambda kv: kv[1][0])
-    algo = edge_bytes_per_kernel(g, L)
-    per_launch_ms = top[1][0] / max(top[1][1], 1)
-    abytes = algo.get(top[0])
-    roofline = None
-    if abytes is not None:
-        achieved = abytes / (per_launch_ms / 1e3) / 1e9
-        roofline = {"kernel": top[0], "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
-                    "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
-                    "algorithmic_bytes": abytes, "ms_per_launch": round(per_launch_ms, 3), "traffic": None}
+    roofline, per_kernel, compulsory = None, {}, None
+    if rank == 0:
+        gl_host = gl.cpu().numpy()
+        b2 = lay["global_block_offset"][2]
+        t_nodes = 3 * int(gl_host[b2:b2 + lay["global_block_size"][2]].sum())   # sum_e |T_e|
+        abytes = algorithmic_bytes(units, m, L, S, t_nodes)
+        for name, (kms, nl) in kernel_ms.items():
+            if name == "k_clique_big":
+                continue
+            if name == "k_clique":
+                kms += kernel_ms.get("k_clique_big", [0.0, 0])[0]
+            if name not in abytes or kms <= 0:
+                continue
+            step_ms = kms / args.steps
+            gbs = abytes[name] / (step_ms / 1e3) / 1e9
+            per_kernel[name] = {"ms_per_step": round(step_ms, 3), "launches_per_step": nl // args.steps,
+                                "algorithmic_gb": round(abytes[name] / 1e9, 3), "achieved_gbs": round(gbs, 2),
+                                "frac": round(gbs / peak, 5)}
+        top = max(kernel_ms.items(), key=lambda kv: kv[1][0])[0]
+        if top in per_kernel:
+            pk = per_kernel[top]
+            roofline = {"kernel": top, "bound": "hbm", "achieved": pk["achieved_gbs"], "peak": peak,
+                        "peak_kind": peak_kind, "unit": "GB/s", "frac": pk["frac"],
+                        "algorithmic_bytes": abytes[top], "ms_per_step": pk["ms_per_step"],
+                        "traffic": TRAFFIC.get((args.workload, top))}
+        # compulsory traffic of the whole count: CSR and types read once, outputs written once
+        cb = 8.0 * m + 8.0 * g["n"] + g["n"] + 4.0 * S * m + 8.0 * G
+        count_ms = sum(v[0] for v in kernel_ms.values()) / args.steps
+        compulsory = {"bytes": cb, "count_ms": round(count_ms, 3),
+                      "frac": round(cb / (count_ms / 1e3) / 1e9 / peak, 6)}
     kernel_share = {k: round(v[0] / sum(x[0] for x in kernel_ms.values()), 4) for k, v in kernel_ms.items()}
 
     # end to end through host buffers
@@ -276,7 +345,8 @@ def run_ours(args):
                        "edges": m, "types": L, "k": 4, "per_edge_slots": S, "global_slots": G,
                        "l2": "inputs and outputs larger than L2 (no flush)",
                        "step": "tg_build + tg_count(k=4) + tg_free, device-resident inputs and outputs"},
-            "status": tg.STATUS[status], "roofline": roofline, "kernel_share": kernel_share,
+            "status": tg.STATUS[status], "roofline": roofline, "kernel_roofline": per_kernel,
+            "compulsory_roofline": compulsory, "kernel_share": kernel_share, "units": units,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches[0]),
         }
         print(json.dumps(line), flush=True)

@@ -187,11 +187,15 @@ def workload(name: str) -> dict:
     er_small   ER G(n=2000, m=10000), L=3 uniform types
     cl_large   Chung-Lu n=2e6, m=2e7, gamma=2.1, max weight 5e4, L=5 Zipf(1.2) types
     sbm_typed  SBM sizes 500k/300k/150k/50k, affinity 1 between / 0.05 within, m=3e7, L=4
+    cl_mid     cl_large scaled down 10x: n=2e5, m=2e6, gamma=2.1, max weight 1.2e4, L=5
+               Zipf(1.2) types (the size used for profiler captures)
     """
     if name == "er_small":
         return erdos_renyi(2000, 10000, 3, SEED_BASE + 1)
     if name == "cl_large":
         return chung_lu(2_000_000, 20_000_000, 2.1, 5.0e4, 5, SEED_BASE + 2, type_zipf=1.2)
+    if name == "cl_mid":
+        return chung_lu(200_000, 2_000_000, 2.1, 1.2e4, 5, SEED_BASE + 7, type_zipf=1.2)
     if name == "sbm_typed":
         aff = np.full((4, 4), 1.0)
         np.fill_diagonal(aff, 0.05)

@@ -114,13 +114,17 @@ typedef struct {
 
 /* Tuning knobs (0 = library default).  Results never depend on them. */
 typedef struct {
-    int32_t light_edge_max_degree;    /* edges with min(d_i,d_j) <= this: warp per edge */
+    int32_t light_edge_max_degree;    /* edges whose triangle set T has at most max(this, 32) nodes:
+                                         warp per edge in the 4-clique pass (CTA per edge above) */
     int32_t light_anchor_max_wedges;  /* wedge anchors with at most this many wedges: warp per anchor */
     int32_t anchor_table_budget_mb;   /* device memory for per-CTA wedge tables */
     int32_t ctas_per_sm;              /* resident CTAs per SM for the per-edge kernels */
     int32_t cycle_budget_mb;          /* device memory for the per-slot 4-cycle array; a batch whose
                                          array would exceed it is counted in chunks of whole graphs */
-    int32_t reserved[3];
+    int32_t hub_min_wedges;           /* anchors with more wedges than this are hubs: each is counted
+                                         by the whole GPU against one node table shared by all CTAs */
+    int32_t hub_l2_mb;                /* bytes of hub node tables in use at once (kept within L2) */
+    int32_t reserved;
 } tg_options;
 
 /* ---- layout ---------------------------------------------------------- */

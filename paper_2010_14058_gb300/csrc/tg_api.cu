@@ -66,7 +66,10 @@ void build_common(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t n
         if (opt->anchor_table_budget_mb > 0) o.anchor_table_budget_mb = opt->anchor_table_budget_mb;
         if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
         if (opt->cycle_budget_mb > 0) o.cycle_budget_mb = opt->cycle_budget_mb;
+        if (opt->hub_min_wedges > 0) o.hub_min_wedges = opt->hub_min_wedges;
+        if (opt->hub_l2_mb > 0) o.hub_l2_mb = opt->hub_l2_mb;
     }
+    o.hub_min_wedges = std::max(o.hub_min_wedges, o.light_anchor_max_wedges);
     o.light_edge_max_degree = std::min(o.light_edge_max_degree, 256);     // warp T list capacity
     o.light_anchor_max_wedges = std::min(o.light_anchor_max_wedges, 2048);
     o.ctas_per_sm = std::min(std::max(o.ctas_per_sm, 1), 8);

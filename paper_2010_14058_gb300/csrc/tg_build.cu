@@ -266,14 +266,15 @@ __global__ void k_anchor_work(GraphView g, int64_t *work) {
     if (lane == 0) work[x] = total;
 }
 
-__global__ void k_classify_anchors(int64_t n, const int64_t *__restrict__ work, int64_t light_max,
-                                   uint8_t *is_light, uint8_t *is_heavy, int32_t *ids,
+__global__ void k_classify_anchors(int64_t n, const int64_t *__restrict__ work, int64_t light_max, int64_t hub_min,
+                                   uint8_t *is_light, uint8_t *is_heavy, uint8_t *is_hub, int32_t *ids,
                                    unsigned long long *heavy_key) {
     int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (x >= n) return;
     int64_t w = work[x];
     is_light[x] = (w > 0 && w <= light_max) ? 1 : 0;
-    is_heavy[x] = (w > light_max) ? 1 : 0;
+    is_heavy[x] = (w > light_max && w <= hub_min) ? 1 : 0;
+    is_hub[x] = (w > hub_min) ? 1 : 0;
     ids[x] = (int32_t)x;
     heavy_key[x] = (unsigned long long)w;
 }
@@ -562,18 +563,32 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         TBuf work(sizeof(int64_t) * std::max<int64_t>(n, 1), s);
         TBuf fl(std::max<int64_t>(n, 1), s), fh(std::max<int64_t>(n, 1), s), ids(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
         TBuf key(sizeof(unsigned long long) * std::max<int64_t>(n, 1), s);
+        TBuf fhub(std::max<int64_t>(n, 1), s);
         if (n > 0) {
             ++G.last_launches;
             k_anchor_work<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(G.view(), work.as<int64_t>());
             ++G.last_launches;
             k_classify_anchors<<<blocks_for(n, kThreads), kThreads, 0, s>>>(
-                n, work.as<int64_t>(), opt.light_anchor_max_wedges, fl.as<uint8_t>(), fh.as<uint8_t>(), ids.as<int32_t>(),
-                key.as<unsigned long long>());
+                n, work.as<int64_t>(), opt.light_anchor_max_wedges, opt.hub_min_wedges, fl.as<uint8_t>(),
+                fh.as<uint8_t>(), fhub.as<uint8_t>(), ids.as<int32_t>(), key.as<unsigned long long>());
             TG_CK(cudaGetLastError());
         }
         G.n_anchors_light = select_flagged(ids.as<int32_t>(), fl.as<uint8_t>(), n, G.anchors_light, s);
         G.n_anchors_heavy = select_flagged(ids.as<int32_t>(), fh.as<uint8_t>(), n, G.anchors_heavy, s);
         sort_desc_by_key(G.anchors_heavy, G.n_anchors_heavy, key.as<unsigned long long>(), s, G.last_launches);
+        G.n_hubs = select_flagged(ids.as<int32_t>(), fhub.as<uint8_t>(), n, G.hubs, s);
+        G.h_hub_id.assign((size_t)G.n_hubs, 0);
+        G.h_hub_wedges.assign((size_t)G.n_hubs, 0);
+        if (G.n_hubs > 0) {
+            TBuf wk(sizeof(unsigned long long) * (size_t)G.n_hubs, s);
+            ++G.last_launches;
+            k_gather_keys<<<blocks_for(G.n_hubs, kThreads), kThreads, 0, s>>>(
+                G.n_hubs, G.hubs.as<int32_t>(), key.as<unsigned long long>(), wk.as<unsigned long long>());
+            TG_CK(cudaGetLastError());
+            TG_CK(cudaMemcpyAsync(G.h_hub_id.data(), G.hubs.p, sizeof(int32_t) * G.n_hubs, cudaMemcpyDeviceToHost, s));
+            TG_CK(cudaMemcpyAsync(G.h_hub_wedges.data(), wk.p, sizeof(int64_t) * G.n_hubs, cudaMemcpyDeviceToHost, s));
+            TG_CK(cudaStreamSynchronize(s));
+        }
     }
     {
         TBuf fl(std::max<int64_t>(m, 1), s), fh(std::max<int64_t>(m, 1), s), ids(sizeof(int32_t) * std::max<int64_t>(m, 1), s);

@@ -360,6 +360,221 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
     }
 }
 
+// ------------------------------------------------------------ hub anchors
+// An anchor u with very many wedges (a hub) is counted by the whole GPU at
+// once: every CTA works on the wedges of the same few hubs, against one node
+// table per hub that all CTAs share, so the tables stay in L2 instead of one
+// dense table per CTA streaming through HBM.  The wedges u - v - w (v, w of
+// lower priority than u) of every hub are flattened into items, one per
+// (hub, v, type of w) with at least one wedge; item_woff is the exclusive
+// prefix of the items' wedge counts, so wedge x of the flattened order is
+// w = adj[item_vb[it] + x - item_woff[it]] for the item it containing x.
+// The counts are the same as k_wedge_heavy's: phase 0 fills h_u[w][t] (the
+// number of type-t neighbours v of u below u that are adjacent to w),
+// phase 1 adds h_u[w][t] - [t = t_v] to the 4-cycle slot of (v, w) and the
+// per-(v, type of w) sums to the slot of (u, v), phase 2 clears the rows.
+
+struct HubView {
+    const int32_t *hubs;        // hub node ids
+    const int64_t *hub_base;    // first node of each hub's graph
+    const int64_t *woff;        // [n_items + 1] first wedge of each item
+    const int32_t *vb;          // adj position of the item's first w
+    const int32_t *sv;          // adj position of v in the hub's row
+    const int32_t *hub;         // hub index of the item
+    const uint8_t *tt;          // type of v << 4 | type of w
+};
+
+constexpr int kHubThreads = 256;
+
+__global__ void k_hub_nv(GraphView g, const int32_t *__restrict__ hubs, int64_t n_hubs, int64_t *nv,
+                         int64_t *hub_base) {
+    const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (h > n_hubs) return;
+    if (h == n_hubs) { nv[h] = 0; return; }
+    const int32_t u = hubs[h];
+    int64_t acc = 0;
+    for (int t = 0; t < g.L; ++t) {
+        int64_t b, cut;
+        seg_prefix(g, u, t, u, b, cut);
+        acc += cut - b;
+    }
+    nv[h] = acc;
+    hub_base[h] = g.node_off[graph_of_node(g, u)];
+}
+
+// CTA per hub: wedge count of every (v, type of w) of the hub
+__global__ void __launch_bounds__(256) k_hub_cnt(GraphView g, const int32_t *__restrict__ hubs, int64_t n_hubs,
+                                                 const int64_t *__restrict__ vbase, int32_t *cnt, int64_t *flag,
+                                                 int32_t *sv_of, int32_t *hub_of) {
+    __shared__ int64_t s_b[kMaxL + 1], s_cnt[kMaxL + 1];
+    const int L = g.L;
+    for (int64_t h = blockIdx.x; h < n_hubs; h += gridDim.x) {
+        const int32_t u = hubs[h];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t acc = 0;
+            for (int t = 0; t < L; ++t) {
+                int64_t b, cut;
+                seg_prefix(g, u, t, u, b, cut);
+                s_b[t] = b;
+                s_cnt[t] = acc;
+                acc += cut - b;
+            }
+            s_cnt[L] = acc;
+        }
+        __syncthreads();
+        const int64_t nV = s_cnt[L], base = vbase[h];
+        for (int64_t kv = threadIdx.x; kv < nV; kv += blockDim.x) {
+            int tv = 0;
+            while (tv + 1 < L && s_cnt[tv + 1] <= kv) ++tv;
+            const int64_t sv = s_b[tv] + (kv - s_cnt[tv]);
+            const int32_t v = g.adj[sv];
+            sv_of[base + kv] = (int32_t)sv;
+            hub_of[base + kv] = (int32_t)h;
+            for (int tw = 0; tw < L; ++tw) {
+                int64_t vb, vcut;
+                seg_prefix(g, v, tw, u, vb, vcut);
+                const int64_t idx = (base + kv) * L + tw;
+                cnt[idx] = (int32_t)(vcut - vb);
+                flag[idx] = vcut > vb ? 1 : 0;
+            }
+        }
+    }
+}
+
+__global__ void k_hub_items(GraphView g, int64_t ni, const int32_t *__restrict__ cnt, const int64_t *__restrict__ pos,
+                            const int32_t *__restrict__ sv_of, const int32_t *__restrict__ hub_of, int32_t *vb,
+                            int32_t *sv, int32_t *hub, uint8_t *tt, int64_t *icnt) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= ni) return;
+    const int32_t c = cnt[idx];
+    if (c == 0) return;
+    const int64_t j = pos[idx], kv = idx / g.L;
+    const int tw = (int)(idx - kv * g.L);
+    const int32_t s = sv_of[kv];
+    const int32_t v = g.adj[s];
+    vb[j] = (int32_t)seg_begin(g, v, tw);
+    sv[j] = s;
+    hub[j] = hub_of[kv];
+    tt[j] = (uint8_t)((g.ty[v] << 4) | tw);
+    icnt[j] = c;
+}
+
+__global__ void k_hub_bounds(int64_t n_hubs, int L, const int64_t *__restrict__ vbase, const int64_t *__restrict__ pos,
+                             const int64_t *__restrict__ woff, int64_t *first_item, int64_t *first_wedge) {
+    const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (h > n_hubs) return;
+    const int64_t it = pos[vbase[h] * L];
+    first_item[h] = it;
+    first_wedge[h] = woff[it];
+}
+
+// largest j in [lo, hi) with woff[j] <= x, given woff[lo] <= x < woff[hi];
+// a 32-way search by the whole warp
+__device__ __forceinline__ int64_t hub_find_item(const int64_t *__restrict__ woff, int64_t lo, int64_t hi, int64_t x,
+                                                 int lane) {
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t p = lo + lane * step;
+        const unsigned b = __ballot_sync(0xffffffffu, p < hi && woff[p] <= x);
+        lo += (int64_t)(31 - __clz(b)) * step;
+        hi = min(hi, lo + step);
+    }
+    const int64_t p = lo + lane;
+    const unsigned b = __ballot_sync(0xffffffffu, p < hi && woff[p] <= x);
+    return lo + (31 - __clz(b));
+}
+
+// One phase of the wedge pass over the wedges [w0, w1) of items [i0, i1)
+// (hubs h0 ...; hub h uses table h - h0).  Each warp takes one contiguous
+// run of wedges, 32 at a time, one wedge per lane.
+__global__ void __launch_bounds__(kHubThreads) k_wedge_hub(GraphView g, CountView cv, HubView hv, int64_t i0,
+                                                           int64_t i1, int64_t w0, int64_t w1, int32_t h0,
+                                                           int phase) {
+    const int L = g.L;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t per = (((w1 - w0) + nw - 1) / nw + 31) & ~(int64_t)31;
+    int64_t x0 = w0 + gw * per;
+    const int64_t xe = min(w1, x0 + per);
+    if (x0 >= xe) return;                                   // warp-uniform
+    const int64_t nnz = cv.a_stride;
+    uint32_t *A = cv.A - cv.a_base;                         // indexed by absolute slot
+    int64_t j = hub_find_item(hv.woff, i0, i1, x0, lane);
+    for (; x0 < xe; x0 += 32) {
+        // the wedges x0 .. x0+31 lie in items j .. j+31 (every item is non-empty)
+        const int64_t x = x0 + lane;
+        const bool act = x < xe;
+        const int64_t wo = j + lane < i1 ? hv.woff[j + lane] : INT64_MAX;
+        int k = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int64_t c = __shfl_sync(0xffffffffu, wo, k + st);
+            if (c <= x) k += st;
+        }
+        const int64_t it = j + k;
+        const int64_t wstart = __shfl_sync(0xffffffffu, wo, k);
+        const int k31 = __shfl_sync(0xffffffffu, k, 31);
+        const int64_t wnext = k31 < 31 ? __shfl_sync(0xffffffffu, wo, k31 < 31 ? k31 + 1 : 31)
+                                       : (j + 32 < i1 ? hv.woff[j + 32] : INT64_MAX);
+        int32_t svp = 0;
+        int tw = 0;
+        uint32_t c[kMaxL];
+#pragma unroll
+        for (int t = 0; t < kMaxL; ++t) c[t] = 0;
+        if (act) {
+            const int32_t hh = hv.hub[it];
+            const uint8_t tt = hv.tt[it];
+            const int tv = tt >> 4;
+            tw = tt & 15;
+            svp = hv.sv[it];
+            const int64_t pos = (int64_t)hv.vb[it] + (x - wstart);
+            const int32_t w = g.adj[pos];
+            uint32_t *row = cv.tables + (int64_t)(hh - h0) * cv.table_stride + (w - hv.hub_base[hh]) * L;
+            if (phase == 0) {
+                atomicAdd(row + tv, 1u);
+            } else if (phase == 1) {
+                const int tu = g.ty[hv.hubs[hh]];
+#pragma unroll
+                for (int t = 0; t < kMaxL; ++t) {
+                    if (t >= L) break;
+                    const uint32_t v = row[t] - (t == tv ? 1u : 0u);
+                    c[t] = v;
+                    if (v) atomicAdd(&A[(int64_t)(tu * L + t) * nnz + pos], v);
+                }
+            } else {
+                for (int t = 0; t < L; ++t) row[t] = 0;
+            }
+        }
+        if (phase == 1) {
+            // per-item sums over the lanes of each item (items are contiguous runs of lanes)
+            const int64_t key = act ? it : -1;
+            unsigned same = 0;
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const int64_t kk = __shfl_up_sync(0xffffffffu, key, 1 << s);
+                if (lane >= (1 << s) && kk == key) same |= 1u << s;
+            }
+            const int64_t knext = __shfl_down_sync(0xffffffffu, key, 1);
+            const bool tail = act && (lane == 31 || knext != key);
+#pragma unroll
+            for (int t = 0; t < kMaxL; ++t) {
+                if (t >= L) break;
+                uint32_t v = c[t];
+#pragma unroll
+                for (int s = 0; s < 5; ++s) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, v, 1 << s);
+                    if (same & (1u << s)) v += y;
+                }
+                if (tail && v) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + svp], v);
+            }
+        }
+        // first item of the next 32 wedges: the item of x0 + 32
+        j = (wnext <= x0 + 32) ? j + k31 + 1 : j + k31;
+    }
+}
+
 // ------------------------------------------------------------ per-edge 4-node
 // The per-edge stage runs as three lean warp-per-edge kernels with the
 // per-edge intermediates in HBM (all indexed relative to the chunk's first
@@ -1109,6 +1324,130 @@ static void ensure_t_sizes(Graph &G, cudaStream_t s) {
 }
 
 // degree-priority wedges of the anchors of one chunk into A
+// hubs counted together: as many tables as fit the L2 share hub_l2_mb
+static int64_t hub_group_max(const Graph &G) {
+    const int64_t per = std::max<int64_t>(G.max_graph_nodes, 1) * G.L * (int64_t)sizeof(uint32_t);
+    return std::max<int64_t>(((int64_t)G.opt.hub_l2_mb << 20) / per, 1);
+}
+
+template <class T>
+static void exclusive_sum(const T *in, T *out, int64_t n, cudaStream_t s) {
+    size_t tb = 0;
+    TG_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, in, out, n, s));
+    TBuf tmp(std::max<size_t>(tb, 16), s);
+    TG_CK(cub::DeviceScan::ExclusiveSum(tmp.p, tb, in, out, n, s));
+}
+
+static HubView hub_view(const Graph &G) {
+    HubView h;
+    h.hubs = G.hubs.as<int32_t>();
+    h.hub_base = G.hub_base.as<int64_t>();
+    h.woff = G.item_woff.as<int64_t>();
+    h.vb = G.item_vb.as<int32_t>();
+    h.sv = G.item_sv.as<int32_t>();
+    h.hub = G.item_hub.as<int32_t>();
+    h.tt = G.item_tt.as<uint8_t>();
+    return h;
+}
+
+// Wedge items of the hub anchors (graph invariant, built at the first count).
+static void prepare_hubs(Graph &G, cudaStream_t s) {
+    const int L = G.L;
+    const int64_t nh = G.n_hubs;
+    const GraphView gv = G.view();
+    TBuf nv(sizeof(int64_t) * (nh + 1), s), vbase(sizeof(int64_t) * (nh + 1), s);
+    G.hub_base.alloc(sizeof(int64_t) * nh);
+    k_hub_nv<<<grid_for(nh + 1, 256, 1 << 20), 256, 0, s>>>(gv, G.hubs.as<int32_t>(), nh, nv.as<int64_t>(),
+                                                            G.hub_base.as<int64_t>());
+    TG_CK(cudaGetLastError());
+    exclusive_sum(nv.as<int64_t>(), vbase.as<int64_t>(), nh + 1, s);
+    int64_t NV = 0;
+    TG_CK(cudaMemcpyAsync(&NV, vbase.as<int64_t>() + nh, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaStreamSynchronize(s));
+    const int64_t NI = NV * L;
+    TBuf cnt(sizeof(int32_t) * std::max<int64_t>(NI, 1), s), flag(sizeof(int64_t) * (NI + 1), s);
+    TBuf pos(sizeof(int64_t) * (NI + 1), s);
+    TBuf sv_of(sizeof(int32_t) * std::max<int64_t>(NV, 1), s), hub_of(sizeof(int32_t) * std::max<int64_t>(NV, 1), s);
+    TG_CK(cudaMemsetAsync(flag.p, 0, sizeof(int64_t) * (NI + 1), s));
+    k_hub_cnt<<<grid_for(nh, 1, sm_count() * 8), 256, 0, s>>>(gv, G.hubs.as<int32_t>(), nh, vbase.as<int64_t>(),
+                                                               cnt.as<int32_t>(), flag.as<int64_t>(),
+                                                               sv_of.as<int32_t>(), hub_of.as<int32_t>());
+    TG_CK(cudaGetLastError());
+    exclusive_sum(flag.as<int64_t>(), pos.as<int64_t>(), NI + 1, s);
+    TG_CK(cudaMemcpyAsync(&G.n_items, pos.as<int64_t>() + NI, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaStreamSynchronize(s));
+    const int64_t ni = std::max<int64_t>(G.n_items, 1);
+    G.item_vb.alloc(sizeof(int32_t) * ni);
+    G.item_sv.alloc(sizeof(int32_t) * ni);
+    G.item_hub.alloc(sizeof(int32_t) * ni);
+    G.item_tt.alloc(ni);
+    G.item_woff.alloc(sizeof(int64_t) * (G.n_items + 1));
+    TBuf icnt(sizeof(int64_t) * (G.n_items + 1), s);
+    TG_CK(cudaMemsetAsync(icnt.p, 0, sizeof(int64_t) * (G.n_items + 1), s));
+    if (NI > 0) {
+        k_hub_items<<<grid_for(NI, 256, 1 << 30), 256, 0, s>>>(gv, NI, cnt.as<int32_t>(), pos.as<int64_t>(),
+                                                               sv_of.as<int32_t>(), hub_of.as<int32_t>(),
+                                                               G.item_vb.as<int32_t>(), G.item_sv.as<int32_t>(),
+                                                               G.item_hub.as<int32_t>(), G.item_tt.as<uint8_t>(),
+                                                               icnt.as<int64_t>());
+        TG_CK(cudaGetLastError());
+    }
+    exclusive_sum(icnt.as<int64_t>(), G.item_woff.as<int64_t>(), G.n_items + 1, s);
+    TBuf fi(sizeof(int64_t) * (nh + 1), s), fw(sizeof(int64_t) * (nh + 1), s);
+    k_hub_bounds<<<grid_for(nh + 1, 256, 1 << 20), 256, 0, s>>>(nh, L, vbase.as<int64_t>(), pos.as<int64_t>(),
+                                                                G.item_woff.as<int64_t>(), fi.as<int64_t>(),
+                                                                fw.as<int64_t>());
+    TG_CK(cudaGetLastError());
+    G.h_hub_item.assign(nh + 1, 0);
+    G.h_hub_woff.assign(nh + 1, 0);
+    TG_CK(cudaMemcpyAsync(G.h_hub_item.data(), fi.p, sizeof(int64_t) * (nh + 1), cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaMemcpyAsync(G.h_hub_woff.data(), fw.p, sizeof(int64_t) * (nh + 1), cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaStreamSynchronize(s));
+    for (int64_t h = 0; h < nh; ++h)   // the items hold exactly the wedges the build counted
+        if (G.h_hub_woff[h + 1] - G.h_hub_woff[h] != G.h_hub_wedges[h]) throw Error{TG_ERR_INTERNAL, "hub wedges"};
+    G.hubs_ready = true;
+}
+
+// The hubs of chunk c, in groups of at most hub_group_max tables (and about
+// 2^22 wedges): phases 0 and 1 of k_wedge_hub per group, then the group's
+// tables are cleared by phase 2 or, when the group touches a large part of
+// them, by one memset.
+static int64_t launch_hubs(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
+    const int64_t hb0 = std::lower_bound(G.h_hub_id.begin(), G.h_hub_id.end(), (int32_t)c.n0) - G.h_hub_id.begin();
+    const int64_t hb1 = std::lower_bound(G.h_hub_id.begin(), G.h_hub_id.end(), (int32_t)std::min<int64_t>(c.n1, INT32_MAX)) -
+                        G.h_hub_id.begin();
+    const int64_t gmax = std::min<int64_t>(hub_group_max(G), G.n_tables);
+    const int64_t table_bytes = G.table_stride * (int64_t)sizeof(uint32_t);
+    const GraphView gv = G.view();
+    const CountView cv = G.cview();
+    const HubView hv = hub_view(G);
+    const int grid = sm_count() * 6;                        // 40 registers: 6 CTAs of 256 per SM
+    int64_t launches = 0;
+    KernelTimer kt(G, s, "k_wedge_hub");
+    for (int64_t h = hb0; h < hb1;) {
+        int64_t h1 = h, wsum = 0;
+        while (h1 < hb1 && h1 - h < gmax && wsum < ((int64_t)1 << 22)) wsum += G.h_hub_wedges[h1++];
+        const int64_t i0 = G.h_hub_item[h], i1 = G.h_hub_item[h1];
+        const int64_t w0 = G.h_hub_woff[h], w1 = G.h_hub_woff[h1];
+        if (w1 > w0) {
+            for (int phase = 0; phase < 2; ++phase) {
+                k_wedge_hub<<<grid, kHubThreads, 0, s>>>(gv, cv, hv, i0, i1, w0, w1, (int32_t)h, phase);
+                ++launches;
+            }
+            const int64_t zbytes = (h1 - h) * table_bytes;
+            if (zbytes <= 32 * wsum) {
+                TG_CK(cudaMemsetAsync(G.tables.p, 0, (size_t)zbytes, s));
+            } else {
+                k_wedge_hub<<<grid, kHubThreads, 0, s>>>(gv, cv, hv, i0, i1, w0, w1, (int32_t)h, 2);
+                ++launches;
+            }
+            TG_CK(cudaGetLastError());
+        }
+        h = h1;
+    }
+    return launches;
+}
+
 static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
     G.a_base = c.s0;
     const GraphView gv = G.view();
@@ -1128,6 +1467,7 @@ static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
             gv, cv, G.anchors_light.as<int32_t>(), G.n_anchors_light, cap, c.n0, c.n1);
         ++launches;
     }
+    if (G.n_hubs > 0) launches += launch_hubs(G, c, s);
     if (G.n_anchors_heavy > 0) {
         KernelTimer kt(G, s, "k_wedge_heavy");
         k_wedge_heavy<<<G.n_tables, kAnchorThreads, 0, s>>>(gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy,
@@ -1214,11 +1554,13 @@ void prepare_counting(Graph &G, int k, cudaStream_t s) {
             G.scan_tmp.alloc(tb);
             G.scan_tmp_bytes = tb;
         }
-        if (G.n_anchors_heavy > 0 && G.n_tables == 0) {
+        if (G.n_hubs > 0 && !G.hubs_ready) prepare_hubs(G, s);
+        if ((G.n_anchors_heavy > 0 || G.n_hubs > 0) && G.n_tables == 0) {
             const int64_t stride = std::max<int64_t>(G.max_graph_nodes, 1) * L;
             const int64_t per = stride * (int64_t)sizeof(uint32_t);
             int64_t budget = (int64_t)G.opt.anchor_table_budget_mb << 20;
-            int64_t nt = std::min<int64_t>({(int64_t)2 * sm_count(), G.n_anchors_heavy, std::max<int64_t>(budget / per, 1)});
+            const int64_t need = std::max<int64_t>(G.n_anchors_heavy, G.n_hubs > 0 ? hub_group_max(G) : 0);
+            int64_t nt = std::min<int64_t>({(int64_t)2 * sm_count(), need, std::max<int64_t>(budget / per, 1)});
             G.tables.alloc((size_t)(nt * per));
             TG_CK(cudaMemsetAsync(G.tables.p, 0, (size_t)(nt * per), s));
             G.table_stride = stride;

@@ -115,6 +115,15 @@ struct Graph {
     // work lists
     DBuf anchors_light, anchors_heavy, edges_light, edges_heavy;
     int64_t n_anchors_light = 0, n_anchors_heavy = 0, n_edges_light = 0, n_edges_heavy = 0;
+    // hub anchors (ascending id) and their wedge items: one item per
+    // (hub, lower-priority neighbour v, type of w) with at least one wedge
+    DBuf hubs, hub_base, item_woff, item_vb, item_sv, item_hub, item_tt;
+    int64_t n_hubs = 0, n_items = 0;
+    std::vector<int32_t> h_hub_id;      // hub node ids
+    std::vector<int64_t> h_hub_wedges;  // wedges of each hub
+    std::vector<int64_t> h_hub_item;    // first item of each hub (n_hubs + 1)
+    std::vector<int64_t> h_hub_woff;    // first wedge of each hub (n_hubs + 1)
+    bool hubs_ready = false;
     // counting state
     DBuf C, tau, A, tables, gacc, status, tiles_full, stage_pe, stage_gl;
     DBuf tcount, toffs, tlist, tsum, kmat, big_list, big_count, scan_tmp, set_scratch;
@@ -190,7 +199,7 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch};
+                             &set_scratch, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt};
     }
     int64_t device_bytes() const {
         int64_t s = 0;
@@ -238,6 +247,8 @@ inline void fill_defaults(tg_options *o) {
     o->anchor_table_budget_mb = 4096;
     o->ctas_per_sm = 4;
     o->cycle_budget_mb = 16384;
+    o->hub_min_wedges = 1 << 16;
+    o->hub_l2_mb = 64;
 }
 
 // number of SMs of the current device

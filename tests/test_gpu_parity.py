@@ -25,6 +25,8 @@ import paper_2010_14058_gb300 as tg  # noqa: E402
 
 # options that route every edge and every anchor through the CTA variants
 ALL_HEAVY = {"light_edge_max_degree": 1, "light_anchor_max_wedges": 1}
+# ... and every anchor with more than one wedge through the whole-GPU hub pass
+ALL_HUB = {"light_edge_max_degree": 1, "light_anchor_max_wedges": 1, "hub_min_wedges": 1}
 
 
 def assert_parity(g, k=4, options=None, reference="paper"):
@@ -50,10 +52,11 @@ def test_tiny_graphs_vs_brute_force(seed):
     assert_parity(random_graph(n, p, L, 9000 + seed), reference="brute")
 
 
+@pytest.mark.parametrize("options", [ALL_HEAVY, ALL_HUB])
 @pytest.mark.parametrize("seed", range(6))
-def test_tiny_graphs_all_cta_variants(seed):
+def test_tiny_graphs_all_cta_variants(seed, options):
     g = random_graph(9 + seed, 0.6, [2, 3, 8][seed % 3], 9100 + seed)
-    assert_parity(g, options=ALL_HEAVY, reference="brute")
+    assert_parity(g, options=options, reference="brute")
 
 
 def test_degenerate_graphs():
@@ -65,6 +68,11 @@ def test_degenerate_graphs():
     assert_parity(graph_from_edges(7, [(0, x) for x in range(1, 7)], [1, 0, 1, 2, 0, 2, 2], 3))
     assert_parity(graph_from_edges(8, [(a, b) for a in range(8) for b in range(a + 1, 8)], [0, 1, 2, 3, 0, 1, 2, 3], 4))
     assert_parity(graph_from_edges(7, [(a, b) for a in range(3) for b in range(3, 7)], [0, 0, 0, 1, 1, 1, 1], 2))
+    for opt in (ALL_HEAVY, ALL_HUB):
+        assert_parity(graph_from_edges(8, [(a, b) for a in range(8) for b in range(a + 1, 8)], [0, 1, 2, 3, 0, 1, 2, 3], 4),
+                      options=opt)
+        assert_parity(graph_from_edges(7, [(a, b) for a in range(3) for b in range(3, 7)], [0, 0, 0, 1, 1, 1, 1], 2),
+                      options=opt)
 
 
 @pytest.mark.parametrize("L", [1, 2, 5, 8])
@@ -82,7 +90,8 @@ def test_er_small_workload_k3():
     assert_parity(graphgen.workload("er_small"), k=3)
 
 
-@pytest.mark.parametrize("options", [None, ALL_HEAVY, {"light_edge_max_degree": 16, "light_anchor_max_wedges": 8}])
+@pytest.mark.parametrize("options", [None, ALL_HEAVY, ALL_HUB, {"light_edge_max_degree": 16, "light_anchor_max_wedges": 8},
+                                     {"hub_min_wedges": 300}, {"hub_min_wedges": 2000, "hub_l2_mb": 1}])
 def test_chung_lu_with_hubs(options):
     # hubs route edges and anchors through both variants
     g = graphgen.chung_lu(4000, 30000, 2.1, 1200.0, 5, 77, type_zipf=1.2)
@@ -139,7 +148,7 @@ def test_edge_endpoints_and_ranges():
     h.free()
 
 
-@pytest.mark.parametrize("options", [None, {"cycle_budget_mb": 1}])
+@pytest.mark.parametrize("options", [None, {"cycle_budget_mb": 1}, {"cycle_budget_mb": 1, "hub_min_wedges": 257}])
 def test_batch_equals_separate_graphs(options):
     # cycle_budget_mb = 1 splits the batch into many chunks of whole graphs
     graphs = [graphgen.erdos_renyi(50 + 30 * x, 200 + 150 * x, 3, 400 + x) for x in range(7)]
