@@ -166,6 +166,22 @@ __global__ void k_rows(int64_t n, int L, const int64_t *__restrict__ rp, const u
     if (lane == 0) nplus[x] = up;
 }
 
+// warp per node x: its higher-priority neighbours (the part of each type
+// segment past the pivot), packed (type << 29 | id), into one contiguous list
+__global__ void k_plus_fill(GraphView g, int32_t *plus_adj) {
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+    const int lane = threadIdx.x & (kWarp - 1);
+    if (warp >= g.n) return;
+    const int64_t x = warp, r = g.rp[x];
+    int64_t out = g.plus_off[x];
+    for (int q = 0; q < g.L; ++q) {
+        const int64_t b = r + g.pivot[x * g.L + q], e = r + g.toff[x * (g.L + 1) + q + 1];
+        for (int64_t k = b + lane; k < e; k += kWarp)
+            plus_adj[out + (k - b)] = (int32_t)(((uint32_t)q << kTypeShift) | (uint32_t)g.adj[k]);
+        out += e - b;
+    }
+}
+
 // warp per internal row x: forward slots (caller id of x < caller id of y) become edges
 __global__ void k_edge_keys(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ adj,
                             const int32_t *__restrict__ old_of, int64_t m_expected,
@@ -319,6 +335,11 @@ int64_t select_flagged(const int32_t *ids, const uint8_t *flags, int64_t n, DBuf
     out.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(c, 1));
     TG_CK(cudaMemcpyAsync(out.p, sel.p, sizeof(int32_t) * (size_t)c, cudaMemcpyDeviceToDevice, s));
     return c;
+}
+
+__global__ void k_widen(int64_t n, const int32_t *__restrict__ in, int64_t *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
 }
 
 // Sorts `ids` (count c) by descending key (keys indexed by id).
@@ -605,6 +626,31 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         sort_desc_by_key(G.edges_heavy, G.n_edges_heavy, cost.as<unsigned long long>(), s, G.last_launches);
     }
     if (read_status(G.status, s) & ST_INVALID_GRAPH) throw Error{TG_ERR_INVALID_GRAPH, "asymmetric rows"};
+
+    // 7. higher-priority neighbour lists (4-clique pass); one per edge
+    G.plus_off.alloc(sizeof(int64_t) * (n + 1));
+    {
+        TBuf np64(sizeof(int64_t) * (n + 1), s);
+        TG_CK(cudaMemsetAsync(np64.p, 0, sizeof(int64_t) * (n + 1), s));
+        if (n > 0) {
+            ++G.last_launches;
+            k_widen<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, G.nplus.as<int32_t>(), np64.as<int64_t>());
+            TG_CK(cudaGetLastError());
+        }
+        cub_call([&](void *t, size_t &b) {
+            return cub::DeviceScan::ExclusiveSum(t, b, np64.as<int64_t>(), G.plus_off.as<int64_t>(), n + 1, s);
+        }, s);
+    }
+    int64_t nplus_total = 0;
+    TG_CK(cudaMemcpyAsync(&nplus_total, G.plus_off.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaStreamSynchronize(s));
+    if (nplus_total != m) throw Error{TG_ERR_INTERNAL, "higher-priority neighbours"};
+    G.plus_adj.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1));
+    if (n > 0) {
+        ++G.last_launches;
+        k_plus_fill<<<blocks_for(n * kWarp, kThreads), kThreads, 0, s>>>(G.view(), G.plus_adj.as<int32_t>());
+        TG_CK(cudaGetLastError());
+    }
 }
 
 }  // namespace tg

@@ -797,19 +797,29 @@ __device__ void clique_pairs(const GraphView &g, const int32_t *T, int32_t nT, c
         const int32_t dplus = valid ? g.nplus[w] : 0;
         if (valid && dplus <= kShort && dplus > 0) {
             const int tw = type_of_index(ts, L, k);
-            const int64_t rw = g.rp[w];
-            for (int q = 0; q < L; ++q) {
-                int64_t sx = rw + g.pivot[(int64_t)w * L + q];
-                const int64_t se = rw + g.toff[(int64_t)w * (L + 1) + q + 1];
-                unsigned c = 0;
-                for (; sx + 4 <= se; sx += 4) {
-                    const int32_t x0 = g.adj[sx], x1 = g.adj[sx + 1], x2 = g.adj[sx + 2], x3 = g.adj[sx + 3];
-                    c += t_set_has(set, lgcap, x0) + t_set_has(set, lgcap, x1) + t_set_has(set, lgcap, x2) +
-                         t_set_has(set, lgcap, x3);
+            int64_t sx = g.plus_off[w];
+            const int64_t se = sx + dplus;
+            unsigned c = 0;
+            uint32_t cur = 0;
+            auto take = [&](uint32_t ent) {                  // entries come in type order
+                const uint32_t q = ent >> kTypeShift;
+                if (q != cur) {
+                    if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
+                    c = 0;
+                    cur = q;
                 }
-                for (; sx < se; ++sx) c += t_set_has(set, lgcap, g.adj[sx]) ? 1u : 0u;
-                if (c) atomicAdd(&sK[tw * kMaxL + q], c);
+                c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
+            };
+            for (; sx + 4 <= se; sx += 4) {
+                const uint32_t x0 = (uint32_t)g.plus_adj[sx], x1 = (uint32_t)g.plus_adj[sx + 1];
+                const uint32_t x2 = (uint32_t)g.plus_adj[sx + 2], x3 = (uint32_t)g.plus_adj[sx + 3];
+                take(x0);
+                take(x1);
+                take(x2);
+                take(x3);
             }
+            for (; sx < se; ++sx) take((uint32_t)g.plus_adj[sx]);
+            if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
         }
         unsigned longs = __ballot_sync(0xffffffffu, valid && dplus > kShort);
         while (longs) {
@@ -817,15 +827,22 @@ __device__ void clique_pairs(const GraphView &g, const int32_t *T, int32_t nT, c
             longs &= longs - 1;
             const int32_t lw = __shfl_sync(0xffffffffu, w, src);
             const int ltw = type_of_index(ts, L, base + src);
-            const int64_t rw = g.rp[lw];
-            for (int q = 0; q < L; ++q) {
-                const int64_t sb = rw + g.pivot[(int64_t)lw * L + q];
-                const int64_t se = rw + g.toff[(int64_t)lw * (L + 1) + q + 1];
-                unsigned c = 0;
-                for (int64_t sx = sb + lane; sx < se; sx += 32) c += t_set_has(set, lgcap, g.adj[sx]) ? 1u : 0u;
-                c = warp_sum_u32(c);
-                if (lane == 0 && c) atomicAdd(&sK[ltw * kMaxL + q], c);
+            // N+(lw) as one list of (type << 29 | id) in type order: each
+            // lane counts its run of one type and flushes when it changes
+            const int64_t pb = g.plus_off[lw], pe = g.plus_off[lw + 1];
+            unsigned c = 0;
+            uint32_t cur = 0;
+            for (int64_t sx = pb + lane; sx < pe; sx += 32) {
+                const uint32_t ent = (uint32_t)g.plus_adj[sx];
+                const uint32_t q = ent >> kTypeShift;
+                if (q != cur) {
+                    if (c) atomicAdd(&sK[ltw * kMaxL + cur], c);
+                    c = 0;
+                    cur = q;
+                }
+                c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
             }
+            if (c) atomicAdd(&sK[ltw * kMaxL + cur], c);
         }
     }
 }

@@ -112,6 +112,7 @@ struct Graph {
 
     // graph (built once)
     DBuf node_off, edge_off, rp, adj, toff, pivot, nplus, ty, old_of, slot_eid, e_lo, e_hi, e_slot_lo, e_slot_hi, delta;
+    DBuf plus_off, plus_adj;
     // work lists
     DBuf anchors_light, anchors_heavy, edges_light, edges_heavy;
     int64_t n_anchors_light = 0, n_anchors_heavy = 0, n_edges_light = 0, n_edges_heavy = 0;
@@ -166,6 +167,8 @@ struct Graph {
         v.e_slot_lo = e_slot_lo.as<int64_t>();
         v.e_slot_hi = e_slot_hi.as<int64_t>();
         v.delta = delta.as<int64_t>();
+        v.plus_off = plus_off.as<int64_t>();
+        v.plus_adj = plus_adj.as<int32_t>();
         return v;
     }
     CountView cview() const {
@@ -199,7 +202,7 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt};
+                             &set_scratch, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt};
     }
     int64_t device_bytes() const {
         int64_t s = 0;

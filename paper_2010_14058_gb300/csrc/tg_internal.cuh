@@ -50,6 +50,9 @@ struct GraphView {
     const int64_t *e_slot_lo;  // [m] slot of e_hi inside row e_lo
     const int64_t *e_slot_hi;  // [m] slot of e_lo inside row e_hi
     const int64_t *delta;      // [n*L*L] sum_{w in Gamma_x^t} d_w^t'
+    const int64_t *plus_off;   // [n+1] start of x's higher-priority neighbours in plus_adj
+    const int32_t *plus_adj;   // [m] higher-priority neighbours of each node, (type << 29 | id),
+                               // grouped by type in (type, id) order
 };
 
 // Per-count working arrays.
