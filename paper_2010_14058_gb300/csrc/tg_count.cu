@@ -205,7 +205,141 @@ __device__ int hash_find(const int32_t *keys, int cap, int32_t w) {
     return -1;
 }
 
-// Light anchors (few wedges): one warp per anchor, table in shared memory.
+// ------------------------------------------------------------ wedges of one v
+// The wedges u - v - w (v, w below the anchor u) of one neighbour v, all
+// types of w flattened: lane t < L finds the part of v's type-t segment
+// below u (one binary search per lane, in parallel) and its exclusive
+// offset; wedge p of v then has type tw = the last lane t whose offset is
+// <= p, and lanes take 32 wedges at a time whatever their types.
+struct VRuns {
+    int64_t b;          // lane t < L: first slot of type t in v's row
+    int32_t off;        // lane t < L: wedges of types < t (total on lanes >= L)
+    int32_t total;      // wedges of v
+};
+
+__device__ __forceinline__ VRuns v_runs(const GraphView &g, int32_t v, int32_t u, int lane) {
+    VRuns r;
+    r.b = 0;
+    int32_t n = 0;
+    if (lane < g.L) {
+        int64_t cut;
+        seg_prefix(g, v, lane, u, r.b, cut);
+        n = (int32_t)(cut - r.b);
+    }
+    int32_t inc = n;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    r.off = inc - n;
+    r.total = __shfl_sync(0xffffffffu, inc, kMaxL - 1);
+    return r;
+}
+
+// per-(v, type of w) sums of phase 1 over the lanes (runs of equal tw are
+// contiguous): tail lanes add them to the 4-cycle slot of (u, v)
+__device__ __forceinline__ void flush_runs(uint32_t *A, int64_t nnz, int L, const uint32_t *c, int key, int tw,
+                                           int64_t sv, int lane) {
+    unsigned same = 0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int kk = __shfl_up_sync(0xffffffffu, key, 1 << s);
+        if (lane >= (1 << s) && kk == key) same |= 1u << s;
+    }
+    const int knext = __shfl_down_sync(0xffffffffu, key, 1);
+    const bool tail = key >= 0 && (lane == 31 || knext != key);
+#pragma unroll
+    for (int t = 0; t < kMaxL; ++t) {
+        if (t >= L) break;
+        uint32_t v = c[t];
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, 1 << s);
+            if (same & (1u << s)) v += y;
+        }
+        if (tail && v) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + sv], v);
+    }
+}
+
+// One phase of the wedges of v for one warp.  rows(w, insert) gives w's
+// counter row (L entries): phase 0 inserts and adds 1 at t_v; phase 1 adds
+// h[w][t] - [t = t_v] to the slot of (v, w) and the per-type sums to the
+// slot of (u, v); phase 2 clears the row (dense tables only).
+template <class Rows>
+__device__ __forceinline__ void wedge_v(const GraphView &g, uint32_t *A, int64_t nnz, int32_t u, int tu, int32_t v,
+                                        int tv, int64_t sv, int phase, int lane, Rows rows) {
+    const int L = g.L;
+    const VRuns r = v_runs(g, v, u, lane);
+    for (int32_t p0 = 0; p0 < r.total; p0 += 32) {
+        const int32_t p = p0 + lane;
+        int tw = 0;
+#pragma unroll
+        for (int st = kMaxL / 2; st > 0; st >>= 1) {
+            const int32_t c = __shfl_sync(0xffffffffu, r.off, tw + st);
+            if (c <= p) tw += st;
+        }
+        const int64_t k = __shfl_sync(0xffffffffu, r.b, tw) + (p - __shfl_sync(0xffffffffu, r.off, tw));
+        const bool act = p < r.total;
+        uint32_t c[kMaxL];
+#pragma unroll
+        for (int t = 0; t < kMaxL; ++t) c[t] = 0;
+        if (act) {
+            const int32_t w = g.adj[k];
+            uint32_t *row = rows(w, phase == 0);
+            if (row) {
+                if (phase == 0) {
+                    atomicAdd(row + tv, 1u);
+                } else if (phase == 1) {
+#pragma unroll
+                    for (int t = 0; t < kMaxL; ++t) {
+                        if (t >= L) break;
+                        const uint32_t x = row[t] - (t == tv ? 1u : 0u);
+                        c[t] = x;
+                        if (x) atomicAdd(&A[(int64_t)(tu * L + t) * nnz + k], x);
+                    }
+                } else {
+                    for (int t = 0; t < L; ++t) row[t] = 0;
+                }
+            }
+        }
+        if (phase == 1) flush_runs(A, nnz, L, c, act ? tw : -1, tw, sv, lane);
+    }
+}
+
+// lower-priority neighbours of u by type: lane t < L gets the first slot
+// of type t and the exclusive offset of its part; returns their number
+__device__ __forceinline__ int32_t u_runs(const GraphView &g, int32_t u, int lane, int64_t &ub, int32_t &uoff) {
+    int32_t n = 0;
+    ub = 0;
+    if (lane < g.L) {
+        int64_t cut;
+        seg_prefix(g, u, lane, u, ub, cut);
+        n = (int32_t)(cut - ub);
+    }
+    int32_t inc = n;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    uoff = inc - n;
+    return __shfl_sync(0xffffffffu, inc, kMaxL - 1);
+}
+
+// neighbour number kv of u's lower-priority neighbours -> (slot, type)
+__device__ __forceinline__ int64_t u_slot(int64_t ub, int32_t uoff, int32_t kv, int &tv) {
+    tv = 0;
+#pragma unroll
+    for (int st = kMaxL / 2; st > 0; st >>= 1) {
+        const int32_t c = __shfl_sync(0xffffffffu, uoff, tv + st);
+        if (c <= kv) tv += st;
+    }
+    return __shfl_sync(0xffffffffu, ub, tv) + (kv - __shfl_sync(0xffffffffu, uoff, tv));
+}
+
+// Light anchors (few wedges): one warp per anchor, table in shared memory
+// (a hash of capacity `cap` >= 2 x the anchor's wedges).
 __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphView g, CountView cv,
                                                                         const int32_t *__restrict__ anchors,
                                                                         int64_t n_anchors, int cap, int64_t n0,
@@ -221,77 +355,67 @@ __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphVie
     const int64_t nw = (int64_t)gridDim.x * kLightAnchorWarps;
     const int64_t nnz = cv.a_stride;
     uint32_t *A = cv.A - cv.a_base;                          // indexed by absolute slot
+    auto rows = [&](int32_t w, bool insert) -> uint32_t * {
+        const int h = insert ? hash_insert(keys, cap, w) : hash_find(keys, cap, w);
+        if (h < 0) {
+            if (insert) set_status(cv.status, ST_INTERNAL);
+            return nullptr;
+        }
+        return cnt + h * L;
+    };
     for (int64_t a = (int64_t)blockIdx.x * kLightAnchorWarps + wid; a < n_anchors; a += nw) {
         const int32_t u = anchors[a];
         if (u < n0 || u >= n1) continue;                    // anchor outside this chunk
         const int tu = g.ty[u];
-        // phase 1
-        for (int tv = 0; tv < L; ++tv) {
-            int64_t ub, ucut;
-            seg_prefix(g, u, tv, u, ub, ucut);
-            for (int64_t sv = ub; sv < ucut; ++sv) {
-                const int32_t v = g.adj[sv];
-                for (int tw = 0; tw < L; ++tw) {
-                    int64_t vb, vcut;
-                    seg_prefix(g, v, tw, u, vb, vcut);
-                    for (int64_t k = vb + lane; k < vcut; k += 32) {
-                        int h = hash_insert(keys, cap, g.adj[k]);
-                        if (h >= 0) atomicAdd(&cnt[h * L + tv], 1u);
-                        else set_status(cv.status, ST_INTERNAL);
-                    }
-                }
+        int64_t ub;
+        int32_t uoff;
+        const int32_t nV = u_runs(g, u, lane, ub, uoff);
+        for (int phase = 0; phase < 2; ++phase) {
+            for (int32_t kv = 0; kv < nV; ++kv) {
+                int tv;
+                const int64_t sv = u_slot(ub, uoff, kv, tv);
+                wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, phase, lane, rows);
             }
+            __syncwarp();
         }
-        __syncwarp();
-        // phase 2
-        for (int tv = 0; tv < L; ++tv) {
-            int64_t ub, ucut;
-            seg_prefix(g, u, tv, u, ub, ucut);
-            for (int64_t sv = ub; sv < ucut; ++sv) {
-                const int32_t v = g.adj[sv];
-                for (int tw = 0; tw < L; ++tw) {
-                    int64_t vb, vcut;
-                    seg_prefix(g, v, tw, u, vb, vcut);
-                    unsigned acc[kMaxL];
-#pragma unroll
-                    for (int t = 0; t < kMaxL; ++t) acc[t] = 0;
-                    for (int64_t k = vb + lane; k < vcut; k += 32) {
-                        int h = hash_find(keys, cap, g.adj[k]);
-                        if (h < 0) continue;
-#pragma unroll
-                        for (int t = 0; t < kMaxL; ++t) {
-                            if (t >= L) break;
-                            unsigned c = cnt[h * L + t] - (t == tv ? 1u : 0u);
-                            if (c) {
-                                atomicAdd(&A[(int64_t)(tu * L + t) * nnz + k], c);
-                                acc[t] += c;
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < kMaxL; ++t) {
-                        if (t >= L) break;
-                        unsigned r = warp_sum_u32(acc[t]);
-                        if (lane == 0 && r) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + sv], r);
-                    }
-                }
-            }
-        }
-        __syncwarp();
         for (int k = lane; k < cap; k += 32) keys[k] = -1;
         for (int k = lane; k < cap * L; k += 32) cnt[k] = 0;
         __syncwarp();
     }
 }
 
-// Heavy anchors: one CTA per anchor, dense table in this CTA's global slice
-// indexed by (w - first node of u's graph).  Warps take the v in V_u.
+// Heavy anchors: one CTA per anchor, warps over the anchor's lower-priority
+// neighbours v.  The rows h[w][.] live in a shared-memory hash of kHeavyCap
+// entries; an anchor whose distinct w exceed 3/4 of it is redone against
+// the CTA's dense node table in global memory (cleared again by phase 2).
+constexpr int kHeavyCap = 4096;
+
+__device__ int hash_insert_bounded(int32_t *keys, int cap, int32_t w, int *fill, int limit) {
+    int h = hash_slot(w, cap);
+    for (int probe = 0; probe < cap; ++probe) {
+        int32_t k = keys[h];
+        if (k == w) return h;
+        if (k == -1) {
+            if (atomicAdd(fill, 1) >= limit) return -1;     // over the load limit
+            const int32_t old = atomicCAS(&keys[h], -1, w);
+            if (old == -1) return h;
+            atomicSub(fill, 1);
+            if (old == w) return h;
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    return -1;
+}
+
 __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, CountView cv,
                                                                const int32_t *__restrict__ anchors,
                                                                int64_t n_anchors, int64_t n0, int64_t n1) {
-    __shared__ int64_t s_b[kMaxL + 1], s_cnt[kMaxL + 1];
+    extern __shared__ int32_t hsm[];
+    __shared__ int s_fill, s_over;
     const int L = g.L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    int32_t *keys = hsm;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(hsm + kHeavyCap);
     uint32_t *tbl = cv.tables + (int64_t)blockIdx.x * cv.table_stride;
     const int64_t nnz = cv.a_stride;
     uint32_t *A = cv.A - cv.a_base;                          // indexed by absolute slot
@@ -300,60 +424,45 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
         if (u < n0 || u >= n1) continue;                    // anchor outside this chunk (uniform per CTA)
         const int tu = g.ty[u];
         const int64_t base = g.node_off[graph_of_node(g, u)];
-        if (threadIdx.x == 0) {
-            int64_t acc = 0;
-            for (int t = 0; t < L; ++t) {
-                int64_t b, cut;
-                seg_prefix(g, u, t, u, b, cut);
-                s_b[t] = b;
-                s_cnt[t] = acc;
-                acc += cut - b;
+        for (int k = threadIdx.x; k < kHeavyCap; k += blockDim.x) keys[k] = -1;
+        for (int k = threadIdx.x; k < kHeavyCap * L; k += blockDim.x) cnt[k] = 0;
+        if (threadIdx.x == 0) { s_fill = 0; s_over = 0; }
+        __syncthreads();
+        int64_t ub;
+        int32_t uoff;
+        const int32_t nV = u_runs(g, u, lane, ub, uoff);
+        auto hash_rows = [&](int32_t w, bool insert) -> uint32_t * {
+            int h;
+            if (insert) {
+                h = hash_insert_bounded(keys, kHeavyCap, w, &s_fill, kHeavyCap * 3 / 4);
+                if (h < 0) { s_over = 1; return nullptr; }
+            } else {
+                h = hash_find(keys, kHeavyCap, w);
+                if (h < 0) return nullptr;
             }
-            s_cnt[L] = acc;
+            return cnt + h * L;
+        };
+        auto dense_rows = [&](int32_t w, bool) -> uint32_t * { return tbl + (int64_t)(w - base) * L; };
+        for (int32_t kv = wid; kv < nV; kv += nwarp) {
+            int tv;
+            const int64_t sv = u_slot(ub, uoff, kv, tv);
+            wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, hash_rows);
         }
         __syncthreads();
-        const int64_t nV = s_cnt[L];
-        for (int phase = 0; phase < 3; ++phase) {
-            for (int64_t kv = wid; kv < nV; kv += nwarp) {
-                int tv = 0;
-                while (tv + 1 < L && s_cnt[tv + 1] <= kv) ++tv;
-                const int64_t sv = s_b[tv] + (kv - s_cnt[tv]);
-                const int32_t v = g.adj[sv];
-                for (int tw = 0; tw < L; ++tw) {
-                    int64_t vb, vcut;
-                    seg_prefix(g, v, tw, u, vb, vcut);
-                    if (phase == 0) {
-                        for (int64_t k = vb + lane; k < vcut; k += 32)
-                            atomicAdd(&tbl[(g.adj[k] - base) * L + tv], 1u);
-                    } else if (phase == 1) {
-                        unsigned acc[kMaxL];
-#pragma unroll
-                        for (int t = 0; t < kMaxL; ++t) acc[t] = 0;
-                        for (int64_t k = vb + lane; k < vcut; k += 32) {
-                            const uint32_t *h = tbl + (g.adj[k] - base) * L;
-#pragma unroll
-                            for (int t = 0; t < kMaxL; ++t) {
-                                if (t >= L) break;
-                                unsigned c = h[t] - (t == tv ? 1u : 0u);
-                                if (c) {
-                                    atomicAdd(&A[(int64_t)(tu * L + t) * nnz + k], c);
-                                    acc[t] += c;
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int t = 0; t < kMaxL; ++t) {
-                            if (t >= L) break;
-                            unsigned r = warp_sum_u32(acc[t]);
-                            if (lane == 0 && r) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + sv], r);
-                        }
-                    } else {
-                        for (int64_t k = vb + lane; k < vcut; k += 32) {
-                            uint32_t *h = tbl + (g.adj[k] - base) * L;
-                            for (int t = 0; t < L; ++t) h[t] = 0;
-                        }
-                    }
-                }
+        const bool dense = s_over != 0;                     // uniform after the barrier
+        if (dense)
+            for (int32_t kv = wid; kv < nV; kv += nwarp) {
+                int tv;
+                const int64_t sv = u_slot(ub, uoff, kv, tv);
+                wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, dense_rows);
+            }
+        __syncthreads();
+        for (int phase = 1; phase < (dense ? 3 : 2); ++phase) {
+            for (int32_t kv = wid; kv < nV; kv += nwarp) {
+                int tv;
+                const int64_t sv = u_slot(ub, uoff, kv, tv);
+                if (dense) wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, phase, lane, dense_rows);
+                else wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, phase, lane, hash_rows);
             }
             __syncthreads();
         }
@@ -730,7 +839,8 @@ __device__ __forceinline__ uint32_t t_hash(int32_t x, int lgcap) {
     return ((uint32_t)x * 2654435761u) >> (32 - lgcap);
 }
 
-// T as an open-addressing set (capacity 2^lgcap >= 2|T|, entries -1 when
+// T as an open-addressing set (capacity 2^lgcap >= 2|T|, 4|T| for the warp
+// sets of k_clique; entries -1 when
 // empty), built by the group.
 __device__ void t_set_build(const int32_t *T, int32_t nT, int32_t *set, int lgcap, int gsize, int gr) {
     const int cap = 1 << lgcap;
@@ -850,7 +960,7 @@ __device__ void clique_pairs(const GraphView &g, const int32_t *T, int32_t nT, c
 // Warp per edge (edges with |T| <= big_t): K into kmat.
 __global__ void __launch_bounds__(256) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
     __shared__ unsigned sKw[8][kMaxL * kMaxL];
-    __shared__ int32_t setw[8][512];
+    __shared__ int32_t setw[8][1024];
     const int L = g.L, LL = L * L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned *sK = sKw[wid];
@@ -869,7 +979,7 @@ __global__ void __launch_bounds__(256) k_clique(GraphView g, CountView cv, int64
         int32_t ts[kMaxL + 1];
         t_bounds(cv, L, e, ts);
         int lg = 1;
-        while ((1 << lg) < 2 * nT) ++lg;
+        while ((1 << lg) < 4 * nT) ++lg;
         clique_pairs(g, cv.tlist + cv.toffs[er], nT, ts, sK, setw[wid], lg, 32, lane);
         __syncwarp();
         for (int k = lane; k < LL; k += 32) km[k] = sK[(k / L) * kMaxL + (k % L)];
@@ -1274,6 +1384,7 @@ void prepare_edges(Graph &G, int k, cudaStream_t s) {
     raise_smem_limit((const void *)k_edge3, hist_bytes(G.L, 3));
     raise_smem_limit((const void *)k_epi4, hist_bytes(G.L, 4));
     raise_smem_limit((const void *)k_clique_big, kBigSetSmem * sizeof(int32_t));
+    raise_smem_limit((const void *)k_wedge_heavy, (size_t)kHeavyCap * (1 + G.L) * sizeof(int32_t));
     if (k == 4 && !G.set_scratch.p) {
         // a set of capacity >= 2 max degree per CTA, for edges whose T exceeds shared memory
         int64_t cap = 1;
@@ -1487,7 +1598,8 @@ static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
     if (G.n_hubs > 0) launches += launch_hubs(G, c, s);
     if (G.n_anchors_heavy > 0) {
         KernelTimer kt(G, s, "k_wedge_heavy");
-        k_wedge_heavy<<<G.n_tables, kAnchorThreads, 0, s>>>(gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy,
+        k_wedge_heavy<<<G.n_tables, kAnchorThreads, (size_t)kHeavyCap * (1 + L) * sizeof(int32_t), s>>>(
+            gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy,
                                                              c.n0, c.n1);
         ++launches;
     }
