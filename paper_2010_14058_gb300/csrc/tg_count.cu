@@ -724,6 +724,19 @@ __device__ void flush_hist(unsigned long long *hist, int G, unsigned long long *
     }
 }
 
+// the sum of `copies` histograms of one graph into gacc; clears them
+__device__ void flush_hist_copies(unsigned long long *hist, int hw, int copies, int G, unsigned long long *gacc,
+                                  int graph, int gsize, int gr) {
+    for (int s = gr; s < G; s += gsize) {
+        unsigned long long v = 0;
+        for (int c = 0; c < copies; ++c) {
+            v += hist[c * hw + s];
+            hist[c * hw + s] = 0;
+        }
+        if (v) atomicAdd(&gacc[(int64_t)graph * G + s], v);
+    }
+}
+
 struct Tile {
     int64_t begin, end;
     int32_t graph, pad;
@@ -1028,15 +1041,48 @@ __device__ __forceinline__ long long lane_get(long long v, int t) { return __shf
 // inclusion-exclusion of Thm. 1 over S_i, S_j, T, I; then Lemmas 1-4).
 // Lane l holds entry k = l (and k = l + 32 when L*L > 32) of each L x L
 // matrix, (x, y) = (k / L, k % L); transposed entries come by shuffle.
+// Shared memory of k_epi4: `copies` histograms of G(L) u64 (warp w adds into
+// copy w % copies, so fewer warps contend per entry), then the multiset
+// rank tables: rank2[p][q], rank3[p][q][t], rank4[p][q][pair] (uint16).
+__host__ __device__ __forceinline__ size_t epi4_hist_words(int L) { return (size_t)((global_slots(L, 4) + 1) & ~1); }
+__host__ __device__ __forceinline__ size_t epi4_smem_bytes(int L, int copies) {
+    const int P = L * (L + 1) / 2;
+    return epi4_hist_words(L) * copies * sizeof(unsigned long long) +
+           (size_t)(L * L + L * L * L + L * L * P + 1) * sizeof(uint16_t);
+}
+
 __global__ void __launch_bounds__(256, 3) k_epi4(GraphView g, CountView cv, const Tile *__restrict__ tiles,
                                              int64_t n_tiles, int64_t row_base, uint32_t *per_edge_out,
-                                             unsigned long long *gacc) {
-    extern __shared__ unsigned long long hist[];
+                                             unsigned long long *gacc, int copies) {
+    extern __shared__ unsigned long long hist_all[];
     const int L = g.L, LL = L * L, P = L * (L + 1) / 2;
     const int G = (int)global_slots(L, 4);
     const int S = (int)per_edge_slots(L, 4);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int s = threadIdx.x; s < G; s += blockDim.x) hist[s] = 0;
+    const int HW = (int)epi4_hist_words(L);
+    unsigned long long *hist = hist_all + (wid % copies) * HW;
+    uint16_t *rank2 = reinterpret_cast<uint16_t *>(hist_all + (size_t)copies * HW);
+    uint16_t *rank3 = rank2 + LL;
+    uint16_t *rank4 = rank3 + LL * L;
+    for (int s = threadIdx.x; s < copies * HW; s += blockDim.x) hist_all[s] = 0;
+    for (int k = threadIdx.x; k < LL * P; k += blockDim.x) {
+        const int pq = k / P, pi = k % P;
+        int t = 0;
+        while (pair_idx(L, t, L - 1) < pi) ++t;
+        int ms[4] = {pq / L, pq % L, t, t + (pi - pair_idx(L, t, t))};
+        sort4(ms);
+        rank4[k] = (uint16_t)multiset_rank_dev(L, 4, ms);
+    }
+    for (int k = threadIdx.x; k < LL * L; k += blockDim.x) {
+        int ms[3] = {k / LL, (k / L) % L, k % L};
+        sort3(ms);
+        rank3[k] = (uint16_t)multiset_rank_dev(L, 3, ms);
+    }
+    for (int k = threadIdx.x; k < LL; k += blockDim.x) {
+        int ms[2] = {k / L < k % L ? k / L : k % L, k / L < k % L ? k % L : k / L};
+        rank2[k] = (uint16_t)multiset_rank_dev(L, 2, ms);
+    }
+    const int off1 = gblock_off(L, 1), off2 = gblock_off(L, 2), off4 = gblock_off(L, 3), c4 = multichoose(L, 4);
     __syncthreads();
     int cur_graph = -1;
     const int kA = lane, kB = lane + 32;                     // this lane's matrix entries
@@ -1047,7 +1093,7 @@ __global__ void __launch_bounds__(256, 3) k_epi4(GraphView g, CountView cv, cons
         const Tile tile = tiles[ti];
         if (tile.graph != cur_graph) {
             __syncthreads();
-            if (cur_graph >= 0) flush_hist(hist, G, gacc, cur_graph, blockDim.x, threadIdx.x);
+            if (cur_graph >= 0) flush_hist_copies(hist_all, HW, copies, G, gacc, cur_graph, blockDim.x, threadIdx.x);
             __syncthreads();
             cur_graph = tile.graph;
         }
@@ -1146,16 +1192,11 @@ __global__ void __launch_bounds__(256, 3) k_epi4(GraphView g, CountView cv, cons
                     row[lane] = sat32(s3, cv.status);
                     row[L + lane] = sat32(c, cv.status);
                 }
-                int ms[3] = {p, q, lane};
-                sort3(ms);
-                const int r = multiset_rank_dev(L, 3, ms);
-                if (s3) atomicAdd(&hist[gblock_off(L, 1) + r], (unsigned long long)s3);
-                if (c) atomicAdd(&hist[gblock_off(L, 2) + r], (unsigned long long)c);
+                const int r = rank3[(p * L + q) * L + lane];
+                if (s3) atomicAdd(&hist[off1 + r], (unsigned long long)s3);
+                if (c) atomicAdd(&hist[off2 + r], (unsigned long long)c);
             }
-            if (lane == 0) {
-                int ms[2] = {p < q ? p : q, p < q ? q : p};
-                atomicAdd(&hist[multiset_rank_dev(L, 2, ms)], 1ull);
-            }
+            if (lane == 0) atomicAdd(&hist[rank2[p * L + q]], 1ull);
             // orbits, one type pair (t <= u) per lane (two rounds when P > 32)
             for (int base = 0; base < P; base += 32) {
                 const int pi = base + lane;
@@ -1199,21 +1240,20 @@ __global__ void __launch_bounds__(256, 3) k_epi4(GraphView g, CountView cv, cons
                     gv[6] = ct * (at + bt) - gv[7];
                     gv[8] = ct * (ct - 1) / 2 - gv[9];
                 }
-                int ms[4] = {p, q, t, u};
-                sort4(ms);
-                const int r = multiset_rank_dev(L, 4, ms);
+                const int r = rank4[(p * L + q) * P + pi];
+#pragma unroll
                 for (int o = 3; o <= 12; ++o) {
                     const long long v = gv[o - 3];
                     ok = ok && v >= 0;
                     if (row) row[2 * L + (o - 3) * P + pi] = sat32(v, cv.status);
-                    if (v > 0) atomicAdd(&hist[gblock_off(L, graphlet_block(o)) + r], (unsigned long long)v);
+                    if (v > 0) atomicAdd(&hist[off4 + (graphlet_block(o) - 3) * c4 + r], (unsigned long long)v);
                 }
                 if (!ok) set_status(cv.status, ST_INTERNAL);
             }
         }
     }
     __syncthreads();
-    if (cur_graph >= 0) flush_hist(hist, G, gacc, cur_graph, blockDim.x, threadIdx.x);
+    if (cur_graph >= 0) flush_hist_copies(hist_all, HW, copies, G, gacc, cur_graph, blockDim.x, threadIdx.x);
 }
 
 // k = 3: 3-node slots and global blocks 0..2 only (warp per edge)
@@ -1380,9 +1420,16 @@ void raise_smem_limit(const void *func, size_t bytes) {
 
 // Allocations and kernel attributes of the per-edge stage (done before any
 // capture).
+// histogram copies of k_epi4: one per warp while they fit in 64 KB
+static int epi4_copies(int L) {
+    int c = 8;
+    while (c > 1 && epi4_hist_words(L) * c * sizeof(unsigned long long) > (64u << 10)) c >>= 1;
+    return c;
+}
+
 void prepare_edges(Graph &G, int k, cudaStream_t s) {
     raise_smem_limit((const void *)k_edge3, hist_bytes(G.L, 3));
-    raise_smem_limit((const void *)k_epi4, hist_bytes(G.L, 4));
+    raise_smem_limit((const void *)k_epi4, epi4_smem_bytes(G.L, epi4_copies(G.L)));
     raise_smem_limit((const void *)k_clique_big, kBigSetSmem * sizeof(int32_t));
     raise_smem_limit((const void *)k_wedge_heavy, (size_t)kHeavyCap * (1 + G.L) * sizeof(int32_t));
     if (k == 4 && !G.set_scratch.p) {
@@ -1649,8 +1696,9 @@ static int64_t launch_edges4(Graph &G, int64_t b, int64_t e, const Tile *tiles, 
     }
     if (n_tiles > 0) {
         KernelTimer kt(G, s, "k_epi4");
-        k_epi4<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), 256, hist_bytes(G.L, 4), s>>>(
-            gv, cv, tiles, n_tiles, row_base, per_edge_out, gacc);
+        const int copies = epi4_copies(G.L);
+        k_epi4<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), 256, epi4_smem_bytes(G.L, copies), s>>>(
+            gv, cv, tiles, n_tiles, row_base, per_edge_out, gacc, copies);
         ++launches;
     }
     TG_CK(cudaGetLastError());
