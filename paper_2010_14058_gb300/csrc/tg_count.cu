@@ -971,7 +971,7 @@ __device__ void clique_pairs(const GraphView &g, const int32_t *T, int32_t nT, c
 }
 
 // Warp per edge (edges with |T| <= big_t): K into kmat.
-__global__ void __launch_bounds__(256) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
+__global__ void __launch_bounds__(256, 6) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
     __shared__ unsigned sKw[8][kMaxL * kMaxL];
     __shared__ int32_t setw[8][1024];
     const int L = g.L, LL = L * L;
@@ -1003,7 +1003,7 @@ __global__ void __launch_bounds__(256) k_clique(GraphView g, CountView cv, int64
 // CTA per edge for the listed edges with a large T; the set of T lives in
 // shared memory up to kBigSetSmem entries, else in this CTA's global slice.
 constexpr int kBigSetSmem = 1 << 12;
-__global__ void __launch_bounds__(256) k_clique_big(GraphView g, CountView cv, int64_t e0,
+__global__ void __launch_bounds__(256, 8) k_clique_big(GraphView g, CountView cv, int64_t e0,
                                                    const int32_t *__restrict__ big_list,
                                                    const unsigned long long *__restrict__ big_count,
                                                    int32_t *set_scratch, int64_t set_stride) {

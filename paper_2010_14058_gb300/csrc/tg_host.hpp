@@ -74,13 +74,15 @@ struct DBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
-// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync).
+// Temporary device buffer of one call, stream-ordered on `st`, from the
+// same library pool (which keeps freed blocks mapped for the life of the
+// process instead of returning them to the driver at synchronisations).
 struct TBuf {
     void *p = nullptr;
     cudaStream_t s = nullptr;
     TBuf(size_t b, cudaStream_t st) : s(st) {
         if (b == 0) b = 16;
-        TG_CK(cudaMallocAsync(&p, b, s));
+        TG_CK(cudaMallocFromPoolAsync(&p, b, device_pool(), s));
     }
     TBuf(const TBuf &) = delete;
     TBuf &operator=(const TBuf &) = delete;

@@ -93,13 +93,20 @@ __host__ __device__ inline int64_t global_slots(int L, int k) {
 }
 
 // first index in [lo, hi) with a[idx] >= key (a sorted ascending)
+// First position in a[lo, hi) (sorted) whose value is >= key, else hi.
+// Branch-free halving of a 32-bit length (ceil(log2(hi - lo)) steps, the
+// same for every lane searching a segment of the same length).
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *__restrict__ a, int64_t lo, int64_t hi,
                                                    int32_t key) {
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+    if (hi <= lo) return lo;
+    const int32_t *base = a + lo;
+    uint32_t n = (uint32_t)(hi - lo);
+    while (n > 1) {
+        const uint32_t half = n >> 1;
+        base = __ldg(base + half) < key ? base + half : base;
+        n -= half;
     }
-    return lo;
+    return (base - a) + (__ldg(base) < key ? 1 : 0);
 }
 
 __device__ __forceinline__ int64_t seg_begin(const GraphView &g, int64_t x, int t) {
