@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "serve"],
                     help="plain: one graph (the headline line); batched: the ego-network batch vs per-graph launches")
     ap.add_argument("--graphs", type=int, default=8192, help="graphs in the batched workload")
+    ap.add_argument("--tune-graphs", type=int, default=256,
+                    help="batched: graphs of the sub-batch the autotuner measures (0: library defaults)")
     ap.add_argument("--rate", type=float, default=200_000 / 60, help="serving: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=1.0, help="serving: seconds of arrivals")
     ap.add_argument("--pool", type=int, default=128, help="serving: distinct request graphs")
@@ -448,9 +450,23 @@ def run_batched(args):
     col = torch.as_tensor(u["col"], device=dev)
     ty = torch.as_tensor(u["types"], device=dev)
     torch.cuda.synchronize()
+    # autotuned knobs, measured on a sub-batch of the first graphs
+    tuned = None
+    if args.tune_graphs > 0:
+        from paper_2010_14058_gb300 import autotune
+        k = min(args.tune_graphs, ng)
+        no = u["node_off"]
+        nk, zk = int(no[k]), int(u["row_ptr"][int(no[k])])
+        t = time.perf_counter()
+        tuned = autotune.tune(rp[:nk + 1], col[:zk], ty[:nk], L, node_off=no[:k + 1], reps=1, store=False,
+                              stream=stream)
+        tuned["tune_s"] = round(time.perf_counter() - t, 1)
+        tuned["sub_batch_graphs"] = k
+        log(f"autotune on {k} graphs: {tuned['options']} ({tuned['default_ms']} -> {tuned['ms']} ms)")
+    options = tuned["options"] if tuned else None
     # batched: one handle, one captured graph
     t = time.perf_counter()
-    h = tg.tg_build_batch(u["node_off"], rp, col, ty, L, stream=stream)
+    h = tg.tg_build_batch(u["node_off"], rp, col, ty, L, options=options, stream=stream)
     torch.cuda.synchronize()
     build_batch_s = time.perf_counter() - t
     gl_b = torch.zeros((ng, G), dtype=torch.int64, device=dev)
@@ -501,7 +517,9 @@ def run_batched(args):
                        "parent": "Chung-Lu n=4e6 m=4e7 gamma=2.3 max weight 2e4", "generation_s": round(gen_s, 1)},
             "batched": {"count_ms": round(batch_ms, 3), "edges_per_s": round(m / (batch_ms / 1e3), 1),
                         "build_s": round(build_batch_s, 3), "launches_per_count": launches_batch,
-                        "status": tg.STATUS[status_b]},
+                        "status": tg.STATUS[status_b],
+                        "autotune": None if tuned is None else {x: tuned[x] for x in (
+                            "options", "default_ms", "ms", "sub_batch_graphs", "tune_s", "signature")}},
             "plain_per_graph": {"count_ms": round(plain_ms, 3), "edges_per_s": round(m / (plain_ms / 1e3), 1),
                                 "build_s": round(build_plain_s, 3), "status": tg.STATUS[status_p]},
             "speedup_count": round(plain_ms / batch_ms, 2),
@@ -531,7 +549,9 @@ def run_serve(args):
     trace = serve.poisson_trace(pool, args.rate, args.duration, seed=20201029 + 5)
     warm = serve.poisson_trace(pool, 200.0, 0.2, seed=1)
     serve.Server(workers=4).run(warm)
-    served = serve.Server(budget_bytes=40 << 30, workers=4).run(trace)
+    srv = serve.Server(budget_bytes=40 << 30, workers=4, resident_bytes=16 << 30)
+    served = srv.run(trace)
+    srv.close()
     plain = serve.Server(budget_bytes=40 << 30, workers=1, batching=False).run(trace)
     same = all(np.array_equal(a.totals, b.totals) and a.status == 0 and b.status == 0 for a, b in zip(served, plain))
     s1, s0 = serve.summarize(served, trace), serve.summarize(plain, trace)
@@ -540,7 +560,7 @@ def run_serve(args):
             "config": {"workload": "poisson_requests", "rate_per_s": args.rate, "arrival_seconds": args.duration,
                        "requests": len(trace), "edges": s1["edges"], "pool_graphs": args.pool,
                        "request_mix": "Chung-Lu gamma=2.2, m log-uniform [100, 1e6], n=m/5, L uniform 3..8",
-                       "budget_gb": 40, "workers": 4, "pool_generation_s": round(gen_s, 1)},
+                       "budget_gb": 40, "resident_gb": 16, "workers": 4, "pool_generation_s": round(gen_s, 1)},
             "served": s1, "plain_sequential": s0, "results_identical": bool(same)}
     print(json.dumps(line), flush=True)
 

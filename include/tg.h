@@ -116,7 +116,8 @@ typedef struct {
 typedef struct {
     int32_t light_edge_max_degree;    /* edges whose triangle set T has at most max(this, 32) nodes:
                                          warp per edge in the 4-clique pass (CTA per edge above) */
-    int32_t light_anchor_max_wedges;  /* wedge anchors with at most this many wedges: warp per anchor */
+    int32_t light_anchor_max_wedges;  /* wedge anchors with at most this many wedges: warp per anchor
+                                         (at most 2048, and what one CTA's shared memory holds for L) */
     int32_t anchor_table_budget_mb;   /* device memory for per-CTA wedge tables */
     int32_t ctas_per_sm;              /* resident CTAs per SM for the per-edge kernels */
     int32_t cycle_budget_mb;          /* device memory for the per-slot 4-cycle array; a batch whose

@@ -71,7 +71,7 @@ void build_common(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t n
     }
     o.hub_min_wedges = std::max(o.hub_min_wedges, o.light_anchor_max_wedges);
     o.light_edge_max_degree = std::min(o.light_edge_max_degree, 256);     // warp T list capacity
-    o.light_anchor_max_wedges = std::min(o.light_anchor_max_wedges, 2048);
+    o.light_anchor_max_wedges = std::min({o.light_anchor_max_wedges, 2048, tg::light_anchor_limit(L)});
     o.ctas_per_sm = std::min(std::max(o.ctas_per_sm, 1), 8);
     tg_graph *h = new tg_graph();
     try {

@@ -1402,6 +1402,15 @@ __global__ void k_chunk_t(GraphView g, CountView cv, int64_t e0, int64_t e1, uns
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
+int light_anchor_limit(int L) {
+    int dev = 0, optin = 0;
+    TG_CK(cudaGetDevice(&dev));
+    TG_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int cap = 1;                                              // per-warp hash of k_wedge_light
+    while ((size_t)kLightAnchorWarps * (cap * 2) * (1 + L) * sizeof(int32_t) <= (size_t)optin) cap *= 2;
+    return cap / 2;                                           // capacity >= 2 x wedges
+}
+
 void raise_smem_limit(const void *func, size_t bytes) {
     struct Limit { const void *func; int dev; size_t bytes; };
     static std::mutex mu;

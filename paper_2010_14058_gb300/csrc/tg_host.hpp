@@ -37,6 +37,10 @@ inline void throw_cuda(cudaError_t e, const char *what) {
 // Defined in tg_count.cu.
 void raise_smem_limit(const void *func, size_t bytes);
 
+// Largest light_anchor_max_wedges whose per-warp hashes of k_wedge_light fit
+// one CTA's shared memory for L types.  Defined in tg_count.cu.
+int light_anchor_limit(int L);
+
 #define TG_CK(call) ::tg::throw_cuda((call), #call)
 
 // Stream-ordered memory pool of the current device, owned by the library

@@ -10,6 +10,13 @@ admitting.  A request's latency is its completion time minus its arrival
 time.  Results are the global typed-graphlet totals of each request
 (Problem 2), identical to a standalone tg_count of the same graph.
 
+Requests that name their graph (`key`) and are larger than `small_edges`
+leave their built handle -- the typed CSR and the counting state -- on the
+device after they finish, in LRU order within `resident_bytes`; a later
+request for the same graph is counted on that handle without uploading or
+building anything.  Resident handles count against the memory budget and
+idle ones are released, oldest first, when admission needs the room.
+
 All counting runs in libtg through the binding; this module only moves
 host arrays, streams and bookkeeping.
 """
@@ -18,7 +25,8 @@ from __future__ import annotations
 import queue
 import threading
 import time
-from dataclasses import dataclass, field
+from collections import OrderedDict
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -38,6 +46,7 @@ class Request:
     col: np.ndarray
     types: np.ndarray
     arrival: float = 0.0                  # seconds after the start of the run
+    key: object = None                    # identity of the graph (None: never kept resident)
 
     @property
     def n(self) -> int:
@@ -60,6 +69,7 @@ class Result:
     done: float
     status: int
     group_size: int
+    resident: bool = False                # counted on a handle kept from an earlier request
 
     @property
     def latency(self) -> float:
@@ -71,6 +81,14 @@ class _Group:
     reqs: list
     nbytes: int
     started: float = 0.0
+    handle: object = None                 # resident handle to count on (single request)
+
+
+@dataclass
+class _Resident:
+    handle: object
+    nbytes: int
+    busy: bool = False
 
 
 def _union(reqs: list):
@@ -96,10 +114,14 @@ class Server:
     """Admission by device-memory budget, micro-batching, overlapped workers."""
 
     def __init__(self, budget_bytes: int = 40 << 30, workers: int = 4, small_edges: int = 100_000,
-                 batch_edges: int = 4_000_000, batch_graphs: int = 512, batching: bool = True, device: int = 0):
+                 batch_edges: int = 4_000_000, batch_graphs: int = 512, batching: bool = True, device: int = 0,
+                 resident_bytes: int = 0):
         import torch
         self.torch = torch
         self.budget = int(budget_bytes)
+        self.resident_budget = int(resident_bytes)
+        self._resident: OrderedDict = OrderedDict()       # key -> _Resident, oldest first
+        self._resident_total = 0
         self.workers = max(1, int(workers))
         self.small_edges = small_edges
         self.batch_edges = batch_edges
@@ -111,6 +133,18 @@ class Server:
         self._freed = threading.Condition(self._lock)
 
     # ------------------------------------------------------------ groups
+    def _evict_for(self, need: int) -> None:
+        """Releases idle resident handles, oldest first, until `need` more
+        bytes fit the budget (caller holds the lock)."""
+        for key in list(self._resident):
+            if self._in_use + self._resident_total + need <= self.budget:
+                return
+            r = self._resident[key]
+            if not r.busy:
+                del self._resident[key]
+                self._resident_total -= r.nbytes
+                r.handle.free()
+
     def _take_group(self, pending: list) -> _Group | None:
         """Next admissible group from the arrived requests (FIFO by arrival)."""
         if not pending:
@@ -120,7 +154,14 @@ class Server:
         if need > self.budget:
             raise ValueError(f"request {head.rid} needs {need} bytes, more than the budget")
         with self._lock:
-            if self._in_use + need > self.budget:
+            res = self._resident.get(head.key) if head.key is not None else None
+            if res is not None and not res.busy:               # counted on its resident handle
+                res.busy = True
+                self._resident.move_to_end(head.key)
+                pending.pop(0)
+                return _Group([head], 0, handle=res.handle)
+            self._evict_for(need)
+            if self._in_use + self._resident_total + need > self.budget:
                 return None
             group = [pending.pop(0)]
             total_m, total_b = head.m, need
@@ -130,7 +171,7 @@ class Server:
                     r = pending[k]
                     nb = r.bytes_needed()
                     if (r.L == head.L and r.m <= self.small_edges and total_m + r.m <= self.batch_edges
-                            and self._in_use + total_b + nb <= self.budget):
+                            and self._in_use + self._resident_total + total_b + nb <= self.budget):
                         group.append(pending.pop(k))
                         total_m += r.m
                         total_b += nb
@@ -139,10 +180,41 @@ class Server:
             self._in_use += total_b
         return _Group(group, total_b)
 
-    def _release(self, nbytes: int) -> None:
+    def _finish(self, grp: _Group, h) -> None:
+        """After a group: its handle becomes resident (large keyed single
+        requests, while resident_bytes allows) or is freed; its reservation
+        is returned."""
+        r = grp.reqs[0]
         with self._lock:
-            self._in_use -= nbytes
+            if grp.handle is not None:                         # resident hit: stays resident
+                self._resident[r.key].busy = False
+            elif (h is not None and len(grp.reqs) == 1 and r.key is not None and r.m > self.small_edges
+                  and r.key not in self._resident and self.resident_budget > 0):
+                nb = max(h.device_bytes, grp.nbytes)
+                if nb <= self.resident_budget:
+                    while self._resident_total + nb > self.resident_budget:
+                        idle = [k for k, v in self._resident.items() if not v.busy]
+                        if not idle:
+                            break
+                        old = self._resident.pop(idle[0])
+                        self._resident_total -= old.nbytes
+                        old.handle.free()
+                    if self._resident_total + nb <= self.resident_budget:
+                        self._resident[r.key] = _Resident(h, nb)
+                        self._resident_total += nb
+                        h = None
+            self._in_use -= grp.nbytes
             self._freed.notify_all()
+        if h is not None and grp.handle is None:
+            h.free()
+
+    def close(self) -> None:
+        """Releases every resident handle."""
+        with self._lock:
+            for r in self._resident.values():
+                r.handle.free()
+            self._resident.clear()
+            self._resident_total = 0
 
     # ------------------------------------------------------------ worker
     def _run_group(self, grp: _Group, stream, t0: float) -> list:
@@ -152,7 +224,9 @@ class Server:
         lay = tg.tg_layout(L, 4)
         G = lay["global_slots"]
         with torch.cuda.stream(stream):
-            if len(reqs) == 1:
+            if grp.handle is not None:
+                h = grp.handle
+            elif len(reqs) == 1:
                 r = reqs[0]
                 h = tg.tg_build(torch.from_numpy(r.row_ptr).to("cuda", non_blocking=False),
                                 torch.from_numpy(r.col).to("cuda"), torch.from_numpy(r.types).to("cuda"), L,
@@ -165,11 +239,10 @@ class Server:
             tg.tg_count(h, 4, None, out, stream=stream)
             host = out.to("cpu", non_blocking=False)
             status = tg.tg_query_status(h)
-            h.free()
         done = time.perf_counter() - t0
-        res = [Result(r.rid, host[k].numpy().copy(), r.arrival, grp.started, done, status, len(reqs))
-               for k, r in enumerate(reqs)]
-        return res
+        res = [Result(r.rid, host[k].numpy().copy(), r.arrival, grp.started, done, status, len(reqs),
+                      grp.handle is not None) for k, r in enumerate(reqs)]
+        return res, h
 
     # ------------------------------------------------------------ run
     def run(self, requests: list, realtime: bool = True) -> list:
@@ -191,14 +264,15 @@ class Server:
                 grp = work.get()
                 if grp is None:
                     return
+                h = None
                 try:
-                    out = self._run_group(grp, stream, t0)
+                    out, h = self._run_group(grp, stream, t0)
                     with res_lock:
                         results.extend(out)
                 except Exception as exc:  # reported after the run
                     errors.append(exc)
                 finally:
-                    self._release(grp.nbytes)
+                    self._finish(grp, h)
 
         threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.workers)]
         for th in threads:
@@ -238,7 +312,8 @@ def summarize(results: list, requests: list) -> dict:
     return {"requests": len(results), "edges": int(edges), "span_s": round(float(span), 3),
             "edges_per_s": round(edges / span, 1), "p50_ms": round(float(np.percentile(lat, 50) * 1e3), 3),
             "p99_ms": round(float(np.percentile(lat, 99) * 1e3), 3), "mean_ms": round(float(lat.mean() * 1e3), 3),
-            "mean_group": round(float(np.mean([r.group_size for r in results])), 2)}
+            "mean_group": round(float(np.mean([r.group_size for r in results])), 2),
+            "resident_hits": int(sum(r.resident for r in results))}
 
 
 def request_pool(count: int, seed: int, m_min: int = 100, m_max: int = 1_000_000, gamma: float = 2.2,
@@ -269,7 +344,8 @@ def poisson_trace(pool: list, rate_per_s: float, duration_s: float, seed: int) -
         t += rng.exponential(1.0 / rate_per_s)
         if t > duration_s:
             break
-        g = pool[int(rng.integers(len(pool)))]
-        out.append(Request(rid, g["L"], g["row_ptr"], g["col"], g["types"], t))
+        k = int(rng.integers(len(pool)))
+        g = pool[k]
+        out.append(Request(rid, g["L"], g["row_ptr"], g["col"], g["types"], t, key=k))
         rid += 1
     return out

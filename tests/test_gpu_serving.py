@@ -50,3 +50,17 @@ def test_summary(trace):
     res = serve.Server(workers=2).run(trace)
     s = serve.summarize(res, trace)
     assert s["requests"] == len(trace) and s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_resident_handles(trace):
+    # graphs above 5,000 edges stay on the device after their first request;
+    # repeats are counted on those handles, with the same totals
+    srv = serve.Server(budget_bytes=4 << 30, workers=3, small_edges=5_000, batch_edges=200_000,
+                       resident_bytes=1 << 30)
+    res = srv.run(trace)
+    alone = serve.Server(workers=1, batching=False).run(trace, realtime=False)
+    srv.close()
+    assert sum(r.resident for r in res) > 0
+    for a, b in zip(res, alone):
+        assert a.status == 0
+        np.testing.assert_array_equal(a.totals, b.totals)
