@@ -136,7 +136,7 @@ def load_peaks():
 TRAFFIC = {}
 
 
-def kernel_units(g: dict, light_anchor_max: int = 256, hub_min: int = 1 << 16) -> dict:
+def kernel_units(g: dict, light_anchor_max: int = 64, hub_min: int = 1 << 16) -> dict:
     """Work units of the count kernels, computed on the host from the graph:
     degree-priority wedges (the search for the 4-cycles behind P) split
     by the anchor class the build assigns (light: at most light_anchor_max
@@ -167,7 +167,28 @@ def kernel_units(g: dict, light_anchor_max: int = 256, hub_min: int = 1 << 16) -
             "typed_min_sum": float(mins)}
 
 
-def algorithmic_bytes(u: dict, m: int, L: int, S: int, t_nodes: int) -> dict:
+def clique_units(pe, L: int, big_t: int = 256, chunk: int = 1 << 22) -> dict:
+    """|T_e| (sum of the triangle slots) and K_e (sum of the 4-clique orbit
+    slots g12) of every edge, read from the per-edge rows, summed over the
+    edges counted by k_clique (|T| <= big_t) and by k_clique_big."""
+    import torch
+    P = L * (L + 1) // 2
+    k0 = 2 * L + 9 * P
+    out = {"t_small": 0, "t_big": 0, "k_small": 0, "k_big": 0, "edges_big": 0}
+    for a in range(0, pe.shape[0], chunk):
+        rows = pe[a:a + chunk]
+        T = rows[:, L:2 * L].long().sum(1)
+        K = rows[:, k0:k0 + P].long().sum(1)
+        big = T > big_t
+        out["t_small"] += int(T[~big].sum())
+        out["t_big"] += int(T[big].sum())
+        out["k_small"] += int(K[~big].sum())
+        out["k_big"] += int(K[big].sum())
+        out["edges_big"] += int(big.sum())
+    return out
+
+
+def algorithmic_bytes(u: dict, m: int, L: int, S: int, t_nodes: int, cu: dict | None = None) -> dict:
     """Bytes each count kernel must move at least once in this formulation
     (reads of its inputs and writes of its outputs, intermediates included),
     per launch over the whole graph:
@@ -179,8 +200,11 @@ def algorithmic_bytes(u: dict, m: int, L: int, S: int, t_nodes: int) -> dict:
                   the three L x L sums 24 L^2; per triangle node: its id
                   written 4, two edge ids 8, two typed-triangle rows 8L,
                   its type offsets 4(L+1);
-      k_clique*   per triangle node: its id read 4; per edge: K written 8L^2
-                  (a lower bound: the N+ scans are not counted);
+      k_clique, k_clique_big (edges with |T| up to / above max(light edge
+                  degree, 32)): per triangle node its id read 4, per adjacent
+                  pair inside T one adjacency entry read 4, per edge K written
+                  8L^2 (a lower bound: the misses of the N+ scans are not
+                  counted);
       k_epi4      per edge: endpoints and slots 24, C row 4L, two type
                   offset rows 8(L+1), tsum 24L^2, K 8L^2, the two 4-cycle
                   slot columns 8L^2, tau and delta of both endpoints 32L^2,
@@ -192,7 +216,9 @@ def algorithmic_bytes(u: dict, m: int, L: int, S: int, t_nodes: int) -> dict:
         "k_wedge_heavy": 12.0 * u["wedges_heavy"] + 8.0 * L * u["pairs_heavy"],
         "k_wedge_hub": 12.0 * u["wedges_hub"] + 8.0 * L * u["pairs_hub"],
         "k_tsum": (8.0 + 4 * L + 24 * LL) * m + 4.0 * u["typed_min_sum"] + (12.0 + 12 * L + 4) * t_nodes,
-        "k_clique": 4.0 * t_nodes + 8.0 * LL * m,
+        "k_clique": 4.0 * t_nodes + 8.0 * LL * m if cu is None else
+        4.0 * (cu["t_small"] + cu["k_small"]) + 8.0 * LL * (m - cu["edges_big"]),
+        "k_clique_big": None if cu is None else 4.0 * (cu["t_big"] + cu["k_big"]) + 8.0 * LL * cu["edges_big"],
         "k_epi4": (24.0 + 4 * L + 8 * (L + 1) + 72 * LL + 4 * S) * m,
     }
 
@@ -286,13 +312,11 @@ def run_ours(args):
         gl_host = gl.cpu().numpy()
         b2 = lay["global_block_offset"][2]
         t_nodes = 3 * int(gl_host[b2:b2 + lay["global_block_size"][2]].sum())   # sum_e |T_e|
-        abytes = algorithmic_bytes(units, m, L, S, t_nodes)
+        cu = clique_units(pe, L)
+        units.update({"clique": cu})
+        abytes = algorithmic_bytes(units, m, L, S, t_nodes, cu)
         for name, (kms, nl) in kernel_ms.items():
-            if name == "k_clique_big":
-                continue
-            if name == "k_clique":
-                kms += kernel_ms.get("k_clique_big", [0.0, 0])[0]
-            if name not in abytes or kms <= 0:
+            if abytes.get(name) is None or kms <= 0:
                 continue
             step_ms = kms / args.steps
             gbs = abytes[name] / (step_ms / 1e3) / 1e9

@@ -38,7 +38,7 @@ SPACE = {
     "hub_min_wedges": [1 << 14, 1 << 16, 1 << 18, 1 << 20],
     "ctas_per_sm": [2, 3, 4],
 }
-DEFAULTS = {"light_edge_max_degree": 256, "light_anchor_max_wedges": 256, "hub_min_wedges": 1 << 16, "ctas_per_sm": 4}
+DEFAULTS = {"light_edge_max_degree": 256, "light_anchor_max_wedges": 64, "hub_min_wedges": 1 << 16, "ctas_per_sm": 3}
 
 CACHE_PATH = os.environ.get("TG_AUTOTUNE_CACHE", os.path.join(os.path.dirname(__file__), ".autotune.json"))
 _lock = threading.Lock()

@@ -23,7 +23,8 @@ def test_tune_keeps_counts_and_caches(tmp_path):
     space = {"light_edge_max_degree": [32, 256], "hub_min_wedges": [300, 1 << 16], "ctas_per_sm": [2, 4]}
     path = str(tmp_path / "tune.json")
     entry = autotune.tune(rp, col, ty, g["L"], space=space, reps=1, path=path)
-    assert len(entry["trials"]) == 4
+    new_values = sum(len([v for v in vals if v != autotune.DEFAULTS[k]]) for k, vals in space.items())
+    assert len(entry["trials"]) == 1 + new_values                 # defaults, then each other value once
     assert autotune.cached(entry["signature"], path) == entry["options"]
     h = tg.tg_build(rp, col, ty, g["L"], options=entry["options"])
     gl = torch.zeros(tg.tg_layout(g["L"], 4)["global_slots"], dtype=torch.int64, device="cuda")
