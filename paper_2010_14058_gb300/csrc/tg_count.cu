@@ -882,6 +882,56 @@ __device__ __forceinline__ bool t_set_has(const int32_t *set, int lgcap, int32_t
     return false;
 }
 
+// N+ lists of the 4-clique scan: entries (type << 29 | id) in type order;
+// each thread counts its run of one type of x in a register and adds it to
+// sK[type of w][type of x] when the type changes.
+constexpr int32_t kShort = 64;                // longer N+ lists: scanned by a whole warp
+
+__device__ __forceinline__ void scan_short(const GraphView &g, int32_t w, int32_t dplus, int tw, const int32_t *set,
+                                           int lgcap, unsigned *sK) {
+    int64_t sx = g.plus_off[w];
+    const int64_t se = sx + dplus;
+    unsigned c = 0;
+    uint32_t cur = 0;
+    auto take = [&](uint32_t ent) {
+        const uint32_t q = ent >> kTypeShift;
+        if (q != cur) {
+            if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
+            c = 0;
+            cur = q;
+        }
+        c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
+    };
+    for (; sx + 4 <= se; sx += 4) {
+        const uint32_t x0 = (uint32_t)g.plus_adj[sx], x1 = (uint32_t)g.plus_adj[sx + 1];
+        const uint32_t x2 = (uint32_t)g.plus_adj[sx + 2], x3 = (uint32_t)g.plus_adj[sx + 3];
+        take(x0);
+        take(x1);
+        take(x2);
+        take(x3);
+    }
+    for (; sx < se; ++sx) take((uint32_t)g.plus_adj[sx]);
+    if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
+}
+
+__device__ __forceinline__ void scan_long(const GraphView &g, int32_t w, int tw, const int32_t *set, int lgcap,
+                                          unsigned *sK, int lane) {
+    const int64_t pb = g.plus_off[w], pe = g.plus_off[w + 1];
+    unsigned c = 0;
+    uint32_t cur = 0;
+    for (int64_t sx = pb + lane; sx < pe; sx += 32) {
+        const uint32_t ent = (uint32_t)g.plus_adj[sx];
+        const uint32_t q = ent >> kTypeShift;
+        if (q != cur) {
+            if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
+            c = 0;
+            cur = q;
+        }
+        c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
+    }
+    if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
+}
+
 // 4-clique pairs of one edge by a group of `gsize` threads (whole warps):
 // adjacent pairs (w, x) of T, each counted once as (smaller id, larger id),
 // into sK[type of smaller][type of larger].  Few pairs: every pair checked
@@ -910,62 +960,19 @@ __device__ void clique_pairs(const GraphView &g, const int32_t *T, int32_t nT, c
     }
     t_set_build(T, nT, set, lgcap, gsize, gr);
     // members in blocks of 32 per warp: each lane scans N+ of its own member
-    // when it is short (type segment by type segment, 4 loads in flight);
-    // long ones are scanned by the whole warp
-    constexpr int32_t kShort = 64;
+    // when it is short (4 loads in flight); long ones are scanned by the
+    // whole warp
     for (int32_t base = wid * 32; base < nT; base += nwarp * 32) {
         const int32_t k = base + lane;
         const bool valid = k < nT;
         const int32_t w = valid ? T[k] : 0;
         const int32_t dplus = valid ? g.nplus[w] : 0;
-        if (valid && dplus <= kShort && dplus > 0) {
-            const int tw = type_of_index(ts, L, k);
-            int64_t sx = g.plus_off[w];
-            const int64_t se = sx + dplus;
-            unsigned c = 0;
-            uint32_t cur = 0;
-            auto take = [&](uint32_t ent) {                  // entries come in type order
-                const uint32_t q = ent >> kTypeShift;
-                if (q != cur) {
-                    if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
-                    c = 0;
-                    cur = q;
-                }
-                c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
-            };
-            for (; sx + 4 <= se; sx += 4) {
-                const uint32_t x0 = (uint32_t)g.plus_adj[sx], x1 = (uint32_t)g.plus_adj[sx + 1];
-                const uint32_t x2 = (uint32_t)g.plus_adj[sx + 2], x3 = (uint32_t)g.plus_adj[sx + 3];
-                take(x0);
-                take(x1);
-                take(x2);
-                take(x3);
-            }
-            for (; sx < se; ++sx) take((uint32_t)g.plus_adj[sx]);
-            if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
-        }
+        if (valid && dplus <= kShort && dplus > 0) scan_short(g, w, dplus, type_of_index(ts, L, k), set, lgcap, sK);
         unsigned longs = __ballot_sync(0xffffffffu, valid && dplus > kShort);
         while (longs) {
             const int src = __ffs(longs) - 1;
             longs &= longs - 1;
-            const int32_t lw = __shfl_sync(0xffffffffu, w, src);
-            const int ltw = type_of_index(ts, L, base + src);
-            // N+(lw) as one list of (type << 29 | id) in type order: each
-            // lane counts its run of one type and flushes when it changes
-            const int64_t pb = g.plus_off[lw], pe = g.plus_off[lw + 1];
-            unsigned c = 0;
-            uint32_t cur = 0;
-            for (int64_t sx = pb + lane; sx < pe; sx += 32) {
-                const uint32_t ent = (uint32_t)g.plus_adj[sx];
-                const uint32_t q = ent >> kTypeShift;
-                if (q != cur) {
-                    if (c) atomicAdd(&sK[ltw * kMaxL + cur], c);
-                    c = 0;
-                    cur = q;
-                }
-                c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
-            }
-            if (c) atomicAdd(&sK[ltw * kMaxL + cur], c);
+            scan_long(g, __shfl_sync(0xffffffffu, w, src), type_of_index(ts, L, base + src), set, lgcap, sK, lane);
         }
     }
 }

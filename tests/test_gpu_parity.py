@@ -233,3 +233,27 @@ def test_repeated_counts_are_identical():
     for pe, gl in outs[1:]:
         assert torch.equal(pe, outs[0][0]) and torch.equal(gl, outs[0][1])
     h.free()
+
+
+def test_big_t_with_long_neighbour_lists():
+    # edge (0, 1) has |T| = 360 (one CTA) and every triangle node has ~1,100
+    # neighbours of higher priority (hubs padded with private leaves), all
+    # scanned warp-wide
+    nt, nh, leaves = 360, 1100, 760
+    T = np.arange(2, 2 + nt)
+    H = np.arange(2 + nt, 2 + nt + nh)
+    first_leaf = 2 + nt + nh
+    n = first_leaf + nh * leaves
+    eu = [np.array([0]), np.zeros(nt, np.int64), np.ones(nt, np.int64), T[:-1], np.repeat(T, nh),
+          np.repeat(H, leaves)]
+    ev = [np.array([1]), T, T, T[1:], np.tile(H, nt), first_leaf + np.arange(nh * leaves)]
+    eu, ev = np.concatenate(eu).astype(np.int32), np.concatenate(ev).astype(np.int32)
+    order = np.lexsort((ev, eu))
+    types = np.random.default_rng(8).integers(0, 3, n).astype(np.uint8)
+    g = graphgen.csr_from_edges(n, eu[order], ev[order], types, 3, "long N+ lists")
+    pe, gl, st = gpu_count(g)
+    assert st == 0, tg.STATUS[st]
+    ids = np.array([0, 1, 2, 3, 400, 700, 721, 722, 1000, 5000])   # (0,1), (0,t), (1,t), (t,t+1), (t,h)
+    rows_o, _ = oracle.paper_edges(g, ids)
+    np.testing.assert_array_equal(pe[ids], rows_o)
+    assert pe[0, 3:6].sum() == nt                           # the triangle slots of edge (0, 1)
