@@ -358,6 +358,38 @@ def run_ours(args):
         e2e = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(bo)}
 
+    # the same end to end with the sparse per-edge form (only nonzero counts
+    # cross PCIe: row offsets, uint16 slots, uint32 counts)
+    e2e_sparse = None
+    if not args.no_e2e and rank == 0:
+        h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
+        d_off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+        nnz = tg.tg_count_sparse(h, 4, d_off, stream=stream)
+        h.free()
+        d_slot = torch.empty(nnz, dtype=torch.int16, device=dev)
+        d_val = torch.empty(nnz, dtype=torch.int32, device=dev)
+        d_gl = torch.empty(G, dtype=torch.int64, device=dev)
+        p_off = torch.empty(m + 1, dtype=torch.int64).pin_memory()
+        p_slot = torch.empty(nnz, dtype=torch.int16).pin_memory()
+        p_val = torch.empty(nnz, dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
+            tg.tg_count_sparse(h, 4, d_off, d_slot, d_val, d_gl, stream=stream)
+            with torch.cuda.stream(stream):
+                p_off.copy_(d_off, non_blocking=True)
+                p_slot.copy_(d_slot, non_blocking=True)
+                p_val.copy_(d_val, non_blocking=True)
+                h_gl.copy_(d_gl, non_blocking=True)
+            h.free()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        bo = p_off.numel() * 8 + nnz * 6 + G * 8
+        e2e_sparse = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+                      "d2h_bytes_per_step": int(bo), "nonzero_pairs": int(nnz),
+                      "pairs_per_edge": round(nnz / max(m, 1), 2)}
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(g, args.cpu_seconds)
@@ -373,7 +405,8 @@ def run_ours(args):
                        "step": "tg_build + tg_count(k=4) + tg_free, device-resident inputs and outputs"},
             "status": tg.STATUS[status], "roofline": roofline, "kernel_roofline": per_kernel,
             "compulsory_roofline": compulsory, "kernel_share": kernel_share, "units": units,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches[0]),
+            "cpu_baseline": cpu, "e2e": e2e, "e2e_sparse": e2e_sparse, "clocks": clk,
+            "gpu_launches": int(launches[0]),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

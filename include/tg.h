@@ -209,6 +209,23 @@ tg_status tg_count_range(tg_graph *g, int32_t k, int64_t e_begin, int64_t e_end,
 tg_status tg_finalize_global(int32_t L, int32_t k, int32_t ngraphs, const int64_t *raw,
                              int64_t *out);
 
+/* Problem 1 in the sparse form of Sec. 4.6 (X_ij: only the nonzero counts
+ * of each edge).  Edge e's pairs are entries row_off[e] .. row_off[e+1]-1
+ * of slot / value: slot = its per-edge slot in the dense layout of
+ * tg_layout (increasing), value = the count.  row_off: int64 [m+1]; slot:
+ * uint16, value: uint32, `cap` entries each; all three DEVICE memory owned
+ * by the caller (row_off may be NULL).  *nnz (host) receives the number of
+ * pairs.  With slot = value = NULL the call only sizes: it fills row_off and
+ * *nnz and returns TG_OK.  If the pairs exceed cap, the ones that fit whole
+ * windows may have been written, *nnz is the capacity needed and the call
+ * returns TG_ERR_TOO_LARGE.  global_out as in tg_count (host or device, may
+ * be NULL).  The edges are counted in windows whose dense rows take at most
+ * 1 GB of library memory; synchronises `stream` once per window.  Errors:
+ * TG_ERR_INVALID_ARG (k, NULL nnz, only one of slot/value, host arrays),
+ * TG_ERR_TOO_LARGE, TG_ERR_OOM, TG_ERR_CUDA. */
+tg_status tg_count_sparse(tg_graph *g, int32_t k, int64_t *row_off, uint16_t *slot, uint32_t *value,
+                          int64_t cap, int64_t *nnz, int64_t *global_out, void *stream);
+
 /* Batched form: counts every graph of a batch handle with the whole
  * sequence of kernels captured once into a CUDA graph and replayed on later
  * calls with the same (k, per_edge_out, global_out, stream).  Results are

@@ -241,6 +241,31 @@ tg_status tg_count_range(tg_graph *gh, int32_t k, int64_t e_begin, int64_t e_end
     });
 }
 
+tg_status tg_count_sparse(tg_graph *gh, int32_t k, int64_t *row_off, uint16_t *slot, uint32_t *value, int64_t cap,
+                          int64_t *nnz, int64_t *global_out, void *stream) {
+    return guarded([&] {
+        if (!gh || (k != 3 && k != 4) || !nnz || cap < 0 || (!slot) != (!value))
+            throw Error{TG_ERR_INVALID_ARG, "args"};
+        for (const void *p : {(const void *)row_off, (const void *)slot, (const void *)value})
+            if (p && !tg::is_device_pointer(p)) throw Error{TG_ERR_INVALID_ARG, "sparse arrays must be device memory"};
+        Graph &G = gh->g;
+        cudaStream_t s = (cudaStream_t)stream;
+        G.stream = s;
+        tg::prepare_counting(G, k, s);
+        tg::prepare_edges(G, k, s);
+        const size_t gl_bytes = (size_t)G.ngraphs * tg::global_slots(G.L, k) * sizeof(int64_t);
+        bool gl_staged = false;
+        int64_t *gl = device_out(global_out, gl_bytes, G.stage_gl, gl_staged);
+        TG_CK(cudaMemsetAsync(G.gacc.p, 0, (size_t)G.ngraphs * tg::global_slots(G.L, 4) * sizeof(unsigned long long), s));
+        bool fits = true;
+        *nnz = tg::count_sparse(G, k, row_off, slot, value, cap, fits, s);
+        if (gl) tg::launch_finalize(G, k, gl, s);
+        if (gl_staged) TG_CK(cudaMemcpyAsync(global_out, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
+        TG_CK(cudaStreamSynchronize(s));
+        if (slot && !fits) throw Error{TG_ERR_TOO_LARGE, "sparse capacity"};
+    });
+}
+
 tg_status tg_finalize_global(int32_t L, int32_t k, int32_t ngraphs, const int64_t *raw, int64_t *out) {
     return guarded([&] {
         check_types(L);

@@ -61,6 +61,7 @@ SIGNATURES = {
     "tg_finalize_global": ([_i32, _i32, _i32, _vp, _vp], _i32),
     "tg_count_batch": ([_vp, _i32, _vp, _vp, _vp], _i32),
     "tg_query_status": ([_vp], _i32),
+    "tg_count_sparse": ([_vp, _i32, _vp, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _vp], _i32),
     "tg_status_string": ([_i32], ctypes.c_char_p),
     "tg_last_error": ([], ctypes.c_char_p),
     "tg_last_launch_count": ([_vp], _i64),
@@ -266,6 +267,24 @@ def tg_finalize_global(L: int, k: int, ngraphs: int, raw: np.ndarray) -> np.ndar
     out = np.zeros_like(raw)
     _check(load().tg_finalize_global(L, k, ngraphs, raw.ctypes.data, out.ctypes.data), "tg_finalize_global")
     return out
+
+
+def tg_count_sparse(g: Graph, k: int, row_off=None, slot=None, value=None, global_out=None, stream=None) -> int:
+    """Sparse per-edge counts (device tensors: row_off int64 [m+1], slot
+    int16/uint16, value int32/uint32); returns the number of pairs.  With
+    slot = value = None only sizes.  Raises TGError(TG_ERR_TOO_LARGE) when
+    the pairs exceed the arrays (the needed size is in .nnz)."""
+    cap = 0 if slot is None else int(slot.shape[0])
+    if value is not None and int(value.shape[0]) < cap:
+        cap = int(value.shape[0])
+    nnz = _i64(0)
+    code = load().tg_count_sparse(g.handle, k, _ptr(row_off), _ptr(slot), _ptr(value), cap, ctypes.byref(nnz),
+                                  _ptr(global_out), _stream(stream))
+    if code != 0:
+        err = TGError(code, "tg_count_sparse", tg_last_error())
+        err.nnz = int(nnz.value)
+        raise err
+    return int(nnz.value)
 
 
 def tg_count_batch(g: Graph, k: int, per_edge_out=None, global_out=None, stream=None) -> None:
