@@ -38,6 +38,7 @@ def test_tune_batch():
     graphs = [graphgen.chung_lu(400 + 50 * x, 2500 + 300 * x, 2.2, 120.0, 3, 40 + x) for x in range(6)]
     u = graphgen.concat(graphs)
     rp, col, ty = (torch.as_tensor(u[k], device="cuda") for k in ("row_ptr", "col", "types"))
-    entry = autotune.tune(rp, col, ty, 3, node_off=u["node_off"], space={"light_anchor_max_wedges": [64, 1024]},
-                          reps=1, store=False)
-    assert entry["ngraphs"] == 6 and len(entry["trials"]) == 3        # defaults + two new values
+    space = {"light_anchor_max_wedges": [64, 1024], "ctas_per_sm": [2]}
+    entry = autotune.tune(rp, col, ty, 3, node_off=u["node_off"], space=space, reps=1, store=False)
+    new_values = sum(len([v for v in vals if v != autotune.DEFAULTS[k]]) for k, vals in space.items())
+    assert entry["ngraphs"] == 6 and len(entry["trials"]) == 1 + new_values
