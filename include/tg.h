@@ -226,6 +226,22 @@ tg_status tg_finalize_global(int32_t L, int32_t k, int32_t ngraphs, const int64_
 tg_status tg_count_sparse(tg_graph *g, int32_t k, int64_t *row_off, uint16_t *slot, uint32_t *value,
                           int64_t cap, int64_t *nnz, int64_t *global_out, void *stream);
 
+/* Typed-graphlet weighted graph, the first step of Alg. 5: for the typed
+ * graphlet H = (block, rank) -- block as in tg_layout's global blocks (0
+ * edge, 1 3-path, 2 triangle, 3 4-path, 4 4-star, 5 4-cycle, 6 tailed
+ * triangle, 7 chordal cycle, 8 4-clique), rank = the lexicographic rank of
+ * H's type multiset within the block -- weights[e] = the number of instances
+ * of H that contain both endpoints of edge e, and (if degree != NULL)
+ * degree[x] = sum of weights[e] over the edges e at node x (the
+ * typed-graphlet degree D_xx).  per_edge_rows: this handle's rows from
+ * tg_count with the same k (blocks 0-2 need k = 3 or 4, blocks 3-8 k = 4).
+ * weights: int64 [m] in edge-id order; degree: int64 [n] in the caller's
+ * node ids.  All three DEVICE memory owned by the caller.  Synchronises
+ * `stream`.  Errors: TG_ERR_INVALID_ARG (k, block, rank, NULL, host
+ * memory), TG_ERR_CUDA. */
+tg_status tg_graphlet_weights(tg_graph *g, int32_t k, const uint32_t *per_edge_rows, int32_t block, int64_t rank,
+                              int64_t *weights, int64_t *degree, void *stream);
+
 /* Batched form: counts every graph of a batch handle with the whole
  * sequence of kernels captured once into a CUDA graph and replayed on later
  * calls with the same (k, per_edge_out, global_out, stream).  Results are

@@ -266,6 +266,18 @@ tg_status tg_count_sparse(tg_graph *gh, int32_t k, int64_t *row_off, uint16_t *s
     });
 }
 
+tg_status tg_graphlet_weights(tg_graph *gh, int32_t k, const uint32_t *per_edge_rows, int32_t block, int64_t rank,
+                              int64_t *weights, int64_t *degree, void *stream) {
+    return guarded([&] {
+        if (!gh || (k != 3 && k != 4) || !per_edge_rows || !weights) throw Error{TG_ERR_INVALID_ARG, "args"};
+        for (const void *p : {(const void *)per_edge_rows, (const void *)weights, (const void *)degree})
+            if (p && !tg::is_device_pointer(p)) throw Error{TG_ERR_INVALID_ARG, "arrays must be device memory"};
+        Graph &G = gh->g;
+        G.stream = (cudaStream_t)stream;
+        tg::launch_weights(G, k, per_edge_rows, block, rank, weights, degree, G.stream);
+    });
+}
+
 tg_status tg_finalize_global(int32_t L, int32_t k, int32_t ngraphs, const int64_t *raw, int64_t *out) {
     return guarded([&] {
         check_types(L);

@@ -278,6 +278,9 @@ void prepare_capture(Graph &G, int k, cudaStream_t s);
 int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out,
                   unsigned long long *gacc, bool full, cudaStream_t s);
 int64_t launch_finalize(Graph &G, int k, int64_t *global_out, cudaStream_t s);
+// Typed-graphlet weighted graph (tg_weights.cu).
+void launch_weights(Graph &G, int k, const uint32_t *rows, int block, int64_t rank, int64_t *weights,
+                    int64_t *degree, cudaStream_t s);
 // Sparse per-edge counts (tg_sparse.cu): returns the number of nonzero
 // pairs; writes them only while they fit `cap` (fits = false otherwise).
 int64_t count_sparse(Graph &G, int k, int64_t *row_off, uint16_t *slot, uint32_t *value, int64_t cap, bool &fits,

@@ -62,6 +62,7 @@ SIGNATURES = {
     "tg_count_batch": ([_vp, _i32, _vp, _vp, _vp], _i32),
     "tg_query_status": ([_vp], _i32),
     "tg_count_sparse": ([_vp, _i32, _vp, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _vp], _i32),
+    "tg_graphlet_weights": ([_vp, _i32, _vp, _i32, _i64, _vp, _vp, _vp], _i32),
     "tg_status_string": ([_i32], ctypes.c_char_p),
     "tg_last_error": ([], ctypes.c_char_p),
     "tg_last_launch_count": ([_vp], _i64),
@@ -285,6 +286,14 @@ def tg_count_sparse(g: Graph, k: int, row_off=None, slot=None, value=None, globa
         err.nnz = int(nnz.value)
         raise err
     return int(nnz.value)
+
+
+def tg_graphlet_weights(g: Graph, k: int, per_edge_rows, block: int, rank: int, weights, degree=None,
+                        stream=None) -> None:
+    """W (int64 [m]) and, optionally, D (int64 [n]) of the typed graphlet
+    (block, rank), from this handle's per-edge rows (device tensors)."""
+    _check(load().tg_graphlet_weights(g.handle, k, _ptr(per_edge_rows), block, rank, _ptr(weights), _ptr(degree),
+                                      _stream(stream)), "tg_graphlet_weights")
 
 
 def tg_count_batch(g: Graph, k: int, per_edge_out=None, global_out=None, stream=None) -> None:
