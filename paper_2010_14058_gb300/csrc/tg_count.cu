@@ -765,6 +765,15 @@ __global__ void k_tcount(GraphView g, CountView cv, int64_t e0, int64_t e1, int6
 
 // Warp per edge: T list and the triangle-node sums (Cor. 1; gathers of the
 // typed triangle counts of the edges (i,w), (j,w) and of d_w^t').
+// Acc = uint32_t when the maximum degree is below 2^16 (every sum here is at
+// most |T| x d < 2^32), else unsigned long long.
+__device__ __forceinline__ uint32_t warp_allsum(uint32_t v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_allsum(unsigned long long v) { return warp_allsum_u64(v); }
+
+template <class Acc>
 __global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int64_t e0, int64_t e1) {
     const int L = g.L, LL = L * L;
     const int lane = threadIdx.x & 31;
@@ -776,10 +785,18 @@ __global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int6
         unsigned long long *sum = cv.tsum + er * 3 * LL;
         int32_t pos = 0;
         for (int t = 0; t < L; ++t) {
-            unsigned long long a1[kMaxL], a2[kMaxL], a3[kMaxL];
+            if (cv.C[e * L + t] == 0) {                     // no triangle node of type t
+                if (lane < L) {
+                    sum[t * L + lane] = 0;
+                    sum[LL + t * L + lane] = 0;
+                    sum[2 * LL + t * L + lane] = 0;
+                }
+                continue;
+            }
+            Acc a1[kMaxL], a2[kMaxL], a3[kMaxL];
 #pragma unroll
             for (int q = 0; q < kMaxL; ++q) { a1[q] = 0; a2[q] = 0; a3[q] = 0; }
-            if (cv.C[e * L + t] != 0) {
+            {
                 int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
                 int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
                 bool swapped = false;
@@ -818,11 +835,11 @@ __global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int6
 #pragma unroll
             for (int q = 0; q < kMaxL; ++q) {
                 if (q >= L) break;
-                const unsigned long long v1 = warp_allsum_u64(a1[q]), v2 = warp_allsum_u64(a2[q]), v3 = warp_allsum_u64(a3[q]);
+                const Acc v1 = warp_allsum(a1[q]), v2 = warp_allsum(a2[q]), v3 = warp_allsum(a3[q]);
                 if (lane == q) {
-                    sum[t * L + q] = v1;
-                    sum[LL + t * L + q] = v2;
-                    sum[2 * LL + t * L + q] = v3;
+                    sum[t * L + q] = (unsigned long long)v1;
+                    sum[LL + t * L + q] = (unsigned long long)v2;
+                    sum[2 * LL + t * L + q] = (unsigned long long)v3;
                 }
             }
         }
@@ -1695,7 +1712,8 @@ static int64_t launch_edges4(Graph &G, int64_t b, int64_t e, const Tile *tiles, 
                                         ne + 1, s));
     {
         KernelTimer kt(G, s, "k_tsum");
-        k_tsum<<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e);
+        if (G.max_degree < (1 << 16)) k_tsum<uint32_t><<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e);
+        else k_tsum<unsigned long long><<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e);
         ++launches;
     }
     {

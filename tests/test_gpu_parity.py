@@ -257,3 +257,25 @@ def test_big_t_with_long_neighbour_lists():
     rows_o, _ = oracle.paper_edges(g, ids)
     np.testing.assert_array_equal(pe[ids], rows_o)
     assert pe[0, 3:6].sum() == nt                           # the triangle slots of edge (0, 1)
+
+
+def test_degree_above_65535_uses_wide_sums():
+    # a hub of degree 70,060 (70,000 leaves and a 60-node random cluster that
+    # is also joined to it): the per-edge sums take the 64-bit path
+    leaves, nc = 70_000, 60
+    hub, c0 = 0, 1
+    l0 = c0 + nc
+    rng = np.random.default_rng(61)
+    cl = [(c0 + a, c0 + b) for a in range(nc) for b in range(a + 1, nc) if rng.random() < 0.3]
+    eu = np.concatenate([np.zeros(nc + leaves, np.int64), np.array([a for a, _ in cl])])
+    ev = np.concatenate([np.arange(c0, c0 + nc), np.arange(l0, l0 + leaves), np.array([b for _, b in cl])])
+    order = np.lexsort((ev, eu))
+    n = l0 + leaves
+    g = graphgen.csr_from_edges(n, eu[order].astype(np.int32), ev[order].astype(np.int32),
+                                rng.integers(0, 3, n).astype(np.uint8), 3, "hub of degree 70,060")
+    assert np.diff(g["row_ptr"]).max() >= 1 << 16
+    pe, gl, st = gpu_count(g)
+    assert st == 0, tg.STATUS[st]
+    ids = np.array([0, 5, 59, 60, 61, 5000, 70_059, nc + leaves, nc + leaves + 7, g["m"] - 1])
+    rows_o, _ = oracle.paper_edges(g, ids)
+    np.testing.assert_array_equal(pe[ids], rows_o)
