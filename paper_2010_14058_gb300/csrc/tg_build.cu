@@ -342,6 +342,12 @@ __global__ void k_widen(int64_t n, const int32_t *__restrict__ in, int64_t *out)
     if (i < n) out[i] = in[i];
 }
 
+__global__ void k_count_above(int64_t c, const int32_t *__restrict__ ids, const unsigned long long *__restrict__ key,
+                              unsigned long long limit, unsigned long long *count) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < c && key[ids[i]] > limit) atomicAdd(count, 1ull);
+}
+
 // Sorts `ids` (count c) by descending key (keys indexed by id).
 __global__ void k_gather_keys(int64_t c, const int32_t *__restrict__ ids, const unsigned long long *__restrict__ key,
                               unsigned long long *out) {
@@ -597,6 +603,21 @@ void build_graph(Graph &G, int32_t ngraphs, const int64_t *node_off_host, int64_
         G.n_anchors_light = select_flagged(ids.as<int32_t>(), fl.as<uint8_t>(), n, G.anchors_light, s);
         G.n_anchors_heavy = select_flagged(ids.as<int32_t>(), fh.as<uint8_t>(), n, G.anchors_heavy, s);
         sort_desc_by_key(G.anchors_heavy, G.n_anchors_heavy, key.as<unsigned long long>(), s, G.last_launches);
+        {   // heavy anchors above the shared-memory hash's limit (they lead the sorted list)
+            TBuf cnt(sizeof(unsigned long long), s);
+            TG_CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+            if (G.n_anchors_heavy > 0) {
+                ++G.last_launches;
+                k_count_above<<<blocks_for(G.n_anchors_heavy, kThreads), kThreads, 0, s>>>(
+                    G.n_anchors_heavy, G.anchors_heavy.as<int32_t>(), key.as<unsigned long long>(), kHeavyFit,
+                    cnt.as<unsigned long long>());
+                TG_CK(cudaGetLastError());
+            }
+            unsigned long long c = 0;
+            TG_CK(cudaMemcpyAsync(&c, cnt.p, sizeof(c), cudaMemcpyDeviceToHost, s));
+            TG_CK(cudaStreamSynchronize(s));
+            G.n_heavy_dense = (int64_t)c;
+        }
         G.n_hubs = select_flagged(ids.as<int32_t>(), fhub.as<uint8_t>(), n, G.hubs, s);
         G.h_hub_id.assign((size_t)G.n_hubs, 0);
         G.h_hub_wedges.assign((size_t)G.n_hubs, 0);

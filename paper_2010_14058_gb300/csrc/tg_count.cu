@@ -113,6 +113,10 @@ __global__ void __launch_bounds__(256) k_tri(GraphView g, CountView cv) {
         for (int t = 0; t < g.L; ++t) {
             int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
             int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
+            if (ei == bi || ej == bj) {                     // an empty typed segment (warp-uniform)
+                if (lane == 0) cv.C[e * g.L + t] = 0;
+                continue;
+            }
             if (ei - bi > ej - bj) {
                 int64_t x = bi; bi = bj; bj = x;
                 x = ei; ei = ej; ej = x;
@@ -388,7 +392,8 @@ __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphVie
 // neighbours v.  The rows h[w][.] live in a shared-memory hash of kHeavyCap
 // entries; an anchor whose distinct w exceed 3/4 of it is redone against
 // the CTA's dense node table in global memory (cleared again by phase 2).
-constexpr int kHeavyCap = 4096;
+// Anchors with more wedges than that limit go to the dense table directly:
+// on power-law graphs their wedge ends are almost all distinct.
 
 __device__ int hash_insert_bounded(int32_t *keys, int cap, int32_t w, int *fill, int limit) {
     int h = hash_slot(w, cap);
@@ -407,9 +412,10 @@ __device__ int hash_insert_bounded(int32_t *keys, int cap, int32_t w, int *fill,
     return -1;
 }
 
-__global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, CountView cv,
+__global__ void __launch_bounds__(kAnchorThreads, 2) k_wedge_heavy(GraphView g, CountView cv,
                                                                const int32_t *__restrict__ anchors,
-                                                               int64_t n_anchors, int64_t n0, int64_t n1) {
+                                                               int64_t n_anchors, int64_t n_dense, int64_t n0,
+                                                               int64_t n1) {
     extern __shared__ int32_t hsm[];
     __shared__ int s_fill, s_over;
     const int L = g.L;
@@ -424,9 +430,14 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
         if (u < n0 || u >= n1) continue;                    // anchor outside this chunk (uniform per CTA)
         const int tu = g.ty[u];
         const int64_t base = g.node_off[graph_of_node(g, u)];
-        for (int k = threadIdx.x; k < kHeavyCap; k += blockDim.x) keys[k] = -1;
-        for (int k = threadIdx.x; k < kHeavyCap * L; k += blockDim.x) cnt[k] = 0;
-        if (threadIdx.x == 0) { s_fill = 0; s_over = 0; }
+        // the first n_dense anchors (wedges above the hash's load limit, sorted
+        // first) would overflow the hash: they go to the dense table at once
+        const bool pre_dense = a < n_dense;
+        if (!pre_dense) {
+            for (int k = threadIdx.x; k < kHeavyCap; k += blockDim.x) keys[k] = -1;
+            for (int k = threadIdx.x; k < kHeavyCap * L; k += blockDim.x) cnt[k] = 0;
+        }
+        if (threadIdx.x == 0) { s_fill = 0; s_over = pre_dense ? 1 : 0; }
         __syncthreads();
         int64_t ub;
         int32_t uoff;
@@ -443,12 +454,14 @@ __global__ void __launch_bounds__(kAnchorThreads) k_wedge_heavy(GraphView g, Cou
             return cnt + h * L;
         };
         auto dense_rows = [&](int32_t w, bool) -> uint32_t * { return tbl + (int64_t)(w - base) * L; };
-        for (int32_t kv = wid; kv < nV; kv += nwarp) {
-            int tv;
-            const int64_t sv = u_slot(ub, uoff, kv, tv);
-            wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, hash_rows);
+        if (!pre_dense) {
+            for (int32_t kv = wid; kv < nV; kv += nwarp) {
+                int tv;
+                const int64_t sv = u_slot(ub, uoff, kv, tv);
+                wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, hash_rows);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         const bool dense = s_over != 0;                     // uniform after the barrier
         if (dense)
             for (int32_t kv = wid; kv < nV; kv += nwarp) {
@@ -1679,7 +1692,7 @@ static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
     if (G.n_anchors_heavy > 0) {
         KernelTimer kt(G, s, "k_wedge_heavy");
         k_wedge_heavy<<<G.n_tables, kAnchorThreads, (size_t)kHeavyCap * (1 + L) * sizeof(int32_t), s>>>(
-            gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy,
+            gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy, G.n_heavy_dense,
                                                              c.n0, c.n1);
         ++launches;
     }

@@ -122,6 +122,7 @@ struct Graph {
     // work lists
     DBuf anchors_light, anchors_heavy, edges_light, edges_heavy;
     int64_t n_anchors_light = 0, n_anchors_heavy = 0, n_edges_light = 0, n_edges_heavy = 0;
+    int64_t n_heavy_dense = 0;          // leading heavy anchors with more than kHeavyFit wedges
     // hub anchors (ascending id) and their wedge items: one item per
     // (hub, lower-priority neighbour v, type of w) with at least one wedge
     DBuf hubs, hub_base, item_woff, item_vb, item_sv, item_hub, item_tt;

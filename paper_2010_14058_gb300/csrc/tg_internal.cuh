@@ -30,6 +30,8 @@ constexpr int kMaxL = TG_MAX_TYPES;
 constexpr int kWarp = 32;
 constexpr int kTypeShift = 29;                     // packed (type << 29 | id) sort keys
 constexpr int32_t kIdMask = (1 << kTypeShift) - 1;
+constexpr int kHeavyCap = 4096;                    // shared-memory hash rows of a heavy anchor
+constexpr int kHeavyFit = kHeavyCap / 4 * 3;       // its load limit (distinct wedge ends)
 
 // Read-only view of a built graph, passed to kernels by value.
 struct GraphView {
