@@ -124,7 +124,8 @@ typedef struct {
                                          array would exceed it is counted in chunks of whole graphs */
     int32_t hub_min_wedges;           /* anchors with more wedges than this are hubs: each is counted
                                          by the whole GPU against one node table shared by all CTAs */
-    int32_t hub_l2_mb;                /* bytes of hub node tables in use at once (kept within L2) */
+    int32_t hub_l2_mb;                /* MB of hub node tables in use at once (about the L2 size:
+                                         more hubs per launch, fewer launches) */
     int32_t reserved;
 } tg_options;
 

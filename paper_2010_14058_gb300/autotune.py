@@ -13,6 +13,8 @@ them"); they pick which kernel variant takes which part of the work:
                            by one CTA each with a shared-memory hash) -- the
                            table-versus-hash choice per degree bucket
   ctas_per_sm              resident CTAs per SM of the orbit epilogue
+  hub_l2_mb                hub node tables counted together (more hubs per
+                           launch against L2 pressure)
 
 tune() measures tg_count (CUDA events on the given stream) for one graph or
 batch handle per candidate, by coordinate descent from the defaults, and
@@ -37,8 +39,10 @@ SPACE = {
     "light_anchor_max_wedges": [64, 256, 1024, 2048],
     "hub_min_wedges": [1 << 14, 1 << 16, 1 << 18, 1 << 20],
     "ctas_per_sm": [2, 3, 4],
+    "hub_l2_mb": [64, 128, 256],
 }
-DEFAULTS = {"light_edge_max_degree": 256, "light_anchor_max_wedges": 64, "hub_min_wedges": 1 << 16, "ctas_per_sm": 3}
+DEFAULTS = {"light_edge_max_degree": 256, "light_anchor_max_wedges": 64, "hub_min_wedges": 1 << 16, "ctas_per_sm": 3,
+            "hub_l2_mb": 128}
 
 CACHE_PATH = os.environ.get("TG_AUTOTUNE_CACHE", os.path.join(os.path.dirname(__file__), ".autotune.json"))
 _lock = threading.Lock()

@@ -258,7 +258,7 @@ inline void fill_defaults(tg_options *o) {
     o->ctas_per_sm = 3;
     o->cycle_budget_mb = 16384;
     o->hub_min_wedges = 1 << 16;
-    o->hub_l2_mb = 64;
+    o->hub_l2_mb = 128;
 }
 
 // number of SMs of the current device
