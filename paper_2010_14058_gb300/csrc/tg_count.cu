@@ -949,8 +949,7 @@ __device__ __forceinline__ void scan_long(const GraphView &g, int32_t w, int tw,
     const int64_t pb = g.plus_off[w], pe = g.plus_off[w + 1];
     unsigned c = 0;
     uint32_t cur = 0;
-    for (int64_t sx = pb + lane; sx < pe; sx += 32) {
-        const uint32_t ent = (uint32_t)g.plus_adj[sx];
+    auto take = [&](uint32_t ent) {
         const uint32_t q = ent >> kTypeShift;
         if (q != cur) {
             if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
@@ -958,6 +957,16 @@ __device__ __forceinline__ void scan_long(const GraphView &g, int32_t w, int tw,
             cur = q;
         }
         c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
+    };
+    // four strided entries per lane per round, loads issued first (a lane's
+    // entries stay in list order, so its type runs stay in order)
+    for (int64_t sx = pb + lane; sx < pe; sx += 128) {
+        uint32_t ent[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ent[u] = sx + 32 * u < pe ? (uint32_t)g.plus_adj[sx + 32 * u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (sx + 32 * u < pe) take(ent[u]);
     }
     if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
 }
