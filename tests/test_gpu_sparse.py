@@ -70,3 +70,43 @@ def test_sparse_many_windows_equals_dense():
     np.testing.assert_array_equal(va, va_e)
     np.testing.assert_array_equal(gl, gd.cpu().numpy())
     assert 0 < ro[-1] <= g["m"] * S, (ro[-1], g["m"] * S)
+
+
+def test_sparse_empty_and_errors():
+    from oracle_pins import graph_from_edges
+    g = graph_from_edges(5, [], [0, 1, 2, 0, 1], 3)                  # nodes, no edges
+    h = tg.tg_build(*tg.to_device(g), 3)
+    row_off = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    assert tg.tg_count_sparse(h, 4, row_off) == 0 and int(row_off[0]) == 0
+    with pytest.raises(tg.TGError) as e:                             # host arrays are refused
+        tg.tg_count_sparse(h, 4, np.zeros(1, np.int64))
+    assert e.value.name == "TG_ERR_INVALID_ARG"
+    h.free()
+
+
+def test_sparse_on_a_chunked_batch():
+    graphs = [graphgen.erdos_renyi(60 + 20 * x, 300 + 90 * x, 3, 50 + x) for x in range(9)]
+    graphs.append(graphgen.chung_lu(1500, 7000, 2.1, 400.0, 3, 77))
+    u = graphgen.concat(graphs)
+    rp, col, ty = (torch.as_tensor(u[k], device="cuda") for k in ("row_ptr", "col", "types"))
+    h = tg.tg_build_batch(u["node_off"], rp, col, ty, 3, options={"cycle_budget_mb": 1})
+    ro, sl, va, _ = sparse_batch(h, 4)
+    dense = torch.zeros((h.m, tg.tg_layout(3, 4)["per_edge_slots"]), dtype=torch.int32, device="cuda")
+    tg.tg_count(h, 4, dense, None)
+    ro_e, sl_e, va_e = expected(dense.cpu().numpy().view(np.uint32).astype(np.int64))
+    np.testing.assert_array_equal(ro, ro_e)
+    np.testing.assert_array_equal(sl, sl_e)
+    np.testing.assert_array_equal(va, va_e)
+    h.free()
+
+
+def sparse_batch(h, k):
+    row_off = torch.zeros(h.m + 1, dtype=torch.int64, device="cuda")
+    nnz = tg.tg_count_sparse(h, k, row_off)
+    slot = torch.zeros(max(nnz, 1), dtype=torch.int16, device="cuda")
+    value = torch.zeros(max(nnz, 1), dtype=torch.int32, device="cuda")
+    gl = torch.zeros((h.ngraphs, tg.tg_layout(h.L, k)["global_slots"]), dtype=torch.int64, device="cuda")
+    assert tg.tg_count_sparse(h, k, row_off, slot, value, gl) == nnz
+    assert tg.tg_query_status(h) == 0
+    return (row_off.cpu().numpy(), slot[:nnz].cpu().numpy().view(np.uint16).astype(np.int64),
+            value[:nnz].cpu().numpy().view(np.uint32).astype(np.int64), gl.cpu().numpy())

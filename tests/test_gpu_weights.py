@@ -89,3 +89,28 @@ def test_weights_equal_brute_force(seed):
     with pytest.raises(tg.TGError):
         tg.tg_graphlet_weights(h, 4, rows, 3, lay["global_block_size"][3], w)
     h.free()
+
+
+def test_weights_k3_one_type_and_empty():
+    from oracle_pins import graph_from_edges
+    # L = 1: the triangle weight of every edge of K4 is 2, the 3-path weight 0
+    g = graph_from_edges(4, [(a, b) for a in range(4) for b in range(a + 1, 4)], [0, 0, 0, 0], 1)
+    h = tg.tg_build(*tg.to_device(g), 1)
+    rows = torch.zeros((h.m, tg.tg_layout(1, 3)["per_edge_slots"]), dtype=torch.int32, device="cuda")
+    tg.tg_count(h, 3, rows, None)
+    w = torch.zeros(h.m, dtype=torch.int64, device="cuda")
+    d = torch.zeros(4, dtype=torch.int64, device="cuda")
+    tg.tg_graphlet_weights(h, 3, rows, 2, 0, w, d)
+    assert w.tolist() == [2] * 6 and d.tolist() == [6] * 4
+    tg.tg_graphlet_weights(h, 3, rows, 1, 0, w)
+    assert w.tolist() == [0] * 6
+    with pytest.raises(tg.TGError):
+        tg.tg_graphlet_weights(h, 3, rows, 3, 0, w)                  # 4-node block with k = 3 rows
+    h.free()
+    e = graph_from_edges(3, [], [0, 0, 0], 1)
+    h = tg.tg_build(*tg.to_device(e), 1)
+    d3 = torch.full((3,), 7, dtype=torch.int64, device="cuda")
+    tg.tg_graphlet_weights(h, 3, torch.zeros(1, dtype=torch.int32, device="cuda"), 0, 0,
+                           torch.zeros(1, dtype=torch.int64, device="cuda"), d3)
+    assert d3.tolist() == [0, 0, 0]
+    h.free()
