@@ -228,6 +228,7 @@ tg_status tg_count_range(tg_graph *gh, int32_t k, int64_t e_begin, int64_t e_end
         if (gl_staged) TG_CK(cudaMemcpyAsync(gl, global_accum, gl_bytes, cudaMemcpyHostToDevice, s));
         unsigned long long *acc = gl ? reinterpret_cast<unsigned long long *>(gl) : nullptr;
         tg::DBuf scratch;
+        scratch.owner = &G.stream;
         if (!acc) {
             scratch.alloc(gl_bytes);
             TG_CK(cudaMemsetAsync(scratch.p, 0, gl_bytes, s));

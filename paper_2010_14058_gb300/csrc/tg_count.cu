@@ -1496,6 +1496,7 @@ void prepare_edges(Graph &G, int k, cudaStream_t s) {
         G.set_scratch.alloc(sizeof(int32_t) * (size_t)(G.set_stride * G.big_blocks));
     }
     DBuf unused;
+    unused.owner = &G.stream;
     int64_t nt = 0;
     tiles_for(G, 0, G.m, nt, unused, s);
     if (k == 4 && G.n_anchors_light > 0) {
@@ -1817,7 +1818,8 @@ int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per
         launches += launch_triangles(G, s);
         G.prepared_k = std::max(G.prepared_k, 3);
     }
-    DBuf tmp;
+    DBuf tmp;                                                // tiles of a range, stream-ordered
+    tmp.owner = &G.stream;
     int64_t n_tiles = 0;
     const Tile *tiles = tiles_for(G, e_begin, e_end, n_tiles, tmp, s);
     if (k == 3) {
