@@ -8,8 +8,8 @@ At 20-30 M edges the oracle cannot count every edge, so:
   (Sigma C(d,2) = 3-paths + 3 triangles; Sigma C(d,3) = stars + paws +
   2 diamonds + 4 cliques; Sigma_E (d_u-1)(d_v-1) - 3 triangles = 4-paths +
   4 C4 + 2 paws + 6 diamonds + 12 cliques), every per-edge orbit sum must be
-  |E(H)| times the matching global total (Sec. 6), and Property 1 with S_i
-  excluding j must hold on every edge.
+  |E(H)| times the matching global total (Sec. 6), and the degree identity of
+  Sec. 7.1 with S_i excluding j must hold on every edge.
 The run is the same launch configuration bench.py times (tg_build +
 tg_count, k = 4, device buffers).
 """

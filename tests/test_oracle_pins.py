@@ -2,7 +2,7 @@
 
 Each test checks the oracle against something other than itself: values the
 paper prints (tests/golden), closed forms of graph families, invariants the
-paper states (Prop. 2, Sec. 4.4, Sec. 6), standard untyped identities,
+paper states (Prop. 1, Sec. 4.4, Sec. 6), standard untyped identities,
 subgraph isomorphism by networkx, and library enumeration order for the
 layout.  The three oracle routes (Alg. 1-3 + Lemmas, Table 3 definitions,
 brute force) must also agree with each other.
@@ -240,7 +240,7 @@ def test_networkx_isomorphism_classification():
 
 @pytest.mark.parametrize("seed", range(6))
 def test_sum_over_types_is_untyped(seed):
-    """Prop. 2: summing typed counts over all type combinations gives the
+    """Prop. 1: summing typed counts over all type combinations gives the
     untyped counts (per edge and global)."""
     g = random_graph(14, 0.35, 4, 2000 + seed)
     L = g["L"]
@@ -286,7 +286,7 @@ def test_untyped_identities_and_property1(seed):
     pe1, gl1 = oracle.paper(g1)
     for lhs, rhs in untyped_identities(g, gl1):
         assert lhs == rhs
-    # Property 1 with S_i excluding j (and S_j excluding i):
+    # the degree identity of Sec. 7.1 with S_i excluding j (and S_j excluding i):
     # d_i + d_j = 2|T_ij| + |S_i| + |S_j| + 2
     deg = np.diff(g["row_ptr"])
     for e, (a, b) in enumerate(edge_list(g)):
