@@ -8,10 +8,12 @@
 // (t = type of the first node, t' = type of the second):
 //
 //   c[t]        |T_ij^t| (Cor. 1), by typed set intersection       (k_tri)
-//   TCi[t][t']  sum_{w in T^t} c_{iw}^{t'}                         (k_edge4)
-//   TCj[t][t']  sum_{w in T^t} c_{jw}^{t'}                         (k_edge4)
-//   DT[t][t']   sum_{w in T^t} d_w^{t'}                            (k_edge4)
-//   K[t][t']    ordered adjacent pairs (w,x) in T^t x T^t'         (k_edge4)
+//   TCi[t][t']  sum_{w in T^t} c_{iw}^{t'}                         (k_tsum)
+//   TCj[t][t']  sum_{w in T^t} c_{jw}^{t'}                         (k_tsum)
+//   DT[t][t']   sum_{w in T^t} d_w^{t'}                            (k_tsum)
+//   K[t][t']    ordered adjacent pairs (w,x) in T^t x T^t' (each pair is found
+//               once, from its smaller id, by k_clique / k_clique_big; the
+//               epilogue adds the transpose)
 //   P[t][t']    3-paths j - w - r - i, w of type t, r of type t'   (k_wedge*)
 //   tau_x[t][t'] ordered adjacent pairs inside Gamma_x              (k_tau)
 //   delta_x[t][t'] sum_{w in Gamma_x^t} d_w^{t'}                    (build)
