@@ -36,6 +36,9 @@ def _rank_main(rank, world, port, out_dir, weighted):
 @pytest.mark.parametrize("weighted", [False, True])
 def test_two_gloo_ranks_match_whole_graph(tmp_path, weighted):
     import torch.multiprocessing as mp
+
+    from paper_2010_14058_gb300 import build
+    build.build()                                   # the ranks call tg_finalize_global
     port = _free_port()
     mp.start_processes(_rank_main, args=(2, port, str(tmp_path), weighted), nprocs=2, join=True,
                        start_method="spawn")
