@@ -98,3 +98,32 @@ def test_ego_batch_and_request_pool_shapes():
     assert all(100 <= g["m"] <= 5000 and 3 <= g["L"] <= 8 for g in pool)
     tr = serve.poisson_trace(pool, 500.0, 0.2, seed=1)
     assert all(a.arrival < b.arrival for a, b in zip(tr[:-1], tr[1:])) and all(r.key is not None for r in tr)
+
+
+def test_autotune_descent_with_fake_timings(monkeypatch, tmp_path):
+    # a fake measurement: time = sum of per-knob costs; totals fixed
+    cost = {"light_edge_max_degree": {32: 3.0, 64: 1.0, 128: 2.0, 256: 2.5},
+            "ctas_per_sm": {2: 0.5, 3: 1.0, 4: 2.0}}
+    seen = []
+
+    def fake(build, options, L, G, ngraphs, stream, reps):
+        seen.append(dict(options))
+        return sum(cost[k][v] for k, v in options.items()), np.ones((ngraphs, G), np.int64)
+
+    monkeypatch.setattr(autotune, "_time_count", fake)
+    rp = torch.tensor([0, 1, 2], dtype=torch.int64)
+    col = torch.tensor([1, 0], dtype=torch.int32)
+    ty = torch.zeros(2, dtype=torch.uint8)
+    space = {k: sorted(v) for k, v in cost.items()}
+    e = autotune.tune(rp, col, ty, 2, space=space, reps=1, path=str(tmp_path / "t.json"), stream=object())
+    assert e["options"] == {"light_edge_max_degree": 64, "ctas_per_sm": 2}
+    assert e["ms"] == 1.5 and e["default_ms"] == 2.5 + 1.0
+    assert len(seen) == 1 + 3 + 2 and len({tuple(sorted(o.items())) for o in seen}) == len(seen)   # no repeats
+    assert autotune.cached(e["signature"], str(tmp_path / "t.json")) == e["options"]
+
+    def changing(build, options, L, G, ngraphs, stream, reps):   # a candidate that alters the counts
+        return 1.0, np.full((ngraphs, G), options["ctas_per_sm"], np.int64)
+
+    monkeypatch.setattr(autotune, "_time_count", changing)
+    with pytest.raises(RuntimeError):
+        autotune.tune(rp, col, ty, 2, space={"ctas_per_sm": [2, 3]}, reps=1, store=False, stream=object())
