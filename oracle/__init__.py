@@ -10,6 +10,9 @@ Three independent routes over the same output layout (see oracle.c):
 * :func:`table3` -- each orbit from its Table 3 set-builder definition.
 * :func:`brute`  -- all 3- and 4-node subsets, classified by induced degrees.
 
+:func:`weights` gives the typed-graphlet weighted graph W and degree D of
+Alg. 5 by direct enumeration.
+
 All counts are exact int64.  Parity with these is the acceptance bar for
 the GPU path (bit-exact).
 """
@@ -60,6 +63,7 @@ _SIGS = {
     "oracle_brute": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_edges": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_validate": ("i64 vp vp vp i32", "i32"),
+    "oracle_weights": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_max_threads": ("", "i32"),
 }
 _CT = {"i64": ctypes.c_int64, "i32": ctypes.c_int32, "vp": ctypes.c_void_p}
@@ -190,3 +194,17 @@ def brute(g, lib=None):
     gl = np.zeros(global_slots(L, 4, lib), dtype=np.int64)
     _check(lib.oracle_brute(g["n"], _p(rp), _p(col), _p(ty), L, _p(pe), _p(gl)))
     return pe, gl
+
+
+def weights(g, lib=None):
+    """Alg. 5's W and D for every typed graphlet -> (W int64 [m,G], D int64 [n,G]).
+
+    Column s is global slot s (block offset + type-multiset rank).  Small n only."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    L = g["L"]
+    m = int(rp[-1]) // 2
+    w = np.zeros((m, global_slots(L, 4, lib)), dtype=np.int64)
+    d = np.zeros((g["n"], global_slots(L, 4, lib)), dtype=np.int64)
+    _check(lib.oracle_weights(g["n"], _p(rp), _p(col), _p(ty), L, _p(w), _p(d)))
+    return w, d

@@ -24,6 +24,11 @@
  *                     classified by edge count and induced degrees; no typed
  *                     set is used.  Small graphs only.
  *
+ * Alg. 5 (first two steps): oracle_weights gives the typed-graphlet weighted
+ * graph W (instances of each typed graphlet containing an edge's endpoints)
+ * and its degree D, by direct enumeration of the node sets that contain the
+ * edge.  Small graphs only.
+ *
  * Output layout (shared by specification with the GPU library, written
  * independently on each side):
  *   per edge (row stride S(L) = 2L + 10P, P = L(L+1)/2, int64 here):
@@ -66,7 +71,7 @@
 #define OR_MAX_L 16
 
 /* Planted mistakes for the pin tests: a test compiles a separate copy of
- * this file with -DORACLE_MUTANT=k (k = 1..8) and checks that the pins fail.
+ * this file with -DORACLE_MUTANT=k (k = 1..10) and checks that the pins fail.
  * The default build (ORACLE_MUTANT undefined) contains none of them. */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
@@ -679,4 +684,71 @@ int oracle_brute(int64_t n, const int64_t *row_ptr, const int32_t *col, const ui
                 }
     graph_close(&G);
     return rc;
+}
+
+/* ------------------------------------ typed-graphlet weighted graph */
+
+/* Alg. 5, first two steps, for every typed {2,3,4}-node graphlet H at once:
+ * W[e][s] = the number of instances of H (global slot s) that contain both
+ * endpoints of edge e, D[v][s] = sum over the edges e at v of W[e][s].  An
+ * instance is a connected induced subgraph; since {i,j} is an edge it is an
+ * edge of every instance counted.  Direct enumeration: the edge itself, every
+ * third node x, every pair of other nodes x < y, each set classified by its
+ * induced edge count and degrees.  Small graphs only (m n^2 / 2 sets).
+ * w_out: int64 [m][G(L)]; d_out: int64 [n][G(L)] or NULL. */
+int oracle_weights(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *types, int L,
+                   int64_t *w_out, int64_t *d_out) {
+    graph_t G;
+    int rc = graph_open(&G, n, row_ptr, col, types, L);
+    if (rc != OK) { graph_close(&G); return rc; }
+    const int64_t Gs = oracle_global_slots(L, 4);
+    memset(w_out, 0, (size_t)(G.m * Gs) * sizeof(int64_t));
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(|:bad)
+    for (int64_t e = 0; e < G.m; ++e) {
+        const int64_t i = G.eu[e], j = G.ev[e];
+        int64_t *w = w_out + e * Gs;
+        int t2[2] = {types[i], types[j]};
+        bad |= global_add(w, L, 0, multiset_rank(L, 2, t2), 1);
+        for (int64_t x = 0; x < n; ++x) {
+            if (x == i || x == j) continue;
+            const int ne = 1 + is_adjacent(&G, x, i) + is_adjacent(&G, x, j);
+            if (ne < 2) continue;                                 /* x isolated from the edge */
+            int t3[3] = {types[i], types[j], types[x]};
+            bad |= global_add(w, L, ne == 2 ? 1 : 2, multiset_rank(L, 3, t3), 1);
+        }
+        for (int64_t x = 0; x < n; ++x) {
+            if (x == i || x == j) continue;
+            for (int64_t y = x + 1; y < n; ++y) {
+                if (y == i || y == j) continue;
+                const int64_t v[4] = {i, j, x, y};
+                int ne = 0, deg[4] = {0, 0, 0, 0};
+                for (int a = 0; a < 4; ++a)
+                    for (int b = a + 1; b < 4; ++b)
+                        if (is_adjacent(&G, v[a], v[b])) { ++ne; deg[a]++; deg[b]++; }
+                int mind = 4, maxd = 0;
+                for (int a = 0; a < 4; ++a) {
+                    if (deg[a] < mind) mind = deg[a];
+                    if (deg[a] > maxd) maxd = deg[a];
+                }
+                if (ne < 3 || mind == 0) continue;                /* not connected */
+                int h;
+                if (ne == 3) h = maxd == 3 ? 4 : 3;               /* 4-star : 4-path */
+                else if (ne == 4) h = (maxd == 3 && !MUTANT(9)) ? 6 : 5;   /* tailed-triangle : 4-cycle */
+                else h = ne == 5 ? 7 : 8;                         /* chordal-cycle : 4-clique */
+                int t4[4] = {types[i], types[j], types[x], types[y]};
+                bad |= global_add(w, L, h, multiset_rank(L, 4, t4), 1);
+            }
+        }
+    }
+    if (d_out) {
+        memset(d_out, 0, (size_t)(n * Gs) * sizeof(int64_t));
+        for (int64_t e = 0; e < G.m; ++e)
+            for (int64_t s = 0; s < Gs; ++s) {
+                d_out[G.eu[e] * Gs + s] += w_out[e * Gs + s];
+                if (!MUTANT(10)) d_out[G.ev[e] * Gs + s] += w_out[e * Gs + s];
+            }
+    }
+    graph_close(&G);
+    return bad ? ERR_REMAINDER : OK;
 }

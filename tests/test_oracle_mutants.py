@@ -4,7 +4,8 @@ Each mutant is a copy of oracle.c compiled with -DORACLE_MUTANT=k, which
 plants one plausible mistake: a dropped term in Lemma 1, a lost tie-break
 in Alg. 2, j left inside S_i, transposed operands in Lemma 3, a wrong branch
 in Alg. 3, an unsorted type multiset, a missing 1/2 in Lemma 2, a lost
-exclusion of i and j in Alg. 2.  The pin battery here (closed forms,
+exclusion of i and j in Alg. 2; in the weighted graph of Alg. 5, tailed
+triangles booked as 4-cycles and D missing one endpoint of each edge.  The pin battery here (closed forms,
 layout enumeration, the brute-force and networkx-free subset count) must
 reject every one of them, on the CPU.
 """
@@ -27,6 +28,8 @@ MUTANTS = {
     6: "type multiset not sorted before ranking",
     7: "Lemma 2 without the 1/2",
     8: "Alg. 2 scans i and j as neighbours of w_k",
+    9: "Alg. 5 weights book a tailed triangle as a 4-cycle",
+    10: "Alg. 5 degree adds each edge's weight to one endpoint only",
 }
 
 
@@ -72,6 +75,22 @@ def _battery(lib) -> list:
             c, d = oracle.brute(g, lib=lib)
             return np.array_equal(a, c) and np.array_equal(b, d)
         check(f"brute seed={seed}", vs_brute)
+
+    # weighted graph of Alg. 5: column sums are |E(H)| x global counts, D
+    # sums W over each node's edges
+    edges_of = np.repeat([1, 2, 3, 3, 3, 4, 4, 5, 6], [6, 10, 10, 15, 15, 15, 15, 15, 15])
+    for seed in range(3):
+        g = random_graph(10 + seed, 0.5, 3, 90 + seed)
+
+        def w_sums(g=g):
+            w, d = oracle.weights(g, lib=lib)
+            _, gl = oracle.paper(g, lib=lib)
+            want_d = np.zeros_like(d)
+            src, dst = oracle.edges(g, lib=lib)
+            np.add.at(want_d, src, w)
+            np.add.at(want_d, dst, w)
+            return np.array_equal(w.sum(0), edges_of * gl) and np.array_equal(d, want_d)
+        check(f"weights seed={seed}", w_sums)
     return failed
 
 
