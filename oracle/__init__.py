@@ -11,7 +11,8 @@ Three independent routes over the same output layout (see oracle.c):
 * :func:`brute`  -- all 3- and 4-node subsets, classified by induced degrees.
 
 :func:`weights` gives the typed-graphlet weighted graph W and degree D of
-Alg. 5 by direct enumeration.
+Alg. 5 by direct enumeration; :func:`position_aware` the position-aware
+typed counts of Sec. 5 (Def. 8), per edge and global.
 
 All counts are exact int64.  Parity with these is the acceptance bar for
 the GPU path (bit-exact).
@@ -64,6 +65,12 @@ _SIGS = {
     "oracle_edges": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_validate": ("i64 vp vp vp i32", "i32"),
     "oracle_weights": ("i64 vp vp vp i32 vp vp", "i32"),
+    "oracle_pa_per_edge_slots": ("i32", "i64"),
+    "oracle_pa_block_size": ("i32 i32", "i64"),
+    "oracle_pa_global_slots": ("i32", "i64"),
+    "oracle_pa_class": ("i32 i32 vp", "i64"),
+    "oracle_position_aware": ("i64 vp vp vp i32 vp vp", "i32"),
+    "oracle_position_aware_brute": ("i64 vp vp vp i32 vp", "i32"),
     "oracle_max_threads": ("", "i32"),
 }
 _CT = {"i64": ctypes.c_int64, "i32": ctypes.c_int32, "vp": ctypes.c_void_p}
@@ -208,3 +215,46 @@ def weights(g, lib=None):
     d = np.zeros((g["n"], global_slots(L, 4, lib)), dtype=np.int64)
     _check(lib.oracle_weights(g["n"], _p(rp), _p(col), _p(ty), L, _p(w), _p(d)))
     return w, d
+
+
+def pa_per_edge_slots(L: int, lib=None) -> int:
+    lib = lib or _load()
+    return int(lib.oracle_pa_per_edge_slots(L))
+
+
+def pa_block_sizes(L: int, lib=None) -> list:
+    """Number of position-aware typed graphlets of each global block (Def. 8)."""
+    lib = lib or _load()
+    return [int(lib.oracle_pa_block_size(L, b)) for b in range(9)]
+
+
+def pa_class(L: int, block: int, labelling, lib=None) -> int:
+    """Rank, within its block, of the class of a labelling of the numbered shape."""
+    lib = lib or _load()
+    a = np.ascontiguousarray(labelling, dtype=np.int32)
+    return int(lib.oracle_pa_class(L, block, _p(a)))
+
+
+def position_aware(g, per_edge: bool = True, lib=None):
+    """Sec. 5 per edge and global -> (per_edge int64 [m,S_pa] or None, global int64 [G_pa])."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    L = g["L"]
+    m = int(rp[-1]) // 2
+    if not 1 <= L <= 8:
+        raise OracleError(ERRORS[1])
+    pe = np.zeros((m, pa_per_edge_slots(L, lib)), dtype=np.int64) if per_edge else None
+    gl = np.zeros(int(lib.oracle_pa_global_slots(L)), dtype=np.int64)
+    _check(lib.oracle_position_aware(g["n"], _p(rp), _p(col), _p(ty), L, _p(pe), _p(gl)))
+    return pe, gl
+
+
+def position_aware_brute(g, lib=None):
+    """Position-aware global counts from every node set of the graph.  Small n only."""
+    lib = lib or _load()
+    rp, col, ty = _args(g)
+    if not 1 <= g["L"] <= 8:
+        raise OracleError(ERRORS[1])
+    gl = np.zeros(int(lib.oracle_pa_global_slots(g["L"])), dtype=np.int64)
+    _check(lib.oracle_position_aware_brute(g["n"], _p(rp), _p(col), _p(ty), g["L"], _p(gl)))
+    return gl

@@ -24,6 +24,11 @@
  *                     classified by edge count and induced degrees; no typed
  *                     set is used.  Small graphs only.
  *
+ * Sec. 5 (Def. 8): oracle_position_aware gives position-aware typed
+ * counts per edge and globally, by visiting every connected node set that
+ * contains an edge; oracle_position_aware_brute gives the global counts from
+ * all node sets of the graph.
+ *
  * Alg. 5 (first two steps): oracle_weights gives the typed-graphlet weighted
  * graph W (instances of each typed graphlet containing an edge's endpoints)
  * and its degree D, by direct enumeration of the node sets that contain the
@@ -71,7 +76,7 @@
 #define OR_MAX_L 16
 
 /* Planted mistakes for the pin tests: a test compiles a separate copy of
- * this file with -DORACLE_MUTANT=k (k = 1..10) and checks that the pins fail.
+ * this file with -DORACLE_MUTANT=k (k = 1..12) and checks that the pins fail.
  * The default build (ORACLE_MUTANT undefined) contains none of them. */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
@@ -751,4 +756,432 @@ int oracle_weights(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
     }
     graph_close(&G);
     return bad ? ERR_REMAINDER : OK;
+}
+
+/* ------------------------------- position-aware typed graphlets (Sec. 5) */
+
+/* Def. 8: two typed instances of one shape are the same position-aware
+ * typed graphlet when an isomorphism between them maps every node onto a
+ * node of the same type.  For a shape with its nodes numbered, a
+ * position-aware typed graphlet is therefore a labelling (types of nodes
+ * 0..k-1) up to the shape's automorphisms; its class is represented by the
+ * lexicographically smallest labelling in it, and the classes of a shape
+ * are numbered in the lexicographic order of those representatives.
+ *
+ * Numbered shapes (global blocks as for typed graphlets):
+ *   0 edge 0-1; 1 3-path, 0 the centre; 2 triangle; 3 4-path 0-1-2-3;
+ *   4 4-star, 0 the centre; 5 4-cycle 0-1-2-3-0; 6 tailed triangle, 0 the
+ *   degree-3 node, 1 the tail, 2-3 the rest of the triangle; 7 chordal cycle,
+ *   0-1 the chord; 8 4-clique.
+ *
+ * Per-edge rows, edge e = {lo, hi} (lo < hi, caller ids); "side" 0 = lo,
+ * 1 = hi; ordered type pairs (x, y) at x*L + y; unordered pairs as
+ * pair_index; blocks in this order:
+ *   O1  3-path      [side of the centre][type of the third node]     2L
+ *   O2  triangle    [type of the third node]                          L
+ *   O3  4-path, end edge  [side of the inner endpoint][type of its other
+ *                   neighbour][type of the far end]                   2L^2
+ *   O4  4-path, centre edge [type of lo's other neighbour][of hi's]   L^2
+ *   O5  4-star      [side of the centre][pair of the other leaves]    2P
+ *   O6  4-cycle     [type of lo's other neighbour][of hi's]           L^2
+ *   O7  tailed triangle, tail edge [side of the degree-3 node][pair of
+ *                   the other triangle nodes]                         2P
+ *   O8  tailed triangle, edge opposite the degree-3 node [type of the
+ *                   degree-3 node][type of the tail]                  L^2
+ *   O9  tailed triangle, triangle edge at the degree-3 node [side of the
+ *                   degree-3 node][type of the third triangle node][type
+ *                   of the tail]                                      2L^2
+ *   O10 chordal cycle, outer edge [side of the degree-3 endpoint][type of
+ *                   the other degree-3 node][type of the other
+ *                   degree-2 node]                                    2L^2
+ *   O11 chordal cycle, chord [pair of the degree-2 nodes]             P
+ *   O12 4-clique    [pair of the other nodes]                         P
+ * The per-edge keys fix which endpoint holds each position; merging the
+ * two sides when phi_lo = phi_hi gives the instances of a (position-aware
+ * typed graphlet, edge orbit).  Global counts: Sec. 6 applied per class. */
+
+#define PA_MAX_CODES 4096               /* 8^4 labellings of a 4-node shape: L <= 8 here */
+
+static const int PA_K[9] = {2, 3, 3, 4, 4, 4, 4, 4, 4};
+static const int PA_EDGES[9][6][2] = {
+    {{0, 1}},
+    {{0, 1}, {0, 2}},
+    {{0, 1}, {0, 2}, {1, 2}},
+    {{0, 1}, {1, 2}, {2, 3}},
+    {{0, 1}, {0, 2}, {0, 3}},
+    {{0, 1}, {1, 2}, {2, 3}, {3, 0}},
+    {{0, 1}, {0, 2}, {0, 3}, {2, 3}},
+    {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}},
+    {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}},
+};
+static const int PA_NEDGES[9] = {1, 2, 3, 3, 3, 4, 4, 5, 6};
+
+static void pa_adjacency(int b, int A[4][4]) {
+    memset(A, 0, sizeof(int) * 16);
+    for (int x = 0; x < PA_NEDGES[b]; ++x) {
+        A[PA_EDGES[b][x][0]][PA_EDGES[b][x][1]] = 1;
+        A[PA_EDGES[b][x][1]][PA_EDGES[b][x][0]] = 1;
+    }
+}
+
+/* all permutations of k <= 4 nodes, as arrays; returns their number */
+static int all_perms(int k, int perms[24][4]) {
+    int np = 0, p[4];
+    for (p[0] = 0; p[0] < k; ++p[0])
+        for (p[1] = 0; p[1] < k; ++p[1])
+            for (p[2] = 0; p[2] < (k > 2 ? k : 1); ++p[2])
+                for (p[3] = 0; p[3] < (k > 3 ? k : 1); ++p[3]) {
+                    int used = 0, ok = 1;
+                    for (int a = 0; a < k; ++a) {
+                        if (used & (1 << p[a])) ok = 0;
+                        used |= 1 << p[a];
+                    }
+                    if (!ok) continue;
+                    for (int a = 0; a < 4; ++a) perms[np][a] = a < k ? p[a] : 0;
+                    ++np;
+                }
+    return np;
+}
+
+/* automorphisms of numbered shape b: permutations keeping its adjacency */
+static int pa_automorphisms(int b, int aut[24][4]) {
+    int A[4][4], perms[24][4], k = PA_K[b], na = 0;
+    pa_adjacency(b, A);
+    int np = all_perms(k, perms);
+    for (int x = 0; x < np; ++x) {
+        int ok = 1;
+        for (int u = 0; u < k && ok; ++u)
+            for (int v = 0; v < k && ok; ++v)
+                if (A[u][v] != A[perms[x][u]][perms[x][v]]) ok = 0;
+        if (ok) { memcpy(aut[na], perms[x], sizeof(perms[x])); ++na; }
+    }
+    return na;
+}
+
+static int pa_code(int L, int k, const int *lab) {
+    int c = 0;
+    for (int a = 0; a < k; ++a) c = c * L + lab[a];
+    return c;
+}
+
+/* class table of shape b: cls[code] = rank of the labelling's class;
+ * returns the number of classes */
+static int pa_class_table(int L, int b, int32_t *cls) {
+    int aut[24][4];
+    const int na = pa_automorphisms(b, aut), k = PA_K[b];
+    int ncodes = 1;
+    for (int a = 0; a < k; ++a) ncodes *= L;
+    int nclass = 0;
+    /* codes in increasing order are labellings in lexicographic order, so
+     * a canonical labelling is met before every other member of its class */
+    for (int code = 0; code < ncodes; ++code) {
+        int lab[4], x = code;
+        for (int a = k - 1; a >= 0; --a) { lab[a] = x % L; x /= L; }
+        int best = code;
+        for (int g = 0; g < na; ++g) {
+            int img[4];
+            for (int a = 0; a < k; ++a) img[a] = lab[aut[g][a]];
+            int c = pa_code(L, k, img);
+            if (c < best) best = c;
+        }
+        cls[code] = best == code ? nclass++ : cls[best];
+    }
+    return nclass;
+}
+
+static int64_t pa_block_size(int L, int b) {
+    int32_t cls[PA_MAX_CODES];
+    return pa_class_table(L, b, cls);
+}
+
+int64_t oracle_pa_per_edge_slots(int L) { return 3 * (int64_t)L + 9 * (int64_t)L * L + 6 * npairs(L); }
+
+int64_t oracle_pa_block_size(int L, int b) {
+    if (L < 1 || L > 8 || b < 0 || b > 8) return -1;
+    return pa_block_size(L, b);
+}
+
+int64_t oracle_pa_global_slots(int L) {
+    if (L < 1 || L > 8) return -1;
+    int64_t s = 0;
+    for (int b = 0; b < 9; ++b) s += pa_block_size(L, b);
+    return s;
+}
+
+/* class rank of a labelling of numbered shape b (-1 on a bad argument) */
+int64_t oracle_pa_class(int L, int b, const int32_t *lab) {
+    if (L < 1 || L > 8 || b < 0 || b > 8) return -1;
+    int32_t cls[PA_MAX_CODES];
+    pa_class_table(L, b, cls);
+    int l[4];
+    for (int a = 0; a < PA_K[b]; ++a) {
+        if (lab[a] < 0 || lab[a] >= L) return -1;
+        l[a] = lab[a];
+    }
+    return cls[pa_code(L, PA_K[b], l)];
+}
+
+/* per-edge block offsets O1..O12 (index 1..12) */
+static void pa_offsets(int L, int64_t off[13]) {
+    const int64_t P = npairs(L), LL = (int64_t)L * L;
+    const int64_t size[13] = {0, 2 * L, L, 2 * LL, LL, 2 * P, LL, 2 * P, LL, 2 * LL, 2 * LL, P, P};
+    off[0] = 0;
+    int64_t s = 0;
+    for (int o = 1; o <= 12; ++o) { off[o] = s; s += size[o]; }
+}
+
+typedef struct {
+    int L;
+    int32_t cls[9][PA_MAX_CODES];
+    int64_t block_off[9];
+    int64_t off[13];
+} pa_tables_t;
+
+static void pa_tables(int L, pa_tables_t *T) {
+    T->L = L;
+    int64_t s = 0;
+    for (int b = 0; b < 9; ++b) {
+        T->block_off[b] = s;
+        s += pa_class_table(L, b, T->cls[b]);
+    }
+    pa_offsets(L, T->off);
+}
+
+/* global slot of the instance whose node x sits at numbered position
+ * pos[x] of shape b (types phi of the instance's nodes v[]) */
+static int64_t pa_global_slot(const pa_tables_t *T, int b, int k, const int64_t *v, const int *pos,
+                              const uint8_t *phi) {
+    int lab[4];
+    for (int x = 0; x < k; ++x) lab[pos[x]] = phi[v[x]];
+    return T->block_off[b] + T->cls[b][pa_code(T->L, PA_K[b], lab)];
+}
+
+/* positions of the k nodes of an instance in numbered shape b: the first
+ * permutation (in the order all_perms lists them) that maps the instance's
+ * adjacency onto the shape's; 0 if there is none */
+static int pa_positions(int b, int k, int A[4][4], int *pos) {
+    int S[4][4], perms[24][4];
+    pa_adjacency(b, S);
+    int np = all_perms(k, perms);
+    for (int x = 0; x < np; ++x) {
+        int ok = 1;
+        for (int u = 0; u < k && ok; ++u)
+            for (int w = 0; w < k && ok; ++w)
+                if (A[u][w] != S[perms[x][u]][perms[x][w]]) ok = 0;
+        if (ok) { for (int u = 0; u < k; ++u) pos[u] = perms[x][u]; return 1; }
+    }
+    return 0;
+}
+
+/* Position-aware per-edge rows and global counts.  Every node set that
+ * contains the edge and induces a connected subgraph is visited: third
+ * nodes x adjacent to lo or hi, and pairs {x, y} with x adjacent to lo or hi
+ * and y adjacent to lo, hi or x.  The edge's slot follows from the induced
+ * degrees (layout above); the instance's class from a numbering of its
+ * nodes onto the shape.  Global: raw sums over edges divided by |E(H)|
+ * (Sec. 6).  per_edge_out: int64 [m][S_pa] or NULL; global_out: int64
+ * [G_pa] or NULL. */
+int oracle_position_aware(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *types, int L,
+                          int64_t *per_edge_out, int64_t *global_out) {
+    if (L < 1 || L > 8) return ERR_ARG;
+    graph_t G;
+    int rc = graph_open(&G, n, row_ptr, col, types, L);
+    if (rc != OK) { graph_close(&G); return rc; }
+    pa_tables_t *T = (pa_tables_t *)malloc(sizeof(pa_tables_t));
+    if (!T) { graph_close(&G); return ERR_MEM; }
+    pa_tables(L, T);
+    const int64_t S = oracle_pa_per_edge_slots(L), Gs = oracle_pa_global_slots(L), P = npairs(L);
+    int64_t *raw = (int64_t *)calloc((size_t)Gs, sizeof(int64_t));
+    if (!raw) { free(T); graph_close(&G); return ERR_MEM; }
+    if (per_edge_out) memset(per_edge_out, 0, (size_t)(G.m * S) * sizeof(int64_t));
+    const int64_t *O = T->off;
+    int bad = 0, memfail = 0;
+#pragma omp parallel reduction(|:bad, memfail)
+    {
+        int64_t *acc = (int64_t *)calloc((size_t)Gs, sizeof(int64_t));
+        int64_t *row = (int64_t *)malloc((size_t)S * sizeof(int64_t));
+        uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+        if (!acc || !row || !near) memfail = 1;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t e = 0; e < G.m; ++e) {
+            if (memfail) continue;
+            const int64_t lo = G.eu[e], hi = G.ev[e];
+            memset(row, 0, (size_t)S * sizeof(int64_t));
+            { int64_t v[2] = {lo, hi}; int pos[2] = {0, 1}; acc[pa_global_slot(T, 0, 2, v, pos, types)] += 1; }
+            /* U = neighbours of lo or hi, other than lo and hi */
+            for (int64_t k = G.rp[lo]; k < G.rp[lo + 1]; ++k) near[G.adj[k]] = 1;
+            for (int64_t k = G.rp[hi]; k < G.rp[hi + 1]; ++k) near[G.adj[k]] = 1;
+            near[lo] = near[hi] = 0;
+            for (int64_t x = 0; x < n; ++x) {
+                if (!near[x]) continue;
+                const int al = is_adjacent(&G, x, lo), ah = is_adjacent(&G, x, hi);
+                int64_t v[3] = {lo, hi, x};
+                if (al && ah) {                                          /* triangle */
+                    row[O[2] + types[x]] += 1;
+                    int pos[3] = {0, 1, 2};
+                    acc[pa_global_slot(T, 2, 3, v, pos, types)] += 1;
+                } else {                                                 /* 3-path, centre lo or hi */
+                    row[O[1] + (al ? 0 : 1) * L + types[x]] += 1;
+                    int pos[3] = {al ? 0 : 1, al ? 1 : 0, 2};
+                    acc[pa_global_slot(T, 1, 3, v, pos, types)] += 1;
+                }
+            }
+            /* 4-node sets {lo, hi, x, y}: x in U, and y in U with y > x, or
+             * y outside U adjacent to x */
+            for (int64_t x = 0; x < n; ++x) {
+                if (!near[x]) continue;
+                for (int pass = 0; pass < 2; ++pass) {
+                    const int64_t yb = pass == 0 ? x + 1 : G.rp[x], ye = pass == 0 ? n : G.rp[x + 1];
+                    for (int64_t yi = yb; yi < ye; ++yi) {
+                        const int64_t y = pass == 0 ? yi : G.adj[yi];
+                        if (y == lo || y == hi) continue;
+                        if (pass == 0 && !near[y]) continue;
+                        if (pass == 1 && near[y]) continue;
+                        const int64_t v[4] = {lo, hi, x, y};
+                        int A[4][4] = {{0}}, deg[4] = {0, 0, 0, 0}, ne = 0;
+                        for (int a = 0; a < 4; ++a)
+                            for (int c = a + 1; c < 4; ++c)
+                                if (is_adjacent(&G, v[a], v[c])) { A[a][c] = A[c][a] = 1; deg[a]++; deg[c]++; ++ne; }
+                        int mind = 4, maxd = 0;
+                        for (int a = 0; a < 4; ++a) {
+                            if (deg[a] < mind) mind = deg[a];
+                            if (deg[a] > maxd) maxd = deg[a];
+                        }
+                        if (ne < 3 || mind == 0) continue;               /* not connected */
+                        const int tx = types[x], ty = types[y];
+                        /* the other-node index (2 = x, 3 = y) adjacent to endpoint a */
+#define OTHER_AT(a) (A[a][2] ? 2 : 3)
+                        int b;
+                        if (ne == 3 && maxd == 2) {                      /* 4-path */
+                            b = 3;
+                            if (deg[0] == 2 && deg[1] == 2) {            /* centre edge */
+                                const int nl = OTHER_AT(0), nh = OTHER_AT(1);
+                                row[O[4] + types[v[nl]] * L + types[v[nh]]] += 1;
+                            } else {                                     /* end edge */
+                                const int s = deg[0] == 2 ? 0 : 1;
+                                const int nr = OTHER_AT(s), fr = 5 - nr;
+                                row[O[3] + s * L * L + types[v[nr]] * L + types[v[fr]]] += 1;
+                            }
+                        } else if (ne == 3) {                            /* 4-star, centre lo or hi */
+                            b = 4;
+                            const int s = deg[0] == 3 ? 0 : 1;
+                            row[O[5] + s * P + pair_index(L, tx, ty)] += 1;
+                        } else if (ne == 4 && maxd == 2) {               /* 4-cycle */
+                            b = 5;
+                            const int nl = OTHER_AT(0), nh = OTHER_AT(1);
+                            if (MUTANT(11)) row[O[6] + types[v[nh]] * L + types[v[nl]]] += 1;
+                            else row[O[6] + types[v[nl]] * L + types[v[nh]]] += 1;
+                        } else if (ne == 4) {                            /* tailed triangle */
+                            b = 6;
+                            int a3 = 0, tail = 0;
+                            for (int a = 0; a < 4; ++a) {
+                                if (deg[a] == 3) a3 = a;
+                                if (deg[a] == 1) tail = a;
+                            }
+                            if ((a3 == 0 && tail == 1) || (a3 == 1 && tail == 0)) {          /* tail edge */
+                                row[O[7] + a3 * P + pair_index(L, tx, ty)] += 1;
+                            } else if (a3 >= 2) {                                            /* opposite */
+                                row[O[8] + types[v[a3]] * L + types[v[tail]]] += 1;
+                            } else {                                                         /* at a3 */
+                                const int s = MUTANT(12) ? 1 - a3 : a3;
+                                const int third = 5 - tail;
+                                row[O[9] + s * L * L + types[v[third]] * L + types[v[tail]]] += 1;
+                            }
+                        } else if (ne == 5) {                            /* chordal cycle */
+                            b = 7;
+                            if (deg[0] == 3 && deg[1] == 3) {            /* chord */
+                                row[O[11] + pair_index(L, tx, ty)] += 1;
+                            } else {                                     /* outer edge */
+                                const int s = deg[0] == 3 ? 0 : 1;
+                                const int b3 = deg[2] == 3 ? 2 : 3, d2 = 5 - b3;
+                                row[O[10] + s * L * L + types[v[b3]] * L + types[v[d2]]] += 1;
+                            }
+                        } else {                                         /* 4-clique */
+                            b = 8;
+                            row[O[12] + pair_index(L, tx, ty)] += 1;
+                        }
+#undef OTHER_AT
+                        int pos[4];
+                        if (!pa_positions(b, 4, A, pos)) { bad = 1; continue; }
+                        acc[pa_global_slot(T, b, 4, v, pos, types)] += 1;
+                    }
+                }
+            }
+            for (int64_t k = G.rp[lo]; k < G.rp[lo + 1]; ++k) near[G.adj[k]] = 0;
+            for (int64_t k = G.rp[hi]; k < G.rp[hi + 1]; ++k) near[G.adj[k]] = 0;
+            if (per_edge_out) memcpy(per_edge_out + e * S, row, (size_t)S * sizeof(int64_t));
+        }
+#pragma omp critical
+        if (acc) for (int64_t s = 0; s < Gs; ++s) raw[s] += acc[s];
+        free(acc); free(row); free(near);
+    }
+    if (memfail) rc = ERR_MEM;
+    else if (bad) rc = ERR_REMAINDER;
+    if (rc == OK && global_out) {
+        for (int b = 0; b < 9; ++b) {
+            const int64_t end = b < 8 ? T->block_off[b + 1] : Gs;
+            for (int64_t s = T->block_off[b]; s < end; ++s) {
+                if (raw[s] % EDGES_OF_GRAPHLET[b]) rc = ERR_REMAINDER;
+                global_out[s] = raw[s] / EDGES_OF_GRAPHLET[b];
+            }
+        }
+    }
+    free(raw); free(T);
+    graph_close(&G);
+    return rc;
+}
+
+/* Position-aware global counts by brute force over all 2-, 3- and 4-node
+ * sets (no per-edge step): each connected set counted once in its class.
+ * Small graphs only. */
+int oracle_position_aware_brute(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *types, int L,
+                                int64_t *global_out) {
+    if (L < 1 || L > 8) return ERR_ARG;
+    graph_t G;
+    int rc = graph_open(&G, n, row_ptr, col, types, L);
+    if (rc != OK) { graph_close(&G); return rc; }
+    pa_tables_t *T = (pa_tables_t *)malloc(sizeof(pa_tables_t));
+    if (!T) { graph_close(&G); return ERR_MEM; }
+    pa_tables(L, T);
+    memset(global_out, 0, (size_t)oracle_pa_global_slots(L) * sizeof(int64_t));
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t b = a + 1; b < n; ++b) {
+            const int64_t v2[2] = {a, b};
+            int pos2[2] = {0, 1};
+            if (is_adjacent(&G, a, b)) global_out[pa_global_slot(T, 0, 2, v2, pos2, types)] += 1;
+            for (int64_t c = b + 1; c < n; ++c) {
+                int64_t v3[3] = {a, b, c};
+                int A[4][4] = {{0}}, ne = 0;
+                for (int x = 0; x < 3; ++x)
+                    for (int y = x + 1; y < 3; ++y)
+                        if (is_adjacent(&G, v3[x], v3[y])) { A[x][y] = A[y][x] = 1; ++ne; }
+                if (ne >= 2) {
+                    int pos[3], sh = ne == 2 ? 1 : 2;
+                    if (!pa_positions(sh, 3, A, pos)) rc = ERR_REMAINDER;
+                    else global_out[pa_global_slot(T, sh, 3, v3, pos, types)] += 1;
+                }
+                for (int64_t d = c + 1; d < n; ++d) {
+                    int64_t v4[4] = {a, b, c, d};
+                    int B[4][4] = {{0}}, deg[4] = {0, 0, 0, 0}, m4 = 0;
+                    for (int x = 0; x < 4; ++x)
+                        for (int y = x + 1; y < 4; ++y)
+                            if (is_adjacent(&G, v4[x], v4[y])) { B[x][y] = B[y][x] = 1; deg[x]++; deg[y]++; ++m4; }
+                    int mind = 4;
+                    for (int x = 0; x < 4; ++x) if (deg[x] < mind) mind = deg[x];
+                    if (m4 < 3 || mind == 0) continue;
+                    int pos[4], found = 0;
+                    for (int sh = 3; sh <= 8 && !found; ++sh) {
+                        if (PA_NEDGES[sh] != m4) continue;
+                        if (pa_positions(sh, 4, B, pos)) {
+                            global_out[pa_global_slot(T, sh, 4, v4, pos, types)] += 1;
+                            found = 1;
+                        }
+                    }
+                    if (!found) rc = ERR_REMAINDER;
+                }
+            }
+        }
+    free(T);
+    graph_close(&G);
+    return rc;
 }

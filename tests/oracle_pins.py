@@ -238,3 +238,105 @@ def untyped_identities(g, gl_untyped):
                 s += (deg[u] - 1) * (deg[v] - 1)
     out.append((s - 3 * ntri, np4 + 4 * nc4 + 2 * npaw + 6 * ndia + 12 * nk4))
     return out
+
+
+# ------------------------------------------- position-aware layout (Sec. 5)
+# Numbered shapes: 0 edge; 1 3-path, 0 the centre; 2 triangle; 3 4-path
+# 0-1-2-3; 4 4-star, 0 the centre; 5 4-cycle 0-1-2-3-0; 6 tailed triangle, 0
+# the degree-3 node, 1 the tail; 7 chordal cycle, 0-1 the chord; 8 4-clique.
+
+BLOCK_EDGES = {0: 1, **GRAPHLET_EDGES}
+
+SHAPES = {0: [(0, 1)], 1: [(0, 1), (0, 2)], 2: [(0, 1), (0, 2), (1, 2)], 3: [(0, 1), (1, 2), (2, 3)],
+          4: [(0, 1), (0, 2), (0, 3)], 5: [(0, 1), (1, 2), (2, 3), (3, 0)], 6: [(0, 1), (0, 2), (0, 3), (2, 3)],
+          7: [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)], 8: [(a, b) for a in range(4) for b in range(a + 1, 4)]}
+
+
+def automorphisms(b):
+    k = 2 if b == 0 else (3 if b <= 2 else 4)
+    E = {frozenset(e) for e in SHAPES[b]}
+    return [p for p in itertools.permutations(range(k)) if {frozenset((p[u], p[v])) for u, v in E} == E]
+
+
+def canonical_classes(L, b):
+    """{labelling: rank} for every labelling, ranks by smallest member."""
+    k = len(automorphisms(b)[0])
+    aut = automorphisms(b)
+    canon = {}
+    for lab in itertools.product(range(L), repeat=k):
+        canon[lab] = min(tuple(lab[p[x]] for x in range(k)) for p in aut)
+    reps = sorted(set(canon.values()))
+    rank = {r: i for i, r in enumerate(reps)}
+    return {lab: rank[c] for lab, c in canon.items()}
+
+
+def burnside(L):
+    """Number of labellings up to automorphism, per block, in closed form."""
+    P = L * (L + 1) // 2
+    return [P, L * P, math.comb(L + 2, 3), (L ** 4 + L ** 2) // 2, L * math.comb(L + 2, 3),
+            (L ** 4 + 2 * L ** 3 + 3 * L ** 2 + 2 * L) // 8, L * L * P, P * P, math.comb(L + 3, 4)]
+
+
+def pa_sizes(L):
+    """Per-edge block sizes O1..O12."""
+    P, LL = L * (L + 1) // 2, L * L
+    return [2 * L, L, 2 * LL, LL, 2 * P, LL, 2 * P, LL, 2 * LL, 2 * LL, P, P]
+
+
+def pa_offsets(L):
+    return np.concatenate([[0], np.cumsum(pa_sizes(L))])
+
+
+def slot_instance(L, slot, p_lo, p_hi):
+    """(global block, labelling of the numbered shape) of per-edge slot `slot`
+    for an edge whose endpoints have types p_lo, p_hi."""
+    off = pa_offsets(L)
+    o = int(np.searchsorted(off, slot, side="right"))          # 1..12
+    r = slot - off[o - 1]
+    LL, P = L * L, L * (L + 1) // 2
+    pr = pairs(L)
+    side = lambda s: (p_lo, p_hi) if s == 0 else (p_hi, p_lo)  # noqa: E731  (that side, the other)
+    if o == 1:
+        me, other = side(r // L)
+        return 1, (me, other, r % L)
+    if o == 2:
+        return 2, (p_lo, p_hi, r)
+    if o == 3:
+        me, other = side(r // LL)
+        x, y = divmod(r % LL, L)
+        return 3, (y, x, me, other)
+    if o == 4:
+        x, y = divmod(r, L)
+        return 3, (x, p_lo, p_hi, y)
+    if o == 5:
+        me, other = side(r // P)
+        t, u = pr[r % P]
+        return 4, (me, other, t, u)
+    if o == 6:
+        x, y = divmod(r, L)
+        return 5, (p_lo, p_hi, y, x)
+    if o == 7:
+        me, other = side(r // P)
+        t, u = pr[r % P]
+        return 6, (me, other, t, u)
+    if o == 8:
+        x, y = divmod(r, L)
+        return 6, (x, y, p_lo, p_hi)
+    if o == 9:
+        me, other = side(r // LL)
+        x, y = divmod(r % LL, L)
+        return 6, (me, y, other, x)
+    if o == 10:
+        me, other = side(r // LL)
+        x, y = divmod(r % LL, L)
+        return 7, (me, x, other, y)
+    t, u = pr[r]
+    return (7 if o == 11 else 8), (p_lo, p_hi, t, u)
+
+
+def global_slot_pa(L, block, lab, classes=None):
+    sizes = burnside(L)
+    classes = classes or {}
+    if block not in classes:
+        classes[block] = canonical_classes(L, block)
+    return sum(sizes[:block]) + classes[block][tuple(lab)]

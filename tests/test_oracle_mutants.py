@@ -5,7 +5,9 @@ plants one plausible mistake: a dropped term in Lemma 1, a lost tie-break
 in Alg. 2, j left inside S_i, transposed operands in Lemma 3, a wrong branch
 in Alg. 3, an unsorted type multiset, a missing 1/2 in Lemma 2, a lost
 exclusion of i and j in Alg. 2; in the weighted graph of Alg. 5, tailed
-triangles booked as 4-cycles and D missing one endpoint of each edge.  The pin battery here (closed forms,
+triangles booked as 4-cycles and D missing one endpoint of each edge; in
+the position-aware counts of Sec. 5, the two sides of a 4-cycle key swapped
+and the degree-3 side of a tailed triangle swapped.  The pin battery here (closed forms,
 layout enumeration, the brute-force and networkx-free subset count) must
 reject every one of them, on the CPU.
 """
@@ -16,8 +18,8 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_pins import (expected_clique, expected_complete_bipartite, expected_cycle, expected_star,
-                         graph_from_edges, multisets, random_graph)
+from oracle_pins import (BLOCK_EDGES, burnside, expected_clique, expected_complete_bipartite, expected_cycle,
+                         expected_star, global_slot_pa, graph_from_edges, multisets, random_graph, slot_instance)
 
 MUTANTS = {
     1: "Lemma 1 without the 4-cycle term",
@@ -30,6 +32,8 @@ MUTANTS = {
     8: "Alg. 2 scans i and j as neighbours of w_k",
     9: "Alg. 5 weights book a tailed triangle as a 4-cycle",
     10: "Alg. 5 degree adds each edge's weight to one endpoint only",
+    11: "Sec. 5 4-cycle key (lo's neighbour, hi's neighbour) transposed",
+    12: "Sec. 5 tailed-triangle edge at the degree-3 node booked on the other side",
 }
 
 
@@ -91,6 +95,27 @@ def _battery(lib) -> list:
             np.add.at(want_d, dst, w)
             return np.array_equal(w.sum(0), edges_of * gl) and np.array_equal(d, want_d)
         check(f"weights seed={seed}", w_sums)
+
+    # position-aware counts of Sec. 5: mapping every per-edge slot to the
+    # class of its instance and summing gives |E(H)| x the global counts
+    for seed in range(3):
+        g = random_graph(11 + seed, 0.5, 3, 95 + seed)
+
+        def pa_sums(g=g):
+            pe, gl = oracle.position_aware(g, lib=lib)
+            src, dst = oracle.edges(g, lib=lib)
+            ty, L = g["types"], g["L"]
+            raw = np.zeros_like(gl)
+            classes = {}
+            for e in range(len(src)):
+                raw[global_slot_pa(L, 0, (ty[src[e]], ty[dst[e]]), classes)] += 1
+                for slot in np.nonzero(pe[e])[0]:
+                    b, lab = slot_instance(L, int(slot), int(ty[src[e]]), int(ty[dst[e]]))
+                    raw[global_slot_pa(L, b, lab, classes)] += pe[e, slot]
+            off = np.concatenate([[0], np.cumsum(burnside(L))])
+            return all(np.array_equal(raw[off[b]:off[b + 1]], BLOCK_EDGES[b] * gl[off[b]:off[b + 1]])
+                       for b in range(9))
+        check(f"position-aware seed={seed}", pa_sums)
     return failed
 
 
