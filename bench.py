@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200_000 / 60, help="serving: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=1.0, help="serving: seconds of arrivals")
     ap.add_argument("--pool", type=int, default=128, help="serving: distinct request graphs")
+    ap.add_argument("--position-aware", action="store_true",
+                    help="plain mode: also time the position-aware count (Sec. 5) of the same graph")
     return ap.parse_args()
 
 
@@ -390,6 +392,46 @@ def run_ours(args):
                       "d2h_bytes_per_step": int(bo), "nonzero_pairs": int(nnz),
                       "pairs_per_edge": round(nnz / max(m, 1), 2)}
 
+    # position-aware counts (Sec. 5) of the same graph: same gathering
+    # passes, position-aware epilogue, rows of S_pa slots
+    position_aware = None
+    if args.position_aware and rank == 0:
+        lay_pa = tg.tg_pa_layout(L)
+        pe_pa = torch.empty((m, lay_pa["per_edge_slots"]), dtype=torch.int32, device=dev)
+        gl_pa = torch.empty(lay_pa["global_slots"], dtype=torch.int64, device=dev)
+        pa_ms = {}
+
+        def pa_step(timing: bool):
+            h = tg.tg_build(rp, col, ty, L, stream=stream)
+            if timing:
+                tg.tg_set_timing(h, True)
+            tg.tg_count_position_aware(h, pe_pa, gl_pa, stream=stream)
+            if timing:
+                for name, (kms, n) in tg.tg_get_timing(h).items():
+                    pa_ms[name] = pa_ms.get(name, 0.0) + kms
+            st = tg.tg_query_status(h) if timing else 0
+            h.free()
+            return st
+
+        for _ in range(args.warmup):
+            pa_step(False)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        pa_status = 0
+        for _ in range(args.steps):
+            pa_status = pa_status or pa_step(True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pms = a0.elapsed_time(a1)
+        position_aware = {"value": round(m * args.steps / (pms / 1e3), 1), "unit": UNIT,
+                          "ms_per_step": round(pms / args.steps, 3), "status": tg.STATUS[pa_status],
+                          "per_edge_slots": lay_pa["per_edge_slots"], "global_slots": lay_pa["global_slots"],
+                          "k_epi4_pa_ms_per_step": round(pa_ms.get("k_epi4_pa", 0.0) / args.steps, 3),
+                          "k_epi4_ms_per_step": round(kernel_ms.get("k_epi4", [0.0])[0] / args.steps, 3),
+                          "step": "tg_build + tg_count_position_aware + tg_free, device-resident"}
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(g, args.cpu_seconds)
@@ -408,6 +450,8 @@ def run_ours(args):
             "cpu_baseline": cpu, "e2e": e2e, "e2e_sparse": e2e_sparse, "clocks": clk,
             "gpu_launches": int(launches[0]),
         }
+        if position_aware is not None:
+            line["position_aware"] = position_aware
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -243,6 +243,80 @@ tg_status tg_count_sparse(tg_graph *g, int32_t k, int64_t *row_off, uint16_t *sl
 tg_status tg_graphlet_weights(tg_graph *g, int32_t k, const uint32_t *per_edge_rows, int32_t block, int64_t rank,
                               int64_t *weights, int64_t *degree, void *stream);
 
+/* ---- position-aware typed graphlets (Sec. 5, Def. 8) ------------------
+ *
+ * Def. 8 identifies two typed instances of one shape when an isomorphism
+ * between them maps every node onto a node of the same type.  With the
+ * shape's nodes numbered, a position-aware typed graphlet is a labelling
+ * (types of nodes 0..k-1) up to the automorphisms of the numbered shape;
+ * its global slot ranks it by its lexicographically smallest labelling
+ * within the shape's block.  Numbered shapes (global blocks 0..8): 0 edge
+ * 0-1; 1 3-path, 0 the centre; 2 triangle; 3 4-path 0-1-2-3; 4 4-star, 0
+ * the centre; 5 4-cycle 0-1-2-3-0; 6 tailed triangle, 0 the degree-3 node, 1
+ * the tail, 2-3 the triangle's other edge; 7 chordal cycle, 0-1 the chord;
+ * 8 4-clique.  Block sizes are the numbers of labellings up to symmetry
+ * (Burnside), e.g. (L^4 + L^2)/2 for the 4-path; L^K labellings in all.
+ *
+ * Per-edge rows (uint32, S_pa(L) = 3L + 9L^2 + 6P slots): edge e = {lo, hi},
+ * lo < hi in the caller's ids; "side" 0 = lo, 1 = hi; an ordered type pair
+ * (x, y) at x*L + y; an unordered pair at pair(t, t') as in the typed layout.
+ * Blocks, in this order (block_offset[1..12]):
+ *   O1  3-path: [side of the centre][type of the third node]          2L
+ *   O2  triangle: [type of the third node]                             L
+ *   O3  4-path, end edge: [side of the inner endpoint][type of its other
+ *       neighbour][type of the far end]                                2L^2
+ *   O4  4-path, centre edge: [type of lo's other neighbour][of hi's]   L^2
+ *   O5  4-star: [side of the centre][pair of the other two leaves]     2P
+ *   O6  4-cycle: [type of lo's other neighbour][of hi's]               L^2
+ *   O7  tailed triangle, tail edge: [side of the degree-3 node][pair of
+ *       the other two triangle nodes]                                  2P
+ *   O8  tailed triangle, edge opposite the degree-3 node: [type of the
+ *       degree-3 node][type of the tail]                               L^2
+ *   O9  tailed triangle, triangle edge at the degree-3 node: [side of the
+ *       degree-3 node][type of the third triangle node][type of the tail]
+ *                                                                      2L^2
+ *   O10 chordal cycle, outer edge: [side of the degree-3 endpoint][type of
+ *       the other degree-3 node][type of the other degree-2 node]      2L^2
+ *   O11 chordal cycle, chord: [pair of the two degree-2 nodes]         P
+ *   O12 4-clique: [pair of the other two nodes]                        P
+ * Summing the sides and the orderings of a row gives the typed row of
+ * tg_count (k = 4).  A count above 2^32-1 saturates as in tg_count. */
+typedef struct {
+    int32_t L;
+    int64_t per_edge_slots;           /* S_pa(L) */
+    int64_t global_slots;             /* G_pa(L): sum of the block sizes */
+    int64_t block_offset[13];         /* first per-edge slot of O1..O12; entry 0 unused */
+    int64_t global_block_offset[9];
+    int64_t global_block_size[9];
+    int32_t graphlet_edges[9];        /* |E(H)| of each global block */
+} tg_pa_layout_t;
+
+/* Fills *out for L types.  Pure host function.  Errors:
+ * TG_ERR_TOO_MANY_TYPES, TG_ERR_INVALID_ARG (NULL). */
+tg_status tg_pa_layout(int32_t L, tg_pa_layout_t *out);
+
+/* The smallest labelling of position-aware class `rank` of global block
+ * `block`: types_out[0..k-1] (host, k = 2, 3 or 4 nodes of the numbered
+ * shape).  Pure host function.  Errors: TG_ERR_TOO_MANY_TYPES,
+ * TG_ERR_INVALID_ARG (block, rank, NULL). */
+tg_status tg_pa_labelling(int32_t L, int32_t block, int64_t rank, int32_t *types_out);
+
+/* The global slot (class) counted by per-edge slot `slot` of an edge whose
+ * endpoints have types phi_lo (the smaller caller id) and phi_hi: the
+ * position-aware typed graphlet of the instances that slot counts; slot =
+ * S_pa(L) gives the class of the edge itself (block 0).  *class_out (host)
+ * receives the global slot.  Pure host function.  Errors:
+ * TG_ERR_TOO_MANY_TYPES, TG_ERR_INVALID_ARG (types, slot, NULL). */
+tg_status tg_pa_slot_class(int32_t L, int32_t phi_lo, int32_t phi_hi, int64_t slot, int64_t *class_out);
+
+/* Position-aware counts of every graph of the handle: per_edge_out uint32
+ * [m][S_pa(L)] or NULL; global_out int64 [ngraphs][G_pa(L)] or NULL (each
+ * class's instances: the per-edge sums divided by |E(H)|, Sec. 6).  Host
+ * or device buffers.  The gathering passes are those of tg_count (k = 4);
+ * only the per-edge epilogue differs.  Errors: TG_ERR_INVALID_ARG,
+ * TG_ERR_OOM, TG_ERR_CUDA (device-detected errors go to the status word). */
+tg_status tg_count_position_aware(tg_graph *g, uint32_t *per_edge_out, int64_t *global_out, void *stream);
+
 /* Batched form: counts every graph of a batch handle with the whole
  * sequence of kernels captured once into a CUDA graph and replayed on later
  * calls with the same (k, per_edge_out, global_out, stream).  Results are

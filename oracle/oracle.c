@@ -935,6 +935,9 @@ typedef struct {
     int32_t cls[9][PA_MAX_CODES];
     int64_t block_off[9];
     int64_t off[13];
+    int perms[24][4];                   /* all permutations of 4 nodes */
+    int nperms;
+    int shape[9][4][4];                 /* adjacency of each numbered shape */
 } pa_tables_t;
 
 static void pa_tables(int L, pa_tables_t *T) {
@@ -943,8 +946,10 @@ static void pa_tables(int L, pa_tables_t *T) {
     for (int b = 0; b < 9; ++b) {
         T->block_off[b] = s;
         s += pa_class_table(L, b, T->cls[b]);
+        pa_adjacency(b, T->shape[b]);
     }
     pa_offsets(L, T->off);
+    T->nperms = all_perms(4, T->perms);
 }
 
 /* global slot of the instance whose node x sits at numbered position
@@ -959,14 +964,20 @@ static int64_t pa_global_slot(const pa_tables_t *T, int b, int k, const int64_t 
 /* positions of the k nodes of an instance in numbered shape b: the first
  * permutation (in the order all_perms lists them) that maps the instance's
  * adjacency onto the shape's; 0 if there is none */
-static int pa_positions(int b, int k, int A[4][4], int *pos) {
-    int S[4][4], perms[24][4];
-    pa_adjacency(b, S);
-    int np = all_perms(k, perms);
+static int pa_positions(const pa_tables_t *T, int b, int k, int A[4][4], int *pos) {
+    int small[24][4], nsmall = 0;
+    const int (*perms)[4] = T->perms;
+    int np = T->nperms;
+    if (k < 4) {                                     /* permutations of the first k nodes */
+        nsmall = all_perms(k, small);
+        perms = (const int (*)[4])small;
+        np = nsmall;
+    }
+    const int (*S)[4] = T->shape[b];
     for (int x = 0; x < np; ++x) {
         int ok = 1;
         for (int u = 0; u < k && ok; ++u)
-            for (int w = 0; w < k && ok; ++w)
+            for (int w = u + 1; w < k && ok; ++w)
                 if (A[u][w] != S[perms[x][u]][perms[x][w]]) ok = 0;
         if (ok) { for (int u = 0; u < k; ++u) pos[u] = perms[x][u]; return 1; }
     }
@@ -974,9 +985,9 @@ static int pa_positions(int b, int k, int A[4][4], int *pos) {
 }
 
 /* Position-aware per-edge rows and global counts.  Every node set that
- * contains the edge and induces a connected subgraph is visited: third
- * nodes x adjacent to lo or hi, and pairs {x, y} with x adjacent to lo or hi
- * and y adjacent to lo, hi or x.  The edge's slot follows from the induced
+ * contains the edge and induces a connected subgraph is visited once: third
+ * nodes x in U (the neighbours of lo or hi), and pairs {x, y} with x in U and
+ * y in U after x or y a neighbour of x outside U.  The edge's slot follows from the induced
  * degrees (layout above); the instance's class from a numbering of its
  * nodes onto the shape.  Global: raw sums over edges divided by |E(H)|
  * (Sec. 6).  per_edge_out: int64 [m][S_pa] or NULL; global_out: int64
@@ -1000,48 +1011,59 @@ int oracle_position_aware(int64_t n, const int64_t *row_ptr, const int32_t *col,
     {
         int64_t *acc = (int64_t *)calloc((size_t)Gs, sizeof(int64_t));
         int64_t *row = (int64_t *)malloc((size_t)S * sizeof(int64_t));
-        uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
-        if (!acc || !row || !near) memfail = 1;
+        uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);  /* bit 0: adjacent to lo, bit 1: to hi */
+        int64_t *U = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+        if (!acc || !row || !near || !U) memfail = 1;
 #pragma omp for schedule(dynamic, 16)
         for (int64_t e = 0; e < G.m; ++e) {
             if (memfail) continue;
             const int64_t lo = G.eu[e], hi = G.ev[e];
             memset(row, 0, (size_t)S * sizeof(int64_t));
             { int64_t v[2] = {lo, hi}; int pos[2] = {0, 1}; acc[pa_global_slot(T, 0, 2, v, pos, types)] += 1; }
-            /* U = neighbours of lo or hi, other than lo and hi */
-            for (int64_t k = G.rp[lo]; k < G.rp[lo + 1]; ++k) near[G.adj[k]] = 1;
-            for (int64_t k = G.rp[hi]; k < G.rp[hi + 1]; ++k) near[G.adj[k]] = 1;
-            near[lo] = near[hi] = 0;
-            for (int64_t x = 0; x < n; ++x) {
-                if (!near[x]) continue;
-                const int al = is_adjacent(&G, x, lo), ah = is_adjacent(&G, x, hi);
+            /* U = the nodes other than lo and hi adjacent to lo or hi */
+            int64_t nu = 0;
+            for (int side = 0; side < 2; ++side) {
+                const int64_t a = side == 0 ? lo : hi, other = side == 0 ? hi : lo;
+                for (int64_t k = G.rp[a]; k < G.rp[a + 1]; ++k) {
+                    const int64_t x = G.adj[k];
+                    if (x == other) continue;
+                    if (!near[x]) U[nu++] = x;
+                    near[x] |= (uint8_t)(1 << side);
+                }
+            }
+            for (int64_t ux = 0; ux < nu; ++ux) {                   /* 3-node sets */
+                const int64_t x = U[ux];
                 int64_t v[3] = {lo, hi, x};
-                if (al && ah) {                                          /* triangle */
+                if (near[x] == 3) {                                  /* triangle */
                     row[O[2] + types[x]] += 1;
                     int pos[3] = {0, 1, 2};
                     acc[pa_global_slot(T, 2, 3, v, pos, types)] += 1;
-                } else {                                                 /* 3-path, centre lo or hi */
+                } else {                                             /* 3-path, centre lo or hi */
+                    const int al = near[x] & 1;
                     row[O[1] + (al ? 0 : 1) * L + types[x]] += 1;
                     int pos[3] = {al ? 0 : 1, al ? 1 : 0, 2};
                     acc[pa_global_slot(T, 1, 3, v, pos, types)] += 1;
                 }
             }
-            /* 4-node sets {lo, hi, x, y}: x in U, and y in U with y > x, or
-             * y outside U adjacent to x */
-            for (int64_t x = 0; x < n; ++x) {
-                if (!near[x]) continue;
+            /* 4-node sets {lo, hi, x, y}: x in U, and y in U after x, or y
+             * outside U (and not lo, hi) adjacent to x */
+            for (int64_t ux = 0; ux < nu; ++ux) {
+                const int64_t x = U[ux];
                 for (int pass = 0; pass < 2; ++pass) {
-                    const int64_t yb = pass == 0 ? x + 1 : G.rp[x], ye = pass == 0 ? n : G.rp[x + 1];
+                    const int64_t yb = pass == 0 ? ux + 1 : G.rp[x], ye = pass == 0 ? nu : G.rp[x + 1];
                     for (int64_t yi = yb; yi < ye; ++yi) {
-                        const int64_t y = pass == 0 ? yi : G.adj[yi];
-                        if (y == lo || y == hi) continue;
-                        if (pass == 0 && !near[y]) continue;
-                        if (pass == 1 && near[y]) continue;
+                        const int64_t y = pass == 0 ? U[yi] : G.adj[yi];
+                        if (pass == 1 && (near[y] || y == lo || y == hi)) continue;
                         const int64_t v[4] = {lo, hi, x, y};
                         int A[4][4] = {{0}}, deg[4] = {0, 0, 0, 0}, ne = 0;
-                        for (int a = 0; a < 4; ++a)
-                            for (int c = a + 1; c < 4; ++c)
-                                if (is_adjacent(&G, v[a], v[c])) { A[a][c] = A[c][a] = 1; deg[a]++; deg[c]++; ++ne; }
+                        const int xy = pass == 1 ? 1 : is_adjacent(&G, x, y);
+                        const int adj4[6][3] = {{0, 1, 1}, {0, 2, near[x] & 1}, {0, 3, near[y] & 1},
+                                                {1, 2, (near[x] >> 1) & 1}, {1, 3, (near[y] >> 1) & 1}, {2, 3, xy}};
+                        for (int q = 0; q < 6; ++q)
+                            if (adj4[q][2]) {
+                                const int a = adj4[q][0], c = adj4[q][1];
+                                A[a][c] = A[c][a] = 1; deg[a]++; deg[c]++; ++ne;
+                            }
                         int mind = 4, maxd = 0;
                         for (int a = 0; a < 4; ++a) {
                             if (deg[a] < mind) mind = deg[a];
@@ -1102,18 +1124,17 @@ int oracle_position_aware(int64_t n, const int64_t *row_ptr, const int32_t *col,
                         }
 #undef OTHER_AT
                         int pos[4];
-                        if (!pa_positions(b, 4, A, pos)) { bad = 1; continue; }
+                        if (!pa_positions(T, b, 4, A, pos)) { bad = 1; continue; }
                         acc[pa_global_slot(T, b, 4, v, pos, types)] += 1;
                     }
                 }
             }
-            for (int64_t k = G.rp[lo]; k < G.rp[lo + 1]; ++k) near[G.adj[k]] = 0;
-            for (int64_t k = G.rp[hi]; k < G.rp[hi + 1]; ++k) near[G.adj[k]] = 0;
+            for (int64_t ux = 0; ux < nu; ++ux) near[U[ux]] = 0;
             if (per_edge_out) memcpy(per_edge_out + e * S, row, (size_t)S * sizeof(int64_t));
         }
 #pragma omp critical
         if (acc) for (int64_t s = 0; s < Gs; ++s) raw[s] += acc[s];
-        free(acc); free(row); free(near);
+        free(acc); free(row); free(near); free(U);
     }
     if (memfail) rc = ERR_MEM;
     else if (bad) rc = ERR_REMAINDER;
@@ -1157,7 +1178,7 @@ int oracle_position_aware_brute(int64_t n, const int64_t *row_ptr, const int32_t
                         if (is_adjacent(&G, v3[x], v3[y])) { A[x][y] = A[y][x] = 1; ++ne; }
                 if (ne >= 2) {
                     int pos[3], sh = ne == 2 ? 1 : 2;
-                    if (!pa_positions(sh, 3, A, pos)) rc = ERR_REMAINDER;
+                    if (!pa_positions(T, sh, 3, A, pos)) rc = ERR_REMAINDER;
                     else global_out[pa_global_slot(T, sh, 3, v3, pos, types)] += 1;
                 }
                 for (int64_t d = c + 1; d < n; ++d) {
@@ -1172,7 +1193,7 @@ int oracle_position_aware_brute(int64_t n, const int64_t *row_ptr, const int32_t
                     int pos[4], found = 0;
                     for (int sh = 3; sh <= 8 && !found; ++sh) {
                         if (PA_NEDGES[sh] != m4) continue;
-                        if (pa_positions(sh, 4, B, pos)) {
+                        if (pa_positions(T, sh, 4, B, pos)) {
                             global_out[pa_global_slot(T, sh, 4, v4, pos, types)] += 1;
                             found = 1;
                         }

@@ -128,6 +128,47 @@ tg_status tg_layout(int32_t L, int32_t k, tg_layout_t *out) {
     });
 }
 
+tg_status tg_pa_layout(int32_t L, tg_pa_layout_t *out) {
+    return guarded([&] {
+        check_types(L);
+        if (!out) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        const tg::PaLayout Y = tg::pa_layout(L);
+        tg_pa_layout_t r;
+        std::memset(&r, 0, sizeof(r));
+        r.L = L;
+        r.per_edge_slots = Y.S;
+        r.global_slots = Y.G;
+        for (int o = 1; o <= 12; ++o) r.block_offset[o] = Y.off[o];
+        const int edges_of[9] = {1, 2, 3, 3, 3, 4, 4, 5, 6};
+        for (int b = 0; b < 9; ++b) {
+            r.global_block_offset[b] = Y.boff[b];
+            r.global_block_size[b] = Y.bsize[b];
+            r.graphlet_edges[b] = edges_of[b];
+        }
+        *out = r;
+    });
+}
+
+tg_status tg_pa_labelling(int32_t L, int32_t block, int64_t rank, int32_t *types_out) {
+    return guarded([&] {
+        check_types(L);
+        if (!types_out || block < 0 || block > 8) throw Error{TG_ERR_INVALID_ARG, "block"};
+        if (!tg::pa_labelling(L, block, rank, types_out)) throw Error{TG_ERR_INVALID_ARG, "rank"};
+    });
+}
+
+tg_status tg_pa_slot_class(int32_t L, int32_t phi_lo, int32_t phi_hi, int64_t slot, int64_t *class_out) {
+    return guarded([&] {
+        check_types(L);
+        if (!class_out || phi_lo < 0 || phi_lo >= L || phi_hi < 0 || phi_hi >= L)
+            throw Error{TG_ERR_INVALID_ARG, "types"};
+        const tg::PaLayout Y = tg::pa_layout(L);
+        if (slot < 0 || slot > Y.S) throw Error{TG_ERR_INVALID_ARG, "slot"};
+        const std::vector<int32_t> table = tg::pa_class_table(Y);
+        *class_out = table[(size_t)(phi_lo * L + phi_hi) * (Y.S + 1) + slot];
+    });
+}
+
 void tg_default_options(tg_options *opt) {
     if (opt) tg::fill_defaults(opt);
 }
@@ -202,6 +243,35 @@ tg_status tg_count(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_t *glo
         TG_CK(cudaMemsetAsync(G.gacc.p, 0, (size_t)G.ngraphs * tg::global_slots(G.L, 4) * sizeof(unsigned long long), s));
         int64_t launches = tg::run_count(G, k, 0, G.m, pe, G.gacc.as<unsigned long long>(), true, s);
         if (gl) launches += tg::launch_finalize(G, k, gl, s);
+        if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
+        if (gl_staged) TG_CK(cudaMemcpyAsync(global_out, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
+        if (pe_staged || gl_staged) TG_CK(cudaStreamSynchronize(s));
+        G.last_launches = launches;
+    });
+}
+
+tg_status tg_count_position_aware(tg_graph *gh, uint32_t *per_edge_out, int64_t *global_out, void *stream) {
+    return guarded([&] {
+        if (!gh) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        Graph &G = gh->g;
+        cudaStream_t s = (cudaStream_t)stream;
+        G.stream = s;
+        tg::prepare_counting(G, 4, s);
+        tg::prepare_edges(G, 4, s);
+        tg::prepare_position_aware(G, s);
+        const size_t pe_bytes = (size_t)G.m * G.pa.S * sizeof(uint32_t);
+        const size_t gl_bytes = (size_t)G.ngraphs * G.pa.G * sizeof(int64_t);
+        bool pe_staged = false, gl_staged = false;
+        uint32_t *pe = device_out(per_edge_out, pe_bytes, G.stage_pe, pe_staged);
+        int64_t *gl = device_out(global_out, gl_bytes, G.stage_gl, gl_staged);
+        TG_CK(cudaMemsetAsync(G.pa_gacc.p, 0, (size_t)G.ngraphs * G.pa.G * sizeof(unsigned long long), s));
+        struct Active {                                  // the epilogue writes position-aware rows meanwhile
+            Graph &G;
+            explicit Active(Graph &g) : G(g) { G.pa_active = true; }
+            ~Active() { G.pa_active = false; }
+        } active(G);
+        int64_t launches = tg::run_count(G, 4, 0, G.m, pe, G.pa_gacc.as<unsigned long long>(), true, s);
+        if (gl) launches += tg::launch_finalize_pa(G, gl, s);
         if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
         if (gl_staged) TG_CK(cudaMemcpyAsync(global_out, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
         if (pe_staged || gl_staged) TG_CK(cudaStreamSynchronize(s));

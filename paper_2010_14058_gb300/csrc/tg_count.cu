@@ -1350,6 +1350,203 @@ __global__ void __launch_bounds__(256) k_edge3(GraphView g, CountView cv, const 
     if (cur_graph >= 0) flush_hist(hist, G, gacc, cur_graph, blockDim.x, threadIdx.x);
 }
 
+// ------------------------------------------------- position-aware epilogue
+// Sec. 5 (Def. 8): before k_epi4 folds them into unordered type pairs, its
+// matrices already keep the positions of an instance apart: Ri / Rj (4-path
+// end edges with inner endpoint i / j: w the inner endpoint's other
+// neighbour, r the far end), Q (4-cycles; first index the type of j's
+// neighbour), Wi / Wj (adjacent pairs inside S_i / S_j), CTi / CTj (a
+// triangle node and an adjacent node of S_i / S_j), G8 (a triangle node and
+// its tail in I) and K (adjacent pairs inside T).  k_epi4_pa writes them by
+// position -- the row layout of tg_pa.cu, sides named by caller ids (lo =
+// the smaller) -- and adds every count to the class that the slot and the
+// endpoint types fix (host table).  One warp per edge, as k_epi4.
+struct PaView {
+    const int32_t *cls;       // [L*L][S+1] class of (phi_lo, phi_hi, slot); slot S: the edge itself
+    const int32_t *old_of;    // [n] caller id of each internal node
+    int32_t S;                // per-edge slots
+    int32_t G;                // classes (global slots) per graph
+    int32_t off[13];          // first slot of blocks O1..O12
+};
+
+__host__ __device__ __forceinline__ size_t epi4_pa_hist_words(int G) { return (size_t)((G + 1) & ~1); }
+
+__global__ void __launch_bounds__(256) k_epi4_pa(GraphView g, CountView cv, PaView pv, const Tile *__restrict__ tiles,
+                                                 int64_t n_tiles, int64_t row_base, uint32_t *per_edge_out,
+                                                 unsigned long long *gacc, int copies) {
+    extern __shared__ unsigned long long hist_all[];
+    const int L = g.L, LL = L * L, P = L * (L + 1) / 2;
+    const int S = pv.S, G = pv.G;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int HW = (int)epi4_pa_hist_words(G);
+    unsigned long long *hist = hist_all + (wid % copies) * HW;
+    for (int s = threadIdx.x; s < copies * HW; s += blockDim.x) hist_all[s] = 0;
+    __syncthreads();
+    int cur_graph = -1;
+    const int kA = lane, kB = lane + 32;                     // this lane's matrix entries
+    const int xA = kA / L, yA = kA % L, xB = kB / L, yB = kB % L;
+    const bool hasA = kA < LL, hasB = kB < LL;
+    const int tA = yA * L + xA, tB = yB * L + xB;            // transposed entries
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        const Tile tile = tiles[ti];
+        if (tile.graph != cur_graph) {
+            __syncthreads();
+            if (cur_graph >= 0) flush_hist_copies(hist_all, HW, copies, G, gacc, cur_graph, blockDim.x, threadIdx.x);
+            __syncthreads();
+            cur_graph = tile.graph;
+        }
+        for (int64_t e = tile.begin + wid; e < tile.end; e += nwarp) {
+            const int64_t er = e - cv.e_base;
+            const int32_t i = g.e_lo[e], j = g.e_hi[e];
+            const int p = g.ty[i], q = g.ty[j];
+            long long c = 0, di = 0, dj = 0;
+            if (lane < L) {
+                c = cv.C[e * L + lane];
+                di = typed_degree(g, i, lane);
+                dj = typed_degree(g, j, lane);
+            }
+            const long long a = di - c - (q == lane ? 1 : 0);  // |S_i^t|
+            const long long b = dj - c - (p == lane ? 1 : 0);  // |S_j^t|
+            const unsigned long long *sum = cv.tsum + er * 3 * LL;
+            const unsigned long long *km = cv.kmat + er * LL;
+            const int64_t *tau_i = cv.tau + (int64_t)i * LL, *tau_j = cv.tau + (int64_t)j * LL;
+            const int64_t *del_i = g.delta + (int64_t)i * LL, *del_j = g.delta + (int64_t)j * LL;
+            const uint32_t *A = cv.A - cv.a_base;
+            const int64_t sij = g.e_slot_lo[e], sji = g.e_slot_hi[e];
+            long long TCi[2] = {0, 0}, TCj[2] = {0, 0}, DT[2] = {0, 0}, Kd[2] = {0, 0}, Pm[2] = {0, 0};
+            long long ti_[2] = {0, 0}, tj_[2] = {0, 0}, dI[2] = {0, 0}, dJ[2] = {0, 0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool has = h ? hasB : hasA;
+                const int k = h ? kB : kA, x = h ? xB : xA, y = h ? yB : yA;
+                if (has) {
+                    TCi[h] = (long long)sum[k];
+                    TCj[h] = (long long)sum[LL + k];
+                    DT[h] = (long long)sum[2 * LL + k];
+                    Kd[h] = (long long)km[k];
+                    Pm[h] = (long long)A[(int64_t)(y * L + x) * cv.a_stride + sij] +
+                            (long long)A[(int64_t)(x * L + y) * cv.a_stride + sji];
+                    ti_[h] = tau_i[k];
+                    tj_[h] = tau_j[k];
+                    dI[h] = del_i[k];
+                    dJ[h] = del_j[k];
+                }
+            }
+            long long Ks[2];
+            Ks[0] = Kd[0] + mat_get(Kd[0], Kd[1], hasA ? tA : 0);
+            Ks[1] = Kd[1] + mat_get(Kd[0], Kd[1], hasB ? tB : 0);
+            long long CTi[2], CTj[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = h ? xB : xA, y = h ? yB : yA;
+                const long long cx = lane_get(c, x < L ? x : 0);
+                CTi[h] = TCi[h] - Ks[h] - (y == q ? cx : 0);
+                CTj[h] = TCj[h] - Ks[h] - (y == p ? cx : 0);
+            }
+            long long CTiT[2], CTjT[2];
+            CTiT[0] = mat_get(CTi[0], CTi[1], hasA ? tA : 0);
+            CTiT[1] = mat_get(CTi[0], CTi[1], hasB ? tB : 0);
+            CTjT[0] = mat_get(CTj[0], CTj[1], hasA ? tA : 0);
+            CTjT[1] = mat_get(CTj[0], CTj[1], hasB ? tB : 0);
+            long long Wi[2], Wj[2], Q[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = h ? xB : xA, y = h ? yB : yA;
+                const long long cx = lane_get(c, x < L ? x : 0), cy = lane_get(c, y < L ? y : 0);
+                Wi[h] = ti_[h] - CTi[h] - CTiT[h] - Ks[h] - (x == q ? cy : 0) - (y == q ? cx : 0);
+                Wj[h] = tj_[h] - CTj[h] - CTjT[h] - Ks[h] - (x == p ? cy : 0) - (y == p ? cx : 0);
+                Q[h] = Pm[h] - CTjT[h] - CTi[h] - Ks[h];
+            }
+            long long QT[2];
+            QT[0] = mat_get(Q[0], Q[1], hasA ? tA : 0);
+            QT[1] = mat_get(Q[0], Q[1], hasB ? tB : 0);
+            // orientation: side 0 is the endpoint with the smaller caller id
+            const bool lo_is_i = pv.old_of[i] < pv.old_of[j];
+            const int sI = lo_is_i ? 0 : 1, sJ = 1 - sI;
+            const int pl = lo_is_i ? p : q, ph = lo_is_i ? q : p;
+            const int32_t *cls = pv.cls + (int64_t)(pl * L + ph) * (S + 1);
+            uint32_t *row = per_edge_out ? per_edge_out + (e - row_base) * S : nullptr;
+            bool ok = true;
+            auto emit = [&](int slot, long long v) {
+                ok = ok && v >= 0;
+                if (row) row[slot] = sat32(v, cv.status);
+                if (v > 0) atomicAdd(&hist[cls[slot]], (unsigned long long)v);
+            };
+            if (lane == 0) atomicAdd(&hist[cls[S]], 1ull);            // the edge itself
+            if (lane < L) {
+                if (a < 0 || b < 0) set_status(cv.status, ST_INTERNAL);
+                emit(pv.off[1] + sI * L + lane, a);                  // 3-path centred at i
+                emit(pv.off[1] + sJ * L + lane, b);                  // centred at j
+                emit(pv.off[2] + lane, c);
+            }
+            // ordered blocks: entry (x, y) of each matrix on this lane
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool has = h ? hasB : hasA;
+                const int k = h ? kB : kA, x = h ? xB : xA, y = h ? yB : yA;
+                const int kt = h ? tB : tA;                          // (y, x)
+                const long long cx = lane_get(c, x < L ? x : 0);
+                const long long ax = lane_get(a, x < L ? x : 0), ay = lane_get(a, y < L ? y : 0);
+                const long long bx = lane_get(b, x < L ? x : 0), by = lane_get(b, y < L ? y : 0);
+                const long long djy = lane_get(dj, y < L ? y : 0), diy = lane_get(di, y < L ? y : 0);
+                if (!has) continue;
+                const long long Ri = dI[h] - DT[h] - (x == q ? djy : 0) - (y == p ? ax : 0) - Wi[h] - CTiT[h] - QT[h];
+                const long long Rj = dJ[h] - DT[h] - (x == p ? diy : 0) - (y == q ? bx : 0) - Wj[h] - CTjT[h] - Q[h];
+                const long long G8 = DT[h] - ((y == p ? 1 : 0) + (y == q ? 1 : 0)) * cx - Ks[h] - CTi[h] - CTj[h];
+                emit(pv.off[3] + sI * LL + k, Ri);                   // inner endpoint i: near x, far y
+                emit(pv.off[3] + sJ * LL + k, Rj);
+                emit(pv.off[4] + (lo_is_i ? k : kt), ax * by - QT[h]);   // i's neighbour x, j's y (Lemma 1)
+                emit(pv.off[6] + (lo_is_i ? k : kt), QT[h]);         // 4-cycle: i's neighbour x, j's y
+                emit(pv.off[8] + k, G8);                             // triangle node x, tail y
+                emit(pv.off[9] + sI * LL + k, cx * ay - CTi[h]);     // Lemma 3, degree-3 node i
+                emit(pv.off[9] + sJ * LL + k, cx * by - CTj[h]);
+                emit(pv.off[10] + sI * LL + k, CTi[h]);              // chordal outer edge, degree-3 node i
+                emit(pv.off[10] + sJ * LL + k, CTj[h]);
+            }
+            // unordered pairs (t <= u), one per lane
+            for (int base = 0; base < P; base += 32) {
+                const int pi = base + lane;
+                int t = 0;
+                if (pi < P)
+                    while (pair_idx(L, t, L - 1) < pi) ++t;
+                const int u = pi < P ? t + (pi - pair_idx(L, t, t)) : 0;
+                const int ktu = t * L + u;
+                const long long Witu = mat_get(Wi[0], Wi[1], ktu), Wjtu = mat_get(Wj[0], Wj[1], ktu);
+                const long long Ktu = mat_get(Ks[0], Ks[1], ktu);
+                const long long at = lane_get(a, t), au = lane_get(a, u), bt = lane_get(b, t), bu = lane_get(b, u);
+                const long long ct = lane_get(c, t), cu = lane_get(c, u);
+                if (pi >= P) continue;
+                long long star_i, star_j, tail_i, tail_j, chord, clique;
+                if (t != u) {
+                    star_i = at * au - Witu;                         // Lemma 2, centre i
+                    star_j = bt * bu - Wjtu;
+                    tail_i = Witu;
+                    tail_j = Wjtu;
+                    chord = ct * cu - Ktu;                           // Lemma 4
+                    clique = Ktu;
+                } else {
+                    ok = ok && !(Witu & 1) && !(Wjtu & 1) && !(Ktu & 1);
+                    star_i = at * (at - 1) / 2 - Witu / 2;
+                    star_j = bt * (bt - 1) / 2 - Wjtu / 2;
+                    tail_i = Witu / 2;
+                    tail_j = Wjtu / 2;
+                    chord = ct * (ct - 1) / 2 - Ktu / 2;
+                    clique = Ktu / 2;
+                }
+                emit(pv.off[5] + sI * P + pi, star_i);
+                emit(pv.off[5] + sJ * P + pi, star_j);
+                emit(pv.off[7] + sI * P + pi, tail_i);
+                emit(pv.off[7] + sJ * P + pi, tail_j);
+                emit(pv.off[11] + pi, chord);
+                emit(pv.off[12] + pi, clique);
+            }
+            if (!ok) set_status(cv.status, ST_INTERNAL);
+        }
+    }
+    __syncthreads();
+    if (cur_graph >= 0) flush_hist_copies(hist_all, HW, copies, G, gacc, cur_graph, blockDim.x, threadIdx.x);
+}
+
 // global totals: C_H = (1/|E(H)|) * sum_e x_e (Sec. 6), exact division
 __global__ void k_finalize(int ngraphs, int L, int k, const unsigned long long *__restrict__ gacc, int64_t *out,
                            uint32_t *status) {
@@ -1482,6 +1679,28 @@ static int epi4_copies(int L) {
     int c = 8;
     while (c > 1 && epi4_hist_words(L) * c * sizeof(unsigned long long) > (64u << 10)) c >>= 1;
     return c;
+}
+
+// histogram copies of k_epi4_pa: as many as fit 64 KB (at least one)
+static int epi4_pa_copies(int G) {
+    int c = 8;
+    while (c > 1 && epi4_pa_hist_words(G) * c * sizeof(unsigned long long) > (64u << 10)) c >>= 1;
+    return c;
+}
+
+void prepare_epi4_pa(Graph &G) {
+    raise_smem_limit((const void *)k_epi4_pa,
+                     epi4_pa_hist_words((int)G.pa.G) * epi4_pa_copies((int)G.pa.G) * sizeof(unsigned long long));
+}
+
+static PaView pa_view(const Graph &G) {
+    PaView v;
+    v.cls = G.pa_cls.as<int32_t>();
+    v.old_of = G.old_of.as<int32_t>();
+    v.S = G.pa.S;
+    v.G = (int32_t)G.pa.G;
+    for (int o = 0; o < 13; ++o) v.off[o] = G.pa.off[o];
+    return v;
 }
 
 void prepare_edges(Graph &G, int k, cudaStream_t s) {
@@ -1753,7 +1972,14 @@ static int64_t launch_edges4(Graph &G, int64_t b, int64_t e, const Tile *tiles, 
             G.set_stride);
         ++launches;
     }
-    if (n_tiles > 0) {
+    if (n_tiles > 0 && G.pa_active) {
+        KernelTimer kt(G, s, "k_epi4_pa");
+        const int copies = epi4_pa_copies((int)G.pa.G);
+        k_epi4_pa<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), 256,
+                    epi4_pa_hist_words((int)G.pa.G) * copies * sizeof(unsigned long long), s>>>(
+            gv, cv, pa_view(G), tiles, n_tiles, row_base, per_edge_out, gacc, copies);
+        ++launches;
+    } else if (n_tiles > 0) {
         KernelTimer kt(G, s, "k_epi4");
         const int copies = epi4_copies(G.L);
         k_epi4<<<grid_for(n_tiles, 1, sms * G.opt.ctas_per_sm), 256, epi4_smem_bytes(G.L, copies), s>>>(

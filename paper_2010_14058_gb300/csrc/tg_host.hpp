@@ -102,6 +102,16 @@ inline bool is_device_pointer(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Layout of the position-aware counts (Sec. 5): per-edge blocks O1..O12
+// and the classes of each global block (tg_pa.cu).
+struct PaLayout {
+    int32_t L = 0, S = 0;               // types, per-edge slots
+    int64_t G = 0;                      // classes per graph
+    int32_t off[13] = {0};              // first slot of blocks O1..O12 (index 1..12)
+    int64_t bsize[9] = {0};             // classes of each global block
+    int64_t boff[10] = {0};             // first class of each global block; boff[9] = G
+};
+
 struct Graph {
     int device = 0;
     cudaStream_t stream = nullptr;      // stream of the last call
@@ -151,6 +161,10 @@ struct Graph {
     std::vector<TimerRec> timer_pending;
     std::vector<cudaEvent_t> event_pool;
     std::vector<std::pair<const char *, std::pair<double, int64_t>>> timer_totals;
+    // position-aware counting (Sec. 5): slot -> class table, raw class sums
+    DBuf pa_cls, pa_gacc;
+    PaLayout pa;
+    bool pa_active = false;             // the per-edge epilogue writes position-aware rows
     // CUDA graph of the last batched count
     cudaGraphExec_t batch_exec = nullptr;
     int32_t batch_k = 0;
@@ -209,7 +223,8 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt};
+                             &set_scratch, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
+                &pa_cls, &pa_gacc};
     }
     int64_t device_bytes() const {
         int64_t s = 0;
@@ -279,6 +294,13 @@ void prepare_capture(Graph &G, int k, cudaStream_t s);
 int64_t run_count(Graph &G, int k, int64_t e_begin, int64_t e_end, uint32_t *per_edge_out,
                   unsigned long long *gacc, bool full, cudaStream_t s);
 int64_t launch_finalize(Graph &G, int k, int64_t *global_out, cudaStream_t s);
+// Position-aware typed graphlets (tg_pa.cu; epilogue in tg_count.cu).
+PaLayout pa_layout(int L);
+bool pa_labelling(int L, int block, int64_t rank, int32_t *labelling);
+std::vector<int32_t> pa_class_table(const PaLayout &Y);
+void prepare_position_aware(Graph &G, cudaStream_t s);
+void prepare_epi4_pa(Graph &G);
+int64_t launch_finalize_pa(Graph &G, int64_t *global_out, cudaStream_t s);
 // Typed-graphlet weighted graph (tg_weights.cu).
 void launch_weights(Graph &G, int k, const uint32_t *rows, int block, int64_t rank, int64_t *weights,
                     int64_t *degree, cudaStream_t s);

@@ -35,6 +35,12 @@ class tg_layout_t(ctypes.Structure):
                 ("global_block_size", ctypes.c_int64 * 9), ("graphlet_edges", ctypes.c_int32 * 9)]
 
 
+class tg_pa_layout_t(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("per_edge_slots", ctypes.c_int64), ("global_slots", ctypes.c_int64),
+                ("block_offset", ctypes.c_int64 * 13), ("global_block_offset", ctypes.c_int64 * 9),
+                ("global_block_size", ctypes.c_int64 * 9), ("graphlet_edges", ctypes.c_int32 * 9)]
+
+
 class tg_options(ctypes.Structure):
     _fields_ = [("light_edge_max_degree", ctypes.c_int32), ("light_anchor_max_wedges", ctypes.c_int32),
                 ("anchor_table_budget_mb", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
@@ -60,6 +66,10 @@ SIGNATURES = {
     "tg_count_range": ([_vp, _i32, _i64, _i64, _vp, _vp, _vp], _i32),
     "tg_finalize_global": ([_i32, _i32, _i32, _vp, _vp], _i32),
     "tg_count_batch": ([_vp, _i32, _vp, _vp, _vp], _i32),
+    "tg_pa_layout": ([_i32, ctypes.POINTER(tg_pa_layout_t)], _i32),
+    "tg_pa_labelling": ([_i32, _i32, _i64, _vp], _i32),
+    "tg_pa_slot_class": ([_i32, _i32, _i32, _i64, ctypes.POINTER(_i64)], _i32),
+    "tg_count_position_aware": ([_vp, _vp, _vp, _vp], _i32),
     "tg_query_status": ([_vp], _i32),
     "tg_count_sparse": ([_vp, _i32, _vp, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _vp], _i32),
     "tg_graphlet_weights": ([_vp, _i32, _vp, _i32, _i64, _vp, _vp, _vp], _i32),
@@ -294,6 +304,34 @@ def tg_graphlet_weights(g: Graph, k: int, per_edge_rows, block: int, rank: int, 
     (block, rank), from this handle's per-edge rows (device tensors)."""
     _check(load().tg_graphlet_weights(g.handle, k, _ptr(per_edge_rows), block, rank, _ptr(weights), _ptr(degree),
                                       _stream(stream)), "tg_graphlet_weights")
+
+
+def tg_pa_layout(L: int) -> dict:
+    """Position-aware layout (Sec. 5): per-edge blocks O1..O12 and global class blocks."""
+    lay = tg_pa_layout_t()
+    _check(load().tg_pa_layout(L, ctypes.byref(lay)), "tg_pa_layout")
+    return {"L": lay.L, "per_edge_slots": lay.per_edge_slots, "global_slots": lay.global_slots,
+            "block_offset": list(lay.block_offset), "global_block_offset": list(lay.global_block_offset),
+            "global_block_size": list(lay.global_block_size), "graphlet_edges": list(lay.graphlet_edges)}
+
+
+def tg_pa_labelling(L: int, block: int, rank: int) -> list:
+    """Smallest labelling (types of the numbered shape's nodes) of a position-aware class."""
+    out = np.zeros(4, dtype=np.int32)
+    _check(load().tg_pa_labelling(L, block, rank, out.ctypes.data), "tg_pa_labelling")
+    return out[:2 if block == 0 else (3 if block <= 2 else 4)].tolist()
+
+
+def tg_pa_slot_class(L: int, phi_lo: int, phi_hi: int, slot: int) -> int:
+    """Global slot of the position-aware class that per-edge slot `slot` counts."""
+    out = ctypes.c_int64(0)
+    _check(load().tg_pa_slot_class(L, phi_lo, phi_hi, slot, ctypes.byref(out)), "tg_pa_slot_class")
+    return int(out.value)
+
+
+def tg_count_position_aware(g: Graph, per_edge_out=None, global_out=None, stream=None) -> None:
+    _check(load().tg_count_position_aware(g.handle, _ptr(per_edge_out), _ptr(global_out), _stream(stream)),
+           "tg_count_position_aware")
 
 
 def tg_count_batch(g: Graph, k: int, per_edge_out=None, global_out=None, stream=None) -> None:

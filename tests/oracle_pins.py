@@ -340,3 +340,41 @@ def global_slot_pa(L, block, lab, classes=None):
     if block not in classes:
         classes[block] = canonical_classes(L, block)
     return sum(sizes[:block]) + classes[block][tuple(lab)]
+
+
+def merge_per_edge(L, pe_pa):
+    """Position-aware rows -> typed rows (orbit, unordered pair)."""
+    off = pa_offsets(L)
+    m = pe_pa.shape[0]
+    out = np.zeros((m, 2 * L + 10 * L * (L + 1) // 2), np.int64)
+    LL, P = L * L, L * (L + 1) // 2
+    pr = pairs(L)
+    for t in range(L):
+        out[:, per_edge_slot(L, 1, t)] = pe_pa[:, off[0] + t] + pe_pa[:, off[0] + L + t]
+        out[:, per_edge_slot(L, 2, t)] = pe_pa[:, off[1] + t]
+    for o in range(3, 13):
+        for r in range(pa_sizes(L)[o - 1]):
+            if o in (5, 7, 11, 12):                     # [side][pair] or [pair]
+                t, u = pr[r % P]
+            else:                                       # [side][x][y] or [x][y]
+                x, y = divmod(r % LL, L)
+                t, u = min(x, y), max(x, y)
+            out[:, per_edge_slot(L, o, t, u)] += pe_pa[:, off[o - 1] + r]
+    return out
+
+
+def merge_pa_global(L, gl_pa):
+    """Position-aware totals -> typed totals (each class to its type multiset)."""
+    sizes = burnside(L)
+    typed_sizes = [math.comb(L + 1, 2)] + [math.comb(L + 2, 3)] * 2 + [math.comb(L + 3, 4)] * 6
+    out = np.zeros(sum(typed_sizes), np.int64)
+    s = 0
+    for b in range(9):
+        K = 2 if b == 0 else (3 if b <= 2 else 4)
+        ms_rank = {ms: i for i, ms in enumerate(multisets(L, K))}
+        reps = sorted(set(min(tuple(lab[p[x]] for x in range(K)) for p in automorphisms(b))
+                          for lab in itertools.product(range(L), repeat=K)))
+        for r, rep in enumerate(reps):
+            out[sum(typed_sizes[:b]) + ms_rank[tuple(sorted(rep))]] += gl_pa[s + r]
+        s += sizes[b]
+    return out

@@ -93,3 +93,57 @@ def test_missing_library_fails_loudly(tmp_path):
     from paper_2010_14058_gb300 import tg
     with pytest.raises(tg.LibraryMissing):
         tg.load(str(tmp_path / "libtg.so"))
+
+
+# ------------------------------------------- position-aware host functions
+
+@pytest.mark.parametrize("L", range(1, 9))
+def test_pa_layout_matches_oracle(L, lib):
+    from paper_2010_14058_gb300 import tg
+    lay = tg.tg_pa_layout(L)
+    assert lay["per_edge_slots"] == oracle.pa_per_edge_slots(L)
+    assert lay["global_block_size"] == oracle.pa_block_sizes(L)
+    assert lay["global_slots"] == sum(oracle.pa_block_sizes(L))
+    assert lay["global_block_offset"] == list(np.concatenate([[0], np.cumsum(oracle.pa_block_sizes(L))[:-1]]))
+    from oracle_pins import pa_offsets
+    assert lay["block_offset"][1:] == list(pa_offsets(L)[:12])
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 5])
+def test_pa_labelling_is_each_class_smallest_member(L, lib):
+    """tg_pa_labelling(b, r) lies in the oracle's class r and is its
+    lexicographically smallest labelling."""
+    import itertools
+    from paper_2010_14058_gb300 import tg
+    for b in range(9):
+        K = 2 if b == 0 else (3 if b <= 2 else 4)
+        first = {}
+        for lab in itertools.product(range(L), repeat=K):
+            first.setdefault(oracle.pa_class(L, b, lab), list(lab))
+        for r in range(oracle.pa_block_sizes(L)[b]):
+            assert tg.tg_pa_labelling(L, b, r) == first[r]
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_pa_slot_class_matches_pins(L, lib):
+    """The library's slot -> class table against the test's own decoding of
+    every slot and the oracle's class of the decoded labelling."""
+    from oracle_pins import slot_instance
+    from paper_2010_14058_gb300 import tg
+    lay = tg.tg_pa_layout(L)
+    for pl in range(L):
+        for ph in range(L):
+            assert tg.tg_pa_slot_class(L, pl, ph, lay["per_edge_slots"]) == oracle.pa_class(L, 0, (pl, ph))
+            for slot in range(lay["per_edge_slots"]):
+                b, lab = slot_instance(L, slot, pl, ph)
+                want = lay["global_block_offset"][b] + oracle.pa_class(L, b, lab)
+                assert tg.tg_pa_slot_class(L, pl, ph, slot) == want, (pl, ph, slot)
+
+
+def test_pa_host_functions_reject_bad_arguments(lib):
+    from paper_2010_14058_gb300 import tg
+    for call in (lambda: tg.tg_pa_layout(0), lambda: tg.tg_pa_labelling(9, 0, 0),
+                 lambda: tg.tg_pa_labelling(3, 9, 0), lambda: tg.tg_pa_labelling(3, 3, 45),
+                 lambda: tg.tg_pa_slot_class(3, 3, 0, 0), lambda: tg.tg_pa_slot_class(3, 0, 0, 127)):
+        with pytest.raises(tg.TGError):
+            call()
