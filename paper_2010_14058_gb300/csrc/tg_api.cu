@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "tg_host.hpp"
@@ -162,10 +163,18 @@ tg_status tg_pa_slot_class(int32_t L, int32_t phi_lo, int32_t phi_hi, int64_t sl
         check_types(L);
         if (!class_out || phi_lo < 0 || phi_lo >= L || phi_hi < 0 || phi_hi >= L)
             throw Error{TG_ERR_INVALID_ARG, "types"};
-        const tg::PaLayout Y = tg::pa_layout(L);
-        if (slot < 0 || slot > Y.S) throw Error{TG_ERR_INVALID_ARG, "slot"};
-        const std::vector<int32_t> table = tg::pa_class_table(Y);
-        *class_out = table[(size_t)(phi_lo * L + phi_hi) * (Y.S + 1) + slot];
+        // one table per L, built on first use and kept (a few hundred KB at most)
+        static std::mutex mu;
+        static std::vector<int32_t> tables[TG_MAX_TYPES + 1];
+        static int32_t slots[TG_MAX_TYPES + 1];
+        std::lock_guard<std::mutex> lock(mu);
+        if (tables[L].empty()) {
+            const tg::PaLayout Y = tg::pa_layout(L);
+            tables[L] = tg::pa_class_table(Y);
+            slots[L] = Y.S;
+        }
+        if (slot < 0 || slot > slots[L]) throw Error{TG_ERR_INVALID_ARG, "slot"};
+        *class_out = tables[L][(size_t)(phi_lo * L + phi_hi) * (slots[L] + 1) + slot];
     });
 }
 
