@@ -1360,7 +1360,9 @@ __global__ void __launch_bounds__(256) k_edge3(GraphView g, CountView cv, const 
 // its tail in I) and K (adjacent pairs inside T).  k_epi4_pa writes them by
 // position -- the row layout of tg_pa.cu, sides named by caller ids (lo =
 // the smaller) -- and adds every count to the class that the slot and the
-// endpoint types fix (host table).  One warp per edge, as k_epi4.
+// endpoint types fix (host table).  One warp per edge, as k_epi4; the gather
+// and the matrices Ks, CTi, CTj, Wi, Wj, Q below repeat k_epi4's line for
+// line, and the two kernels must change together.
 struct PaView {
     const int32_t *cls;       // [L*L][S+1] class of (phi_lo, phi_hi, slot); slot S: the edge itself
     const int32_t *old_of;    // [n] caller id of each internal node
