@@ -74,3 +74,10 @@ def test_clique_units_read_the_rows(bench):
     got = bench.clique_units(pe, L, big_t=400, chunk=7)
     assert got == {"t_small": int(T[~big].sum()), "t_big": int(T[big].sum()), "k_small": int(K[~big].sum()),
                    "k_big": int(K[big].sum()), "edges_big": int(big.sum())}
+
+
+def test_count_only_split(bench):
+    got = bench.count_only(20_000_000, 908.4, 942.7)
+    assert got == {"value": round(20_000_000 / 0.9084, 1), "unit": "edges/s", "count_ms": 908.4,
+                   "build_and_free_ms": 34.3}
+    assert bench.count_only(10, 0.0, 1.0) is None
