@@ -45,7 +45,7 @@ int light_anchor_limit(int L);
 
 // Stream-ordered memory pool of the current device, owned by the library
 // (release threshold kept at its maximum, so freed blocks are reused instead
-// of returned to the driver).  Defined in tg_build.cu.
+// of returned to the CUDA driver).  Defined in tg_build.cu.
 cudaMemPool_t device_pool();
 
 // Device buffer owned by a handle; freed by release() or the destructor.
@@ -80,7 +80,7 @@ struct DBuf {
 
 // Temporary device buffer of one call, stream-ordered on `st`, from the
 // same library pool (which keeps freed blocks mapped for the life of the
-// process instead of returning them to the driver at synchronisations).
+// process instead of returning them to the CUDA driver at synchronisations).
 struct TBuf {
     void *p = nullptr;
     cudaStream_t s = nullptr;
