@@ -72,6 +72,9 @@ _SIGS = {
     "oracle_position_aware": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_position_aware_brute": ("i64 vp vp vp i32 vp", "i32"),
     "oracle_max_threads": ("", "i32"),
+    "oracle_graph_open": ("i64 vp vp vp i32 vp", "vp"),
+    "oracle_graph_close": ("vp", "i32"),
+    "oracle_graph_paper_edges": ("vp i32 vp i64 vp vp vp i32", "i32"),
 }
 _CT = {"i64": ctypes.c_int64, "i32": ctypes.c_int32, "vp": ctypes.c_void_p}
 
@@ -82,7 +85,7 @@ def open_library(path: str):
     for name, (args, res) in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = [_CT[a] for a in args.split()]
-        f.restype = _CT[res]
+        f.restype = None if name == "oracle_graph_close" else _CT[res]
     return lib
 
 
@@ -258,3 +261,38 @@ def position_aware_brute(g, lib=None):
     gl = np.zeros(int(lib.oracle_pa_global_slots(g["L"])), dtype=np.int64)
     _check(lib.oracle_position_aware_brute(g["n"], _p(rp), _p(col), _p(ty), g["L"], _p(gl)))
     return gl
+
+
+class OpenGraph:
+    """A graph opened once (validated, rows sorted) for several
+    :meth:`paper_edges` calls -- the per-edge work of Alg. 1-3 + Lemmas on
+    edge samples without re-opening the graph each time.  Used to time the
+    oracle; the counts are those of :func:`paper_edges`."""
+
+    def __init__(self, g, lib=None):
+        self.lib = lib or _load()
+        self.rp, self.col, self.ty = _args(g)            # kept alive: the handle points into them
+        self.L = g["L"]
+        self.m = int(self.rp[-1]) // 2
+        st = ctypes.c_int32(0)
+        self.h = self.lib.oracle_graph_open(g["n"], _p(self.rp), _p(self.col), _p(self.ty), self.L,
+                                            ctypes.addressof(st))
+        if not self.h:
+            raise OracleError(ERRORS.get(st.value, f"error {st.value}"))
+
+    def paper_edges(self, edge_ids, k: int = 4, nthreads: int = 0, per_edge: bool = False, times: bool = False):
+        """-> (rows int64 [len,S] or None, raw sums int64 [G], seconds per edge or None)."""
+        ids = np.ascontiguousarray(edge_ids, dtype=np.int64)
+        pe = np.zeros((len(ids), per_edge_slots(self.L, k, self.lib)), dtype=np.int64) if per_edge else None
+        sums = np.zeros(global_slots(self.L, k, self.lib), dtype=np.int64)
+        sec = np.zeros(len(ids), dtype=np.float64) if times else None
+        _check(self.lib.oracle_graph_paper_edges(self.h, k, _p(ids), len(ids), _p(pe), _p(sums), _p(sec), nthreads))
+        return pe, sums, sec
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.oracle_graph_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

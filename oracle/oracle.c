@@ -69,6 +69,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -480,8 +481,16 @@ static void table3_adapter(const graph_t *G, int64_t i, int64_t j, uint8_t *psi,
     table3_edge(G, i, j, x);
 }
 
+static double now_seconds(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* edge_seconds (optional, listed edges only): the time the thread spent on
+ * each edge, for the benchmark's sampled timing; no effect on the counts. */
 static int run_edges(const graph_t *G, int k, edge_fn fn, int64_t *per_edge, int64_t *global_out,
-                     const int64_t *edge_ids, int64_t n_ids, int nthreads) {
+                     const int64_t *edge_ids, int64_t n_ids, int nthreads, double *edge_seconds) {
     const int L = G->L;
     const int64_t Gs = oracle_global_slots(L, k), S = oracle_per_edge_slots(L, k);
     int64_t *gacc = global_out ? (int64_t *)calloc((size_t)Gs, sizeof(int64_t)) : NULL;
@@ -489,11 +498,12 @@ static int run_edges(const graph_t *G, int k, edge_fn fn, int64_t *per_edge, int
     int64_t count = edge_ids ? n_ids : G->m;
     int bad = 0, memfail = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    /* a per-call thread count that leaves the process default unchanged */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
     (void)nthreads;
 #endif
-#pragma omp parallel reduction(|:bad, memfail)
+#pragma omp parallel num_threads(nt) reduction(|:bad, memfail)
     {
         uint8_t *psi = (uint8_t *)calloc((size_t)(G->n > 0 ? G->n : 1), 1);
         int64_t *lacc = gacc ? (int64_t *)calloc((size_t)Gs, sizeof(int64_t)) : NULL;
@@ -505,8 +515,10 @@ static int run_edges(const graph_t *G, int k, edge_fn fn, int64_t *per_edge, int
 #pragma omp for schedule(dynamic, 64)
             for (int64_t q = 0; q < count; ++q) {
                 int64_t e = edge_ids ? edge_ids[q] : q;
+                double t0 = edge_seconds ? now_seconds() : 0.0;
                 fn(G, G->eu[e], G->ev[e], psi, x);
                 bad |= emit_row(G, k, x, e, per_edge ? per_edge + q * S : NULL, lacc);
+                if (edge_seconds) edge_seconds[q] = now_seconds() - t0;
             }
 #pragma omp critical
             if (gacc) for (int64_t s = 0; s < Gs; ++s) gacc[s] += lacc[s];
@@ -537,7 +549,7 @@ int oracle_paper(int64_t n, const int64_t *row_ptr, const int32_t *col, const ui
     if (k != 3 && k != 4) return ERR_ARG;
     graph_t G;
     int rc = graph_open(&G, n, row_ptr, col, types, L);
-    if (rc == OK) rc = run_edges(&G, k, paper_edge, per_edge_out, global_out, NULL, 0, nthreads);
+    if (rc == OK) rc = run_edges(&G, k, paper_edge, per_edge_out, global_out, NULL, 0, nthreads, NULL);
     graph_close(&G);
     return rc;
 }
@@ -554,17 +566,50 @@ int oracle_paper_edges(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     if (rc == OK)
         for (int64_t q = 0; q < n_ids; ++q)
             if (edge_ids[q] < 0 || edge_ids[q] >= G.m) { rc = ERR_ARG; break; }
-    if (rc == OK) rc = run_edges(&G, k, paper_edge, per_edge_out, sample_sums, edge_ids, n_ids, nthreads);
+    if (rc == OK) rc = run_edges(&G, k, paper_edge, per_edge_out, sample_sums, edge_ids, n_ids, nthreads, NULL);
     graph_close(&G);
     return rc;
 }
 
 /* Table 3 definitions on every edge (k = 4 layout). */
+/* An opened graph kept across calls: the validated, row-sorted copy that
+ * every route above builds first (graph_open), so that a caller timing the
+ * per-edge work of several edge samples opens the graph once.  The caller's
+ * row_ptr and types arrays must outlive the handle (they are not copied). */
+void *oracle_graph_open(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *types, int L,
+                        int32_t *status) {
+    graph_t *G = (graph_t *)malloc(sizeof(graph_t));
+    int rc = G ? graph_open(G, n, row_ptr, col, types, L) : ERR_MEM;
+    if (status) *status = rc;
+    if (rc != OK) {
+        if (G) { graph_close(G); free(G); }
+        return NULL;
+    }
+    return G;
+}
+
+void oracle_graph_close(void *h) {
+    if (!h) return;
+    graph_close((graph_t *)h);
+    free(h);
+}
+
+/* oracle_paper_edges on an opened graph; edge_seconds (optional) receives
+ * the time spent on each listed edge by the thread that counted it. */
+int oracle_graph_paper_edges(void *h, int k, const int64_t *edge_ids, int64_t n_ids, int64_t *per_edge_out,
+                             int64_t *sample_sums, double *edge_seconds, int nthreads) {
+    const graph_t *G = (const graph_t *)h;
+    if (!G || (k != 3 && k != 4) || n_ids < 0) return ERR_ARG;
+    for (int64_t q = 0; q < n_ids; ++q)
+        if (edge_ids[q] < 0 || edge_ids[q] >= G->m) return ERR_ARG;
+    return run_edges(G, k, paper_edge, per_edge_out, sample_sums, edge_ids, n_ids, nthreads, edge_seconds);
+}
+
 int oracle_table3(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *types, int L,
                   int64_t *per_edge_out, int64_t *global_out) {
     graph_t G;
     int rc = graph_open(&G, n, row_ptr, col, types, L);
-    if (rc == OK) rc = run_edges(&G, 4, table3_adapter, per_edge_out, global_out, NULL, 0, 1);
+    if (rc == OK) rc = run_edges(&G, 4, table3_adapter, per_edge_out, global_out, NULL, 0, 1, NULL);
     graph_close(&G);
     return rc;
 }
