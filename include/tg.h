@@ -356,6 +356,22 @@ tg_status tg_set_timing(tg_graph *g, int32_t on);
 tg_status tg_get_timing(tg_graph *g, int32_t max, const char **names, double *ms, int64_t *launches,
                         int32_t *n);
 
+/* Work counters (diagnostics for the benchmark's roofline; no effect on the
+ * counts).  While enabled, the counting kernels add the units of work they
+ * did to per-handle counters, slot TG_WORK_*: the hash-set lookups of the
+ * 4-clique scans (one per entry of N+(w) for every member w of T, Alg. 3's
+ * 4-clique branch) by the warp-per-edge and CTA-per-edge kernels, and the
+ * pair searches of edges with few pairs.  Off by default. */
+#define TG_WORK_CLIQUE_PROBES 0
+#define TG_WORK_CLIQUE_SEARCHES 1
+#define TG_WORK_CLIQUE_BIG_PROBES 2
+#define TG_WORK_SLOTS 8
+tg_status tg_set_work_counting(tg_graph *g, int32_t on);
+
+/* Synchronises the handle's stream, copies min(n, TG_WORK_SLOTS) counters
+ * to out (host, int64; zeros beyond) and clears them. */
+tg_status tg_get_work(tg_graph *g, int64_t *out, int32_t n);
+
 /* Typed 3-node counts without any allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- services whose device memory is all owned by their own pool,
@@ -365,10 +381,12 @@ tg_status tg_get_timing(tg_graph *g, int32_t max, const char **names, double *ms
  * of 2L uint32: typed 3-paths then typed triangles; global typed edge,
  * 3-path and triangle totals, G(L, 3) int64) straight from a caller CSR, no
  * tg_graph handle.  Arguments: device pointers only (TG_ERR_INVALID_ARG
- * otherwise); rows must be sorted by neighbour id; per_edge_out,
- * global_out and device_status may be NULL; device_status receives the
- * device-detected error bits OR-ed in (non-zero: invalid graph or internal
- * error), in stream order.
+ * otherwise); rows must be sorted by neighbour id and symmetric (each edge
+ * in both rows); per_edge_out, global_out and device_status may be NULL;
+ * device_status receives the device-detected error bits OR-ed in, in stream
+ * order: non-zero for an invalid graph (unsorted, one-sided or duplicate
+ * entries, self-loops, ids or types out of range -- the per-edge rows are
+ * then left unwritten) or an internal error.
  * Working memory: one file-scope device array of about 8 MB that every GPU
  * which loads the library keeps until the process exits, shared by all
  * calls; at most 1,048,576 nodes per call (TG_ERR_TOO_LARGE beyond).  The

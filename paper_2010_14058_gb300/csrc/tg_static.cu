@@ -88,6 +88,31 @@ __global__ void k_static_upper(int64_t n, int64_t nnz, const int64_t *__restrict
     if (u == 0) first[0] = 0;
 }
 
+// Symmetry: every entry v of row u needs the entry u in row v (one thread
+// per entry, binary search in row v).  Runs after k_static_upper, so a
+// graph it already rejected is skipped; indices stay clamped to [0, nnz).
+__global__ void k_static_sym(int64_t n, int64_t nnz, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             unsigned long long *status) {
+    if (*(volatile unsigned long long *)status != 0) return;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;                              // row u of entry k: rp[u] <= k < rp[u + 1]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rp[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int64_t u = lo;
+        const int32_t v = col[k];
+        if (v < 0 || v >= n) continue;                       // flagged by k_static_upper
+        const int64_t end = rp[v + 1] < nnz ? rp[v + 1] : nnz;
+        int64_t a = rp[v] > 0 ? rp[v] : 0, b = end;
+        while (a < b) {
+            const int64_t mid = (a + b) >> 1;
+            if (col[mid] < u) a = mid + 1; else b = mid;
+        }
+        if (a >= end || col[a] != u) atomicOr(status, (unsigned long long)ST_INVALID_GRAPH);
+    }
+}
+
 // Inclusive scan of first[1..n] in place (one CTA of 1024 threads).
 __global__ void __launch_bounds__(1024) k_static_scan(int64_t n, unsigned long long *first) {
     __shared__ unsigned long long part[1024];
@@ -110,8 +135,20 @@ __global__ void __launch_bounds__(1024) k_static_scan(int64_t n, unsigned long l
     }
 }
 
-// Warp per row u, one lane per upper edge (u, v): typed degrees of v and the
-// typed common neighbours of u and v by merging the two id-sorted rows.
+// per-type counts of 32 entries of a row at once: lane t < L adds how many
+// of the warp's valid entries have type t
+__device__ __forceinline__ void count_types(bool valid, int type, int L, int lane, int &acc) {
+    for (int t = 0; t < L; ++t) {
+        const unsigned b = __ballot_sync(0xffffffffu, valid && type == t);
+        if (lane == t) acc += __popc(b);
+    }
+}
+
+// Warp per upper edge e = (u, v), u < v, in edge-id order: the row u with
+// first[u] <= e < first[u + 1] by binary search; the typed degrees of u and
+// v and the typed common neighbours (every entry of the shorter row searched
+// in the longer one), all with ballots, so a hub row's edges spread over
+// many warps.
 __global__ void __launch_bounds__(256) k_static_tri3(int64_t n, int64_t m, const int64_t *__restrict__ rp,
                                                     const int32_t *__restrict__ col, const uint8_t *__restrict__ ty,
                                                     int L, const unsigned long long *__restrict__ first,
@@ -119,7 +156,13 @@ __global__ void __launch_bounds__(256) k_static_tri3(int64_t n, int64_t m, const
                                                     unsigned long long *status) {
     __shared__ unsigned long long hist[kStaticGlobal];
     __shared__ int s_bad;
-    if (threadIdx.x == 0) s_bad = *(volatile unsigned long long *)status != 0;
+    if (threadIdx.x == 0) {
+        s_bad = *(volatile unsigned long long *)status != 0;
+        if (!s_bad && first[n] != (unsigned long long)m) {   // upper entries must number the edges
+            atomicOr(status, (unsigned long long)ST_INVALID_GRAPH);
+            s_bad = 1;
+        }
+    }
     __syncthreads();
     if (s_bad) return;                                       // invalid rows: touch nothing (CTA-uniform)
     const int G = mchoose(L, 2) + 2 * mchoose(L, 3);
@@ -127,38 +170,56 @@ __global__ void __launch_bounds__(256) k_static_tri3(int64_t n, int64_t m, const
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += nw) {
+        int64_t lo = 0, hi = n;                              // first[lo] <= e < first[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (first[mid] <= (unsigned long long)e) lo = mid; else hi = mid;
+        }
+        const int64_t u = lo;
         const int64_t ub = rp[u], ue = rp[u + 1];
-        int du[TG_MAX_TYPES];
-        for (int t = 0; t < TG_MAX_TYPES; ++t) du[t] = 0;
-        for (int64_t k = ub; k < ue; ++k) du[ty[col[k]]]++;     // typed degrees of u (every lane)
-        int64_t start = ub;
-        while (start < ue && col[start] < u) ++start;
-        for (int64_t k = start + lane; k < ue; k += 32) {
-            const int32_t v = col[k];
-            const int64_t vb = rp[v], ve = rp[v + 1];
-            int dv[TG_MAX_TYPES], c[TG_MAX_TYPES];
-            for (int t = 0; t < TG_MAX_TYPES; ++t) { dv[t] = 0; c[t] = 0; }
-            int64_t a = ub, b = vb;
-            for (int64_t q = vb; q < ve; ++q) dv[ty[col[q]]]++;
-            while (a < ue && b < ve) {
-                const int32_t x = col[a], y = col[b];
-                if (x < y) ++a;
-                else if (y < x) ++b;
-                else { c[ty[x]]++; ++a; ++b; }
+        const int64_t start = ue - (int64_t)(first[u + 1] - first[u]);    // upper neighbours: a suffix
+        const int32_t v = col[start + (e - (int64_t)first[u])];
+        const int64_t vb = rp[v], ve = rp[v + 1];
+        int du = 0, dv = 0, c = 0;                           // lane t < L: type-t counts
+        for (int64_t k0 = ub; k0 < ue; k0 += 32) {
+            const bool ok = k0 + lane < ue;
+            count_types(ok, ok ? ty[col[k0 + lane]] : 0, L, lane, du);
+        }
+        for (int64_t k0 = vb; k0 < ve; k0 += 32) {
+            const bool ok = k0 + lane < ve;
+            count_types(ok, ok ? ty[col[k0 + lane]] : 0, L, lane, dv);
+        }
+        int64_t sb = ub, se = ue, lb = vb, le = ve;          // search the shorter row in the longer
+        if (se - sb > le - lb) {
+            int64_t x = sb; sb = lb; lb = x;
+            x = se; se = le; le = x;
+        }
+        for (int64_t k0 = sb; k0 < se; k0 += 32) {
+            bool hit = false;
+            int32_t x = 0;
+            if (k0 + lane < se) {
+                x = col[k0 + lane];
+                int64_t a = lb, b = le;
+                while (a < b) {
+                    const int64_t mid = (a + b) >> 1;
+                    if (col[mid] < x) a = mid + 1; else b = mid;
+                }
+                hit = a < le && col[a] == x;
             }
-            const int p = ty[u], q = ty[v];
-            const uint64_t e = first[u] + (uint64_t)(k - start);
-            if ((int64_t)e >= m) {                                // more upper entries than edges: one-sided rows
+            count_types(hit, hit ? ty[x] : 0, L, lane, c);
+        }
+        const int p = ty[u], q = ty[v];
+        if (lane < L) {
+            const int t = lane;
+            const int64_t at = (int64_t)du - c - (q == t ? 1 : 0);      // |S_u^t|, S_u excludes v
+            const int64_t bt = (int64_t)dv - c - (p == t ? 1 : 0);      // |S_v^t|
+            if (at < 0 || bt < 0) {
                 atomicOr(status, (unsigned long long)ST_INVALID_GRAPH);
-                continue;
-            }
-            for (int t = 0; t < L; ++t) {
-                const int64_t at = du[t] - c[t] - (q == t ? 1 : 0);    // |S_u^t|, S_u excludes v
-                const int64_t bt = dv[t] - c[t] - (p == t ? 1 : 0);    // |S_v^t|
+            } else {
                 if (per_edge_out) {
                     per_edge_out[e * 2 * L + t] = (uint32_t)(at + bt);
-                    per_edge_out[e * 2 * L + L + t] = (uint32_t)c[t];
+                    per_edge_out[e * 2 * L + L + t] = (uint32_t)c;
                 }
                 int ms[3] = {p, q, t};
                 for (int x0 = 0; x0 < 2; ++x0)
@@ -166,8 +227,10 @@ __global__ void __launch_bounds__(256) k_static_tri3(int64_t n, int64_t m, const
                         if (ms[x1] > ms[x1 + 1]) { int z = ms[x1]; ms[x1] = ms[x1 + 1]; ms[x1 + 1] = z; }
                 const int r = rank_sorted(L, 3, ms);
                 if (at + bt) atomicAdd(&hist[mchoose(L, 2) + r], (unsigned long long)(at + bt));
-                if (c[t]) atomicAdd(&hist[mchoose(L, 2) + mchoose(L, 3) + r], (unsigned long long)c[t]);
+                if (c) atomicAdd(&hist[mchoose(L, 2) + mchoose(L, 3) + r], (unsigned long long)c);
             }
+        }
+        if (lane == 0) {
             int m2[2] = {p < q ? p : q, p < q ? q : p};
             atomicAdd(&hist[rank_sorted(L, 2, m2)], 1ull);
         }
@@ -215,9 +278,13 @@ extern "C" tg_status tg_count3_static(int64_t n, int64_t nnz, const int64_t *row
         k_static_clear<<<1, 256, 0, s>>>(acc, kStaticGlobal + 1);
         if (n > 0) {
             k_static_upper<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nnz, row_ptr, col, node_types, L, first, st);
+            if (nnz > 0)
+                k_static_sym<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 152 * 32), 256, 0, s>>>(n, nnz, row_ptr,
+                                                                                                    col, st);
             k_static_scan<<<1, 1024, 0, s>>>(n, first);
-            k_static_tri3<<<(unsigned)std::min<int64_t>((n + 7) / 8, 152 * 16), 256, 0, s>>>(
-                n, nnz / 2, row_ptr, col, node_types, L, first, per_edge_out, acc, st);
+            if (nnz > 0)
+                k_static_tri3<<<(unsigned)std::min<int64_t>((nnz / 2 + 7) / 8, 152 * 16), 256, 0, s>>>(
+                    n, nnz / 2, row_ptr, col, node_types, L, first, per_edge_out, acc, st);
         }
         if (global_out) k_static_finalize<<<1, 256, 0, s>>>(L, acc, global_out, st);
         if (device_status) k_static_status<<<1, 32, 0, s>>>(st, device_status);

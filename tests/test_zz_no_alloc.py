@@ -6,13 +6,16 @@ device synchronisation) get typed 3-node counts from a file-scope device
 array instead of allocations.  This test calls it through the C ABI twice in
 a row -- the shared array keeps the previous call's contents, so the second
 call checks that what must start at zero is cleared -- and compares both
-results with tg_count(k = 3) exactly.  It is collected last so that a run
-stopping at the first failure has run every other test already.
+results with tg_count(k = 3) and with the CPU oracle (Alg. 1 and Cor. 1-3)
+exactly.  Rows that are not symmetric must be reported, not counted.  It is
+collected last so that a run stopping at the first failure has run every
+other test already.
 """
 import numpy as np
 import pytest
 
 import graphgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +37,7 @@ def reference_k3(g):
     return pe, gl
 
 
-def static_k3(g):
+def static_k3(g, expect_ok=True):
     rp, col, ty = tg.to_device(g)
     lay = tg.tg_layout(g["L"], 3)
     pe = torch.full((g["m"], lay["per_edge_slots"]), -1, dtype=torch.int32, device="cuda")
@@ -42,7 +45,8 @@ def static_k3(g):
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     tg.tg_count3_static(rp, col, ty, g["L"], pe, gl, st)
     torch.cuda.synchronize()
-    assert int(st.item()) == 0
+    if expect_ok:
+        assert int(st.item()) == 0
     return pe, gl
 
 
@@ -57,6 +61,53 @@ def test_static_matches_tg_count_on_two_calls(graph):
         pe, gl = static_k3(g)
         assert torch.equal(pe, pe_ref)
         assert torch.equal(gl, gl_ref)
+
+
+@pytest.mark.parametrize("graph", [
+    lambda: graphgen.chung_lu(3000, 25000, 2.1, 700.0, 8, 41, type_zipf=1.2),   # a hub row of ~700 entries
+    lambda: graphgen.erdos_renyi(1500, 9123, 3, 17),
+    lambda: graphgen.erdos_renyi(40, 0, 2, 3),                                 # no edges
+])
+def test_static_matches_oracle_on_two_calls(graph):
+    g = graph()
+    pe_o, gl_o = oracle.paper(g, k=3)
+    for _ in range(2):
+        pe, gl = static_k3(g)
+        np.testing.assert_array_equal(pe.cpu().numpy().view(np.uint32).astype(np.int64), pe_o)
+        np.testing.assert_array_equal(gl.cpu().numpy(), gl_o)
+
+
+def one_sided(n, rows, L=2):
+    rp = np.zeros(n + 1, dtype=np.int64)
+    for u, r in enumerate(rows):
+        rp[u + 1] = rp[u] + len(r)
+    col = np.array([v for r in rows for v in r], dtype=np.int32)
+    return {"n": n, "m": len(col) // 2, "L": L, "row_ptr": rp, "col": col,
+            "types": np.arange(n, dtype=np.uint8) % L}
+
+
+@pytest.mark.parametrize("rows", [
+    [[1], [], [0]],                      # 0 -> 1 and 2 -> 0: two entries, upper count 1 = m
+    [[1, 2], [0], [3], [0, 2]],          # 0 -> 2 and 3 -> 0 one-sided, upper count 3 = m
+    [[1], [2], [3], [0]],                # a directed 4-cycle
+])
+def test_static_reports_one_sided_rows(rows):
+    g = one_sided(len(rows), rows)
+    assert oracle.validate(g) != 0        # the oracle rejects them too
+    rp, col, ty = tg.to_device(g)
+    lay = tg.tg_layout(g["L"], 3)
+    pe = torch.zeros((max(g["m"], 1), lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
+    gl = torch.zeros(lay["global_slots"], dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tg.tg_count3_static(rp, col, ty, g["L"], pe, gl, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) != 0
+    # the next valid call is unaffected by the rejected one
+    ok = graphgen.erdos_renyi(60, 150, 2, 9)
+    pe_o, gl_o = oracle.paper(ok, k=3)
+    pe2, gl2 = static_k3(ok)
+    np.testing.assert_array_equal(pe2.cpu().numpy().view(np.uint32).astype(np.int64), pe_o)
+    np.testing.assert_array_equal(gl2.cpu().numpy(), gl_o)
 
 
 def test_static_rejects_too_many_nodes():
