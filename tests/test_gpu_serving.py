@@ -1,9 +1,12 @@
-"""The continuous-batching server: every request's global totals equal a
-standalone tg_count of the same graph (exact integers, tolerance 0), alone
-and in a mix where requests of several sizes and type counts are grouped,
-overlapped on several streams and admitted under a tight memory budget."""
+"""The continuous-batching server: every request's global totals equal the
+CPU oracle's (Alg. 1-3 + Lemmas, Sec. 6) and a standalone tg_count of the
+same graph (exact integers, tolerance 0), alone and in a mix where requests
+of several sizes and type counts are grouped, overlapped on several streams,
+admitted under a tight memory budget and counted on resident handles."""
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -23,6 +26,17 @@ def trace():
     return reqs
 
 
+@pytest.fixture(scope="module")
+def oracle_totals(trace):
+    """Oracle global totals of every distinct graph in the trace, by pool key."""
+    out = {}
+    for r in trace:
+        if r.key not in out:
+            g = {"n": r.n, "m": r.m, "L": r.L, "row_ptr": r.row_ptr, "col": r.col, "types": r.types}
+            out[r.key] = oracle.paper(g, k=4, per_edge=False)[1]
+    return out
+
+
 def standalone(r):
     h = tg.tg_build(torch.from_numpy(r.row_ptr).cuda(), torch.from_numpy(r.col).cuda(),
                     torch.from_numpy(r.types).cuda(), r.L)
@@ -33,7 +47,7 @@ def standalone(r):
     return gl.cpu().numpy()
 
 
-def test_mixed_equals_alone(trace):
+def test_mixed_equals_alone(trace, oracle_totals):
     budget = 3 * max(r.bytes_needed() for r in trace)       # forces waits for memory
     mixed = serve.Server(budget_bytes=budget, workers=4, small_edges=20_000, batch_edges=200_000).run(trace)
     alone = serve.Server(budget_bytes=budget, workers=1, batching=False).run(trace, realtime=False)
@@ -44,6 +58,8 @@ def test_mixed_equals_alone(trace):
         np.testing.assert_array_equal(a.totals, b.totals)
     for r in trace[:12]:
         np.testing.assert_array_equal(mixed[r.rid].totals, standalone(r))
+    for a, r in zip(mixed, trace):                           # every served result is the oracle's
+        np.testing.assert_array_equal(a.totals, oracle_totals[r.key])
 
 
 def test_summary(trace):
@@ -52,7 +68,7 @@ def test_summary(trace):
     assert s["requests"] == len(trace) and s["p99_ms"] >= s["p50_ms"] > 0
 
 
-def test_resident_handles(trace):
+def test_resident_handles(trace, oracle_totals):
     # graphs above 5,000 edges stay on the device after their first request;
     # repeats are counted on those handles, with the same totals
     srv = serve.Server(budget_bytes=4 << 30, workers=3, small_edges=5_000, batch_edges=200_000,
@@ -61,6 +77,7 @@ def test_resident_handles(trace):
     alone = serve.Server(workers=1, batching=False).run(trace, realtime=False)
     srv.close()
     assert sum(r.resident for r in res) > 0
-    for a, b in zip(res, alone):
+    for a, b, r in zip(res, alone, trace):
         assert a.status == 0
         np.testing.assert_array_equal(a.totals, b.totals)
+        np.testing.assert_array_equal(a.totals, oracle_totals[r.key])
