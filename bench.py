@@ -14,9 +14,10 @@ needed between steps.
 
 e2e: the same metric through the public API with host buffers (pinned CSR
 in, per-edge rows and totals out), copies inside the timed region.
-cpu_baseline: the CPU oracle (Alg. 1-3 + Lemmas) on a seeded uniform edge
-sample, on the host cores.  --impl reference times that oracle as the
-reference arm.
+cpu_baseline: the CPU oracle (Alg. 1-3 + Lemmas) on the host cores, its
+full-graph time extrapolated from a seeded stratified edge sample (every
+sampled edge timed), on all cores and on one thread.  --impl reference
+times that oracle, with the same estimator, as the reference arm.
 
 Multi-GPU (torchrun): every rank counts its own copy of the workload (edges
 are independent problems; weak scaling), no collective on the data path.
@@ -55,7 +56,6 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cl_large", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "serve"],
@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=200_000 / 60, help="serving: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=1.0, help="serving: seconds of arrivals")
     ap.add_argument("--pool", type=int, default=128, help="serving: distinct request graphs")
+    ap.add_argument("--oracle-fraction", type=float, default=0.02,
+                    help="batched / serve: fraction of graphs (requests) whose totals the CPU oracle checks")
+    ap.add_argument("--oracle-seconds", type=float, default=240.0,
+                    help="batched / serve: oracle time budget of that check (0: no limit)")
     ap.add_argument("--position-aware", action="store_true",
                     help="plain mode: also time the position-aware count (Sec. 5) of the same graph")
     return ap.parse_args()
@@ -134,8 +138,60 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) per launch of a kernel, from the ncu capture
-# summarised under profiles/ for that workload; removed when the kernel changes.
-TRAFFIC = {("cl_large", "k_clique_big"): 3_713_920_000}
+# summarised under profiles/ for that workload and the current kernel code
+# (an entry is removed when its kernel changes).
+TRAFFIC = {}
+
+# Issue-limited peak of the 4-clique lookups: 152 SMs x 4 schedulers x 32
+# lanes x the maximum SM clock give the lane-instruction rate; one lookup
+# (load the N+ entry, hash, one 16-byte shared-memory bucket load, four
+# compares, the typed hit count) takes at least LOOKUP_INSTR of them.
+LOOKUP_INSTR = 15
+
+
+def alu_peak_lookups(sm_mhz: float, sms: int = 152) -> float:
+    return sms * 4 * 32 * sm_mhz * 1e6 / LOOKUP_INSTR
+
+
+def w_alg_bytes(g: dict, tsize, S: int) -> dict:
+    """The algorithmic traffic model W_alg = sum_e [4(d_i + d_j) +
+    sum_{w in U_e} 4 min(d_w, |U_e| ceil(log2 d_w))] + 4 S m: per edge both
+    rows, then for every node of U_e = (Gamma_i u Gamma_j) minus {i, j} the cheaper
+    of scanning its row or searching U_e's members in it, plus the rows
+    written.  |U_e| = d_i + d_j - 2 - |T_e| (|T_e| from the counts); the sum
+    over U_e is taken over Gamma_i minus {j} and Gamma_j minus {i}, so the
+    nodes of T_e count twice: an upper bound."""
+    rp, col, n = g["row_ptr"], g["col"].astype(np.int64), g["n"]
+    deg = np.diff(rp).astype(np.int64)
+    lg = np.zeros(n, np.int64)
+    lg[deg > 1] = np.ceil(np.log2(deg[deg > 1])).astype(np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    dw, lw = deg[col], lg[col]
+    # threshold of each entry: min(d_w, U lg_w) = d_w exactly when U >= d_w / lg_w
+    r = np.where(lw > 0, dw / np.maximum(lw, 1), np.inf)
+    order = np.lexsort((r, rows))
+    r_s, d_s, l_s = r[order], dw[order].astype(np.float64), lw[order].astype(np.float64)
+    cd = np.concatenate([[0.0], np.cumsum(d_s)])
+    cl = np.concatenate([[0.0], np.cumsum(l_s)])
+    up = col > rows
+    src, dst = rows[up], col[up]
+    o2 = np.lexsort((dst, src))
+    src, dst = src[o2], dst[o2]
+    U = (deg[src] + deg[dst] - 2 - np.asarray(tsize, dtype=np.int64)).astype(np.float64)
+    key = np.where(np.isinf(r_s), 4e15, rows[order] * 1e9 + np.minimum(r_s, 5e8))
+
+    def side(x, other):
+        lo = rp[x].astype(np.int64)
+        hi = rp[x + 1].astype(np.int64)
+        k = np.searchsorted(key, x * 1e9 + U, side="right")
+        k = np.clip(k, lo, hi)
+        tot = (cd[k] - cd[lo]) + U * (cl[hi] - cl[k])
+        # drop the other endpoint, which is in Gamma_x but not in U_e
+        dd, ll = deg[other].astype(np.float64), lg[other].astype(np.float64)
+        return tot - np.minimum(dd, U * ll)
+
+    s = 4.0 * (deg[src] + deg[dst]).sum() + 4.0 * (side(src, dst).sum() + side(dst, src).sum())
+    return {"bytes": float(s + 4.0 * S * len(src)), "model": "upper bound (nodes of T counted from both sides)"}
 
 
 def kernel_units(g: dict, light_anchor_max: int = 64, hub_min: int = 1 << 16) -> dict:
@@ -318,8 +374,15 @@ def run_ours(args):
     # roofline: algorithmic bytes of each count kernel per step over its
     # CUDA-event time per step (k_clique and k_clique_big share one bound)
     peak, peak_kind = load_peaks()
-    roofline, per_kernel, compulsory, count_alone = None, {}, None, None
+    roofline, per_kernel, compulsory, count_alone, walg, work = None, {}, None, None, None, None
     if rank == 0:
+        # the 4-clique lookups of one count, from the library's work counters
+        # (one extra, untimed count)
+        h = tg.tg_build(rp, col, ty, L, stream=stream)
+        tg.tg_set_work_counting(h, True)
+        tg.tg_count(h, 4, pe, gl, stream=stream)
+        work = tg.tg_get_work(h)
+        h.free()
         gl_host = gl.cpu().numpy()
         b2 = lay["global_block_offset"][2]
         t_nodes = 3 * int(gl_host[b2:b2 + lay["global_block_size"][2]].sum())   # sum_e |T_e|
@@ -335,18 +398,45 @@ def run_ours(args):
                                 "algorithmic_gb": round(abytes[name] / 1e9, 3), "achieved_gbs": round(gbs, 2),
                                 "frac": round(gbs / peak, 5)}
         top = max(kernel_ms.items(), key=lambda kv: kv[1][0])[0]
-        if top in per_kernel:
+        sm_mhz = float(clk.get("sm_mhz") or 2070.0)
+        lookups = {"k_clique": work["clique_probes"] + work["clique_searches"],
+                   "k_clique_big": work["clique_big_probes"]}
+        for name, ops in lookups.items():
+            if name in kernel_ms and kernel_ms[name][0] > 0:
+                ms_k = kernel_ms[name][0] / args.steps
+                per_kernel.setdefault(name, {})["lookups"] = ops
+                per_kernel[name]["glookups_per_s"] = round(ops / (ms_k / 1e3) / 1e9, 2)
+                per_kernel[name]["alu_frac"] = round(ops / (ms_k / 1e3) / alu_peak_lookups(sm_mhz), 5)
+        if top in lookups:
+            ms_k = kernel_ms[top][0] / args.steps
+            ach = lookups[top] / (ms_k / 1e3) / 1e9
+            pk_alu = alu_peak_lookups(sm_mhz) / 1e9
+            roofline = {"kernel": top, "bound": "alu", "achieved": round(ach, 2), "peak": round(pk_alu, 1),
+                        "peak_kind": f"derived: 152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock under "
+                                     f"load) / {LOOKUP_INSTR} lane instructions per lookup",
+                        "unit": "Glookups/s", "frac": round(ach / pk_alu, 5), "algorithmic_ops": lookups[top],
+                        "ops": "hash-set lookups of the 4-clique scan, sum over edges of sum_{w in T} |N+(w)|",
+                        "ms_per_step": round(ms_k, 3), "traffic": TRAFFIC.get((args.workload, top))}
+        elif top in per_kernel and "achieved_gbs" in per_kernel[top]:
             pk = per_kernel[top]
             roofline = {"kernel": top, "bound": "hbm", "achieved": pk["achieved_gbs"], "peak": peak,
                         "peak_kind": peak_kind, "unit": "GB/s", "frac": pk["frac"],
                         "algorithmic_bytes": abytes[top], "ms_per_step": pk["ms_per_step"],
                         "traffic": TRAFFIC.get((args.workload, top))}
-        # compulsory traffic of the whole count: CSR and types read once, outputs written once
+        # compulsory traffic of the whole count: CSR and types read once,
+        # outputs written once -- the headline "% of HBM roofline"
         cb = 8.0 * m + 8.0 * g["n"] + g["n"] + 4.0 * S * m + 8.0 * G
         count_ms = sum(v[0] for v in kernel_ms.values()) / args.steps
-        compulsory = {"bytes": cb, "count_ms": round(count_ms, 3),
+        compulsory = {"bound": "hbm", "bytes": cb, "count_ms": round(count_ms, 3), "peak": peak,
+                      "peak_kind": peak_kind, "unit": "GB/s",
+                      "achieved": round(cb / (count_ms / 1e3) / 1e9, 2),
                       "frac": round(cb / (count_ms / 1e3) / 1e9 / peak, 6)}
         count_alone = count_only(m, count_ms, ms_max / args.steps)
+        tsize = pe[:, L:2 * L].sum(dim=1, dtype=torch.int64).cpu().numpy()
+        walg = w_alg_bytes(g, tsize, S)
+        walg["per_s_gb"] = round(walg["bytes"] / (count_ms / 1e3) / 1e9, 2)
+        walg["frac_of_hbm_peak"] = round(walg["per_s_gb"] / peak, 4)
+        walg["note"] = "effective algorithmic bandwidth W_alg / T_count; may exceed HBM (L2 and shared-memory reuse)"
     kernel_share = {k: round(v[0] / sum(x[0] for x in kernel_ms.values()), 4) for k, v in kernel_ms.items()}
 
     # end to end through host buffers
@@ -444,7 +534,7 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_baseline(g, args.cpu_seconds)
+        cpu = cpu_baseline(g)
 
     if rank == 0:
         line = {
@@ -455,8 +545,9 @@ def run_ours(args):
                        "edges": m, "types": L, "k": 4, "per_edge_slots": S, "global_slots": G,
                        "l2": "inputs and outputs larger than L2 (no flush)",
                        "step": "tg_build + tg_count(k=4) + tg_free, device-resident inputs and outputs"},
-            "status": tg.STATUS[status], "roofline": roofline, "kernel_roofline": per_kernel,
-            "compulsory_roofline": compulsory, "count_only": count_alone, "kernel_share": kernel_share,
+            "status": tg.STATUS[status], "roofline": roofline, "hbm_roofline": compulsory,
+            "kernel_roofline": per_kernel, "w_alg": walg, "work": work,
+            "count_only": count_alone, "kernel_share": kernel_share,
             "units": units,
             "cpu_baseline": cpu, "e2e": e2e, "e2e_sparse": e2e_sparse, "clocks": clk,
             "gpu_launches": int(launches[0]),
@@ -469,30 +560,126 @@ def run_ours(args):
 
 
 # --------------------------------------------------------- CPU oracle arm
+#
+# The oracle cannot count the benchmark graph in full within a benchmark run
+# (about 16 days on one core), so both arms estimate its full-graph time
+# from a seeded stratified sample of edges:
+#   * work proxy of edge (u, v): d_u + d_v + s_u + s_v, s_x = sum of the
+#     degrees of x's neighbours -- the oracle marks both neighbourhoods and
+#     scans every neighbour's row (Alg. 1-3), so its time per edge follows
+#     this proxy closely;
+#   * a certainty stratum of the `heaviest` edges by proxy, timed in full;
+#     the other edges in strata by floor(log2(proxy)), each sampled without
+#     replacement, n_h proportional to the stratum's share of the proxy
+#     total (at least 3);
+#   * every sampled edge timed by the thread that counts it; the full-graph
+#     time T = T_open + sum_h (N_h / n_h) * (sum of the stratum's sampled
+#     times) / C, C = threads (a Horvitz-Thompson estimate; with C threads
+#     the per-edge times are taken under C-thread load, and the full graph's
+#     20M edges balance across the threads, so no idle time is added);
+#   * T_open = the one-off graph preparation (copy, row sort, validation).
+# The single-thread figure uses a subsample (every `thin`-th edge of each
+# stratum sample) to stay within the time budget.
 
-def cpu_baseline(g: dict, seconds: float) -> dict:
-    """The CPU oracle (Alg. 1-3 + Lemmas, OpenMP over edges) on a seeded
-    uniform sample of edge ids, sized to take about `seconds`."""
-    import oracle
-    rng = np.random.default_rng(20201029)
-    m = g["m"]
-    n_try = min(m, 2000)
-    ids = np.sort(rng.choice(m, size=n_try, replace=False))
+CPU_SEED = 20201029
+
+
+def edge_cost_proxy(g: dict):
+    """(src, dst, proxy) of every edge in edge-id order (u < v, lexicographic)."""
+    rp, col, n = g["row_ptr"], g["col"].astype(np.int64), g["n"]
+    deg = np.diff(rp)
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    s = np.bincount(rows, weights=deg[col], minlength=n)
+    up = col > rows
+    src, dst = rows[up], col[up]
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    return src, dst, (deg[src] + deg[dst]).astype(np.float64) + s[src] + s[dst]
+
+
+def oracle_design(proxy, budget_edges: int = 1000, heaviest: int = 100, seed: int = CPU_SEED) -> list:
+    """Strata of the estimator: [(name, N_h, sampled edge ids)], seeded."""
+    rng = np.random.default_rng(seed)
+    m = len(proxy)
+    order = np.argsort(-proxy, kind="stable")
+    top = np.sort(order[:min(heaviest, m)])
+    strata = [("heaviest", len(top), top)] if len(top) else []
+    rest = np.sort(order[len(top):])
+    if len(rest) == 0:
+        return strata
+    bins = np.floor(np.log2(np.maximum(proxy[rest], 1.0))).astype(np.int64)
+    total = proxy[rest].sum()
+    for b in np.unique(bins):
+        members = rest[bins == b]
+        share = proxy[members].sum() / total if total > 0 else len(members) / len(rest)
+        n_h = int(min(len(members), max(3, round(budget_edges * share))))
+        pick = np.sort(rng.choice(members, size=n_h, replace=False))
+        strata.append((f"log2 proxy {int(b)}", len(members), pick))
+    return strata
+
+
+def oracle_estimate(og, strata, nthreads: int, thin: int = 1, seed: int = CPU_SEED) -> dict:
+    """Full-graph oracle time from the sampled edge times (see above)."""
+    rng = np.random.default_rng(seed + nthreads)
+    ids, w, h_of = [], [], []
+    for h, (_, N_h, pick) in enumerate(strata):
+        sub = pick[::thin] if thin > 1 else pick
+        if thin > 1 and len(sub) < 2:
+            sub = pick[:2]
+        ids.append(sub)
+        w.append(np.full(len(sub), N_h / len(sub)))
+        h_of.append(np.full(len(sub), h))
+    ids, w, h_of = np.concatenate(ids), np.concatenate(w), np.concatenate(h_of)
+    perm = rng.permutation(len(ids))                  # mix heavy and light edges across the threads
+    ids, w, h_of = ids[perm], w[perm], h_of[perm]
     t = time.perf_counter()
-    oracle.paper_edges(g, ids)
-    el = time.perf_counter() - t
-    if el < seconds and n_try < m:
-        n2 = int(min(m, n_try * max(1.0, 0.9 * seconds / max(el, 1e-3))))
-        ids = np.sort(rng.choice(m, size=n2, replace=False))
-        t = time.perf_counter()
-        oracle.paper_edges(g, ids)
-        el = time.perf_counter() - t
-    return {"value": round(len(ids) / el, 1), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{len(ids)} edge ids drawn uniformly (seed 20201029) from the {m} edges; "
-                      f"all 3- and 4-node orbits of each; {el:.1f} s"}
+    _, _, sec = og.paper_edges(ids, k=4, nthreads=nthreads, times=True)
+    wall = time.perf_counter() - t
+    work = float((w * sec).sum())                     # estimated thread-seconds over all edges
+    var = 0.0                                         # stratified variance of that estimate
+    for h, (_, N_h, _) in enumerate(strata):
+        x = sec[h_of == h]
+        if len(x) > 1 and len(x) < N_h:
+            var += N_h * N_h * (1 - len(x) / N_h) * x.var(ddof=1) / len(x)
+    return {"edges_timed": int(len(ids)), "sample_wall_s": wall, "work_thread_s": work,
+            "work_rel_se": float(np.sqrt(var) / work) if work > 0 else 0.0}
+
+
+def cpu_baseline(g: dict, budget_edges: int = 1000, heaviest: int = 100, thin: int = 10) -> dict:
+    """The CPU oracle (Alg. 1-3 + Lemmas, OpenMP over edges, Sec. 4.7)
+    timed on the host cores by the stratified estimator: full-graph edges/s
+    on all cores (value) and on one thread."""
+    import oracle
+    m = g["m"]
+    _, _, proxy = edge_cost_proxy(g)
+    strata = oracle_design(proxy, budget_edges, heaviest)
+    t = time.perf_counter()
+    og = oracle.OpenGraph(g)
+    t_open = time.perf_counter() - t
+    cores = oracle.max_threads()
+    og.paper_edges(strata[0][2][:min(8, len(strata[0][2]))], nthreads=cores)     # page in the graph
+    allc = oracle_estimate(og, strata, cores)
+    one = oracle_estimate(og, strata, 1, thin=thin)
+    og.close()
+    t_all = t_open + allc["work_thread_s"] / cores
+    t_one = t_open + one["work_thread_s"]
+    n_sample = sum(len(x[2]) for x in strata)
+    return {"value": round(m / t_all, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1thread": round(m / t_one, 2), "full_graph_s_estimate": round(t_all, 1),
+            "full_graph_s_estimate_1thread": round(t_one, 1), "rel_se": round(allc["work_rel_se"], 4),
+            "rel_se_1thread": round(one["work_rel_se"], 4), "open_s": round(t_open, 2),
+            "sample": f"labelled extrapolation to all {m} edges: the {heaviest} heaviest edges by work proxy "
+                      f"(d_u+d_v+sum of neighbour degrees) in full plus a seeded sample (seed {CPU_SEED}) of "
+                      f"{n_sample - len(strata[0][2])} edges over {len(strata) - 1} log2-proxy strata, "
+                      f"n_h proportional to stratum work; every edge timed; Horvitz-Thompson sum + graph "
+                      f"preparation; all cores timed {allc['edges_timed']} edges in {allc['sample_wall_s']:.1f} s, "
+                      f"one thread every {thin}th ({one['edges_timed']} edges) in {one['sample_wall_s']:.1f} s"}
 
 
 def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores.  Each step times the
+    all-cores stratified sample of cpu_baseline and extrapolates the full
+    graph's time; value = edges / the mean extrapolated time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -500,34 +687,73 @@ def run_reference(args):
     import oracle
     g = graphgen.workload(args.workload)
     m = g["m"]
-    rng = np.random.default_rng(7)
-    # size each step's sample so that warmup + steps end within a few minutes
-    ids = np.sort(rng.choice(m, size=min(m, 500), replace=False))
+    _, _, proxy = edge_cost_proxy(g)
+    strata = oracle_design(proxy)
     t = time.perf_counter()
-    oracle.paper_edges(g, ids)
-    el = time.perf_counter() - t
-    per_step = int(min(m, max(500, 500 * 8.0 / max(el, 1e-3))))
-    for _ in range(args.warmup):
-        oracle.paper_edges(g, np.sort(rng.choice(m, size=per_step, replace=False)))
-    total, el = 0, 0.0
-    for _ in range(args.steps):
-        ids = np.sort(rng.choice(m, size=per_step, replace=False))
-        t = time.perf_counter()
-        oracle.paper_edges(g, ids)
-        el += time.perf_counter() - t
-        total += len(ids)
-    value = total / el
+    og = oracle.OpenGraph(g)
+    t_open = time.perf_counter() - t
     cores = oracle.max_threads()
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+    for _ in range(args.warmup):
+        oracle_estimate(og, strata, cores)
+    ests, walls, ses = [], [], []
+    for _ in range(args.steps):
+        r = oracle_estimate(og, strata, cores)
+        ests.append(t_open + r["work_thread_s"] / cores)
+        walls.append(r["sample_wall_s"])
+        ses.append(r["work_rel_se"])
+    one = oracle_estimate(og, strata, 1, thin=10)
+    og.close()
+    t_full = float(np.mean(ests))
+    value = m / t_full
+    n_sample = sum(len(x[2]) for x in strata)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(walls)), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "edges": m,
-                       "types": g["L"], "k": 4},
-            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} uniform edge ids per step from {m}; CPU oracle (Alg. 1-3 + "
-                                       f"Lemmas), OpenMP over edges"},
-            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                       "types": g["L"], "k": 4,
+                       "step": "the oracle (Alg. 1-3 + Lemmas, OpenMP over edges) on the stratified edge sample; "
+                               "value = edges / extrapolated full-graph time"},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "value_1thread": round(m / (t_open + one["work_thread_s"]), 2),
+                             "full_graph_s_estimate": round(t_full, 1),
+                             "step_estimates_spread": round((max(ests) - min(ests)) / t_full, 4),
+                             "rel_se": round(float(np.mean(ses)), 4), "open_s": round(t_open, 2),
+                             "sample": f"per step: the 100 heaviest edges plus {n_sample - len(strata[0][2])} "
+                                       f"seeded edges over {len(strata) - 1} log2-proxy strata (seed {CPU_SEED}), "
+                                       f"every edge timed, extrapolated to all {m} edges (same estimator as "
+                                       f"the GPU arm's cpu_baseline)"},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(graph_of, gpu_totals_of, ids, sizes, seconds: float) -> dict:
+    """The CPU-baseline leg of the batched and served forms: the oracle
+    (Alg. 1-3 + Lemmas, OpenMP over edges, Sec. 4.7) timed on a seeded
+    sample of the graphs (requests), taken smallest first until `seconds`
+    of oracle time are spent (0: the whole sample).  The same pass checks
+    that each sampled graph's GPU totals equal the oracle's (Sec. 6)."""
+    import oracle
+    order = sorted(range(len(ids)), key=lambda k: (sizes[k], ids[k]))
+    checked, mismatched, edges, spent, largest = 0, [], 0, 0.0, 0
+    for k in order:
+        if seconds and spent >= seconds:
+            break
+        x = ids[k]
+        g = graph_of(x)
+        t = time.perf_counter()
+        _, gl = oracle.paper(g, k=4, per_edge=False)
+        spent += time.perf_counter() - t
+        checked += 1
+        edges += g["m"]
+        largest = max(largest, g["m"])
+        if not np.array_equal(gl, gpu_totals_of(x)):
+            mismatched.append(int(x))
+    return {"value": round(edges / spent, 1) if spent > 0 else None, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{checked} of {len(ids)} seeded sampled graphs ("
+                      + ("smallest first within the time budget" if seconds else "all") + f"), {edges} edges, "
+                      f"largest {largest} edges, {spent:.1f} s; whole graphs, all 3- and 4-node orbits",
+            "totals_identical_to_oracle": not mismatched, "mismatched": mismatched[:20]}
 
 
 # ------------------------------------------------------------ batched form
@@ -621,6 +847,22 @@ def run_batched(args):
             if x % 512 == 511:
                 log(f"plain: {x + 1} graphs, build {build_plain_s:.1f} s, count {plain_ms:.0f} ms")
     identical = bool(torch.equal(gl_b, gl_p))
+    # CPU baseline: the oracle on a seeded 2% sample of the graphs, which
+    # also checks their totals
+    rng = np.random.default_rng(CPU_SEED + 4)
+    k_s = max(1, int(np.ceil(args.oracle_fraction * ng)))
+    sample = np.sort(rng.choice(ng, size=min(k_s, ng), replace=False))
+    gl_b_h = gl_b.cpu().numpy()
+
+    def graph_of(x):
+        a, b = int(node_off[x]), int(node_off[x + 1])
+        s0, s1 = int(rp_h[a]), int(rp_h[b])
+        return {"n": b - a, "m": (s1 - s0) // 2, "L": L, "row_ptr": rp_h[a:b + 1] - s0,
+                "col": u["col"][s0:s1] - a, "types": u["types"][a:b]}
+
+    cpu = cpu_baseline_sample(graph_of, lambda x: gl_b_h[x], sample.tolist(),
+                              [int(u["graph_m"][x]) for x in sample], args.oracle_seconds)
+    log(f"oracle sample: {cpu}")
     line = {"metric": METRIC + ", batched form", "value": round(m / (batch_ms / 1e3), 1), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(batch_ms, 3), "higher_is_better": True,
             "dtype": "int64", "data": "synthetic",
@@ -636,7 +878,7 @@ def run_batched(args):
                                 "build_s": round(build_plain_s, 3), "status": tg.STATUS[status_p]},
             "speedup_count": round(plain_ms / batch_ms, 2),
             "speedup_build_plus_count": round((build_plain_s + plain_ms / 1e3) / (build_batch_s + batch_ms / 1e3), 2),
-            "totals_identical": identical}
+            "totals_identical": identical, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -666,6 +908,19 @@ def run_serve(args):
     srv.close()
     plain = serve.Server(budget_bytes=40 << 30, workers=1, batching=False).run(trace)
     same = all(np.array_equal(a.totals, b.totals) and a.status == 0 and b.status == 0 for a, b in zip(served, plain))
+    # CPU baseline: the oracle on a seeded 2% sample of the requests, which
+    # also checks their totals
+    rng = np.random.default_rng(CPU_SEED + 5)
+    k_s = max(1, int(np.ceil(args.oracle_fraction * len(trace))))
+    sample = np.sort(rng.choice(len(trace), size=min(k_s, len(trace)), replace=False)).tolist()
+    by_rid = {r.rid: r for r in served}
+
+    def request_graph(x):
+        r = trace[x]
+        return {"n": r.n, "m": r.m, "L": r.L, "row_ptr": r.row_ptr, "col": r.col, "types": r.types}
+
+    cpu = cpu_baseline_sample(request_graph, lambda x: by_rid[trace[x].rid].totals, sample,
+                              [trace[x].m for x in sample], args.oracle_seconds)
     s1, s0 = serve.summarize(served, trace), serve.summarize(plain, trace)
     line = {"metric": METRIC + ", serving form", "value": s1["edges_per_s"], "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "int64", "data": "synthetic",
@@ -673,7 +928,7 @@ def run_serve(args):
                        "requests": len(trace), "edges": s1["edges"], "pool_graphs": args.pool,
                        "request_mix": "Chung-Lu gamma=2.2, m log-uniform [100, 1e6], n=m/5, L uniform 3..8",
                        "budget_gb": 40, "resident_gb": 16, "workers": 4, "pool_generation_s": round(gen_s, 1)},
-            "served": s1, "plain_sequential": s0, "results_identical": bool(same)}
+            "served": s1, "plain_sequential": s0, "results_identical": bool(same), "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 

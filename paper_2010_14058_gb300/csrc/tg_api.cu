@@ -428,6 +428,32 @@ tg_status tg_set_timing(tg_graph *gh, int32_t on) {
     });
 }
 
+tg_status tg_set_work_counting(tg_graph *gh, int32_t on) {
+    return guarded([&] {
+        if (!gh) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        Graph &G = gh->g;
+        if (on && !G.work.p) {
+            G.work.alloc(sizeof(unsigned long long) * tg::kWorkSlots);
+            TG_CK(cudaMemsetAsync(G.work.p, 0, sizeof(unsigned long long) * tg::kWorkSlots, G.stream));
+        }
+        G.work_on = on != 0;
+    });
+}
+
+tg_status tg_get_work(tg_graph *gh, int64_t *out, int32_t n) {
+    return guarded([&] {
+        if (!gh || !out || n < 0) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        Graph &G = gh->g;
+        unsigned long long h[tg::kWorkSlots] = {0};
+        if (G.work.p) {
+            TG_CK(cudaMemcpyAsync(h, G.work.p, sizeof(h), cudaMemcpyDeviceToHost, G.stream));
+            TG_CK(cudaStreamSynchronize(G.stream));
+            TG_CK(cudaMemsetAsync(G.work.p, 0, sizeof(h), G.stream));
+        }
+        for (int32_t k = 0; k < n; ++k) out[k] = k < tg::kWorkSlots ? (int64_t)h[k] : 0;
+    });
+}
+
 tg_status tg_get_timing(tg_graph *gh, int32_t max, const char **names, double *ms, int64_t *launches, int32_t *n) {
     return guarded([&] {
         if (!gh || !n || max < 0) throw Error{TG_ERR_INVALID_ARG, "NULL"};

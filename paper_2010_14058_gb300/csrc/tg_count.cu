@@ -874,158 +874,158 @@ __device__ __forceinline__ int type_of_index(const int32_t *ts, int L, int32_t k
     return t;
 }
 
-// 4-clique pairs of one edge by a group of `gsize` threads (whole warps):
-// adjacent pairs (w, x) of T, each counted once as (smaller id, larger id),
-// into sK[type of smaller][type of larger].  Either every pair is checked by
-// a binary search in the smaller id's typed row, or every w scans its
-// higher-priority neighbours N+(w) and looks them up in T -- whichever
-// touches fewer entries.
-__device__ __forceinline__ uint32_t t_hash(int32_t x, int lgcap) {
-    return ((uint32_t)x * 2654435761u) >> (32 - lgcap);
+// ------------------------------------------------------------- 4-cliques
+// K[t][t'] of an edge counts the adjacent pairs (w, x) inside T, w of type
+// t and x of type t', each pair once, from its lower-priority node w: x is
+// then one of w's higher-priority neighbours N+(w) (a contiguous list of
+// (type << 29 | id) entries grouped by type, built once per graph).  So
+// every member w of T scans N+(w) and looks each entry up in a hash set of
+// T: sum_{w in T} |N+(w)| lookups, most of them hits.
+//
+// The set: buckets of 4 slots (one 16-byte load per lookup), slots taken
+// in order by atomicCAS, -1 when empty, so a bucket whose last slot is
+// empty is not full and a lookup stops there; with at least 4 slots per
+// member almost every lookup reads one bucket.
+// The scan: one whole warp per member, lanes striding over N+(w) (coalesced
+// loads, 4 in flight per lane) -- the lists behind almost all lookups are
+// tens to thousands of entries long.  Each lane counts its hits by type of
+// x in the 8-bit fields of one 64-bit register; the warp adds them up with
+// __reduce_add_sync when the member type t changes (T is sorted by type),
+// at the end, and before any field can reach 255.
+
+__device__ __forceinline__ uint32_t t_hash(int32_t x, int lgnb) {      // lgnb >= 1
+    return ((uint32_t)x * 2654435761u) >> (32 - lgnb);
 }
 
-// T as an open-addressing set (capacity 2^lgcap >= 2|T|, 4|T| for the warp
-// sets of k_clique; entries -1 when
-// empty), built by the group.
-__device__ void t_set_build(const int32_t *T, int32_t nT, int32_t *set, int lgcap, int gsize, int gr) {
-    const int cap = 1 << lgcap;
-    for (int k = gr; k < cap; k += gsize) set[k] = -1;
+__device__ __forceinline__ void group_sync(int gsize) {
     if (gsize > 32) __syncthreads(); else __syncwarp();
+}
+
+// the set of T (nT distinct ids) in 2^lgnb buckets, built by the group
+__device__ void tset_build(const int32_t *T, int32_t nT, int4 *set, int lgnb, int gsize, int gr) {
+    const int nb = 1 << lgnb;
+    int32_t *slot = reinterpret_cast<int32_t *>(set);
+    for (int k = gr; k < 4 * nb; k += gsize) slot[k] = -1;
+    group_sync(gsize);
     for (int32_t k = gr; k < nT; k += gsize) {
         const int32_t x = T[k];
-        uint32_t h = t_hash(x, lgcap);
-        for (int probe = 0; probe < cap; ++probe) {
-            if (atomicCAS(&set[h], -1, x) == -1) break;
-            h = (h + 1) & (cap - 1);
+        uint32_t b = t_hash(x, lgnb);
+        bool done = false;
+        for (int probe = 0; probe < nb && !done; ++probe) {   // 4 nb >= 2 nT: a free slot exists
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (!done) done = atomicCAS(&slot[4 * b + q], -1, x) == -1;
+            b = (b + 1) & (nb - 1);
         }
     }
-    if (gsize > 32) __syncthreads(); else __syncwarp();
+    group_sync(gsize);
 }
 
-__device__ __forceinline__ bool t_set_has(const int32_t *set, int lgcap, int32_t x) {
-    const int cap = 1 << lgcap;
-    uint32_t h = t_hash(x, lgcap);
-    for (int probe = 0; probe < cap; ++probe) {
-        const int32_t v = set[h];
-        if (v == x) return true;
-        if (v == -1) return false;
-        h = (h + 1) & (cap - 1);
+__device__ __forceinline__ bool tset_has(const int4 *set, int lgnb, int32_t x) {
+    const int nb = 1 << lgnb;
+    uint32_t b = t_hash(x, lgnb);
+    for (int probe = 0; probe < nb; ++probe) {
+        const int4 k = set[b];
+        if (k.x == x || k.y == x || k.z == x || k.w == x) return true;
+        if (k.w == -1) return false;
+        b = (b + 1) & (nb - 1);
     }
     return false;
 }
 
-// N+ lists of the 4-clique scan: entries (type << 29 | id) in type order;
-// each thread counts its run of one type of x in a register and adds it to
-// sK[type of w][type of x] when the type changes.
-constexpr int32_t kShort = 64;                // longer N+ lists: scanned by a whole warp
-
-__device__ __forceinline__ void scan_short(const GraphView &g, int32_t w, int32_t dplus, int tw, const int32_t *set,
-                                           int lgcap, unsigned *sK) {
-    int64_t sx = g.plus_off[w];
-    const int64_t se = sx + dplus;
-    unsigned c = 0;
-    uint32_t cur = 0;
-    auto take = [&](uint32_t ent) {
-        const uint32_t q = ent >> kTypeShift;
-        if (q != cur) {
-            if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
-            c = 0;
-            cur = q;
-        }
-        c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
-    };
-    for (; sx + 4 <= se; sx += 4) {
-        const uint32_t x0 = (uint32_t)g.plus_adj[sx], x1 = (uint32_t)g.plus_adj[sx + 1];
-        const uint32_t x2 = (uint32_t)g.plus_adj[sx + 2], x3 = (uint32_t)g.plus_adj[sx + 3];
-        take(x0);
-        take(x1);
-        take(x2);
-        take(x3);
-    }
-    for (; sx < se; ++sx) take((uint32_t)g.plus_adj[sx]);
-    if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
+// buckets for nT members: 4 slots per member when they fit max_slots, else
+// 2 (2^lgnb buckets of 4 slots); -1 when even that exceeds max_slots
+__device__ __forceinline__ int tset_lgnb(int32_t nT, int max_slots) {
+    int lg = 1;
+    while ((4 << lg) < 4 * nT) ++lg;
+    if ((4 << lg) <= max_slots) return lg;
+    lg = 1;
+    while ((4 << lg) < 2 * nT) ++lg;
+    return (4 << lg) <= max_slots ? lg : -1;
 }
 
-__device__ __forceinline__ void scan_long(const GraphView &g, int32_t w, int tw, const int32_t *set, int lgcap,
-                                          unsigned *sK, int lane) {
-    const int64_t pb = g.plus_off[w], pe = g.plus_off[w + 1];
-    unsigned c = 0;
-    uint32_t cur = 0;
-    auto take = [&](uint32_t ent) {
-        const uint32_t q = ent >> kTypeShift;
-        if (q != cur) {
-            if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
-            c = 0;
-            cur = q;
+// Per-lane hit counters of one warp: field q (8 bits) of `acc` counts hits
+// on entries of type q.  flush() adds the warp's fields to K[tw][.] and
+// clears them; every lane must call it (warp-uniform control flow).
+struct CliqueAcc {
+    unsigned long long acc = 0;
+    int since = 0;              // scan rounds since the last flush (<= 63: <= 252 hits per field)
+    int tw = -1;                // type of the members counted into acc
+    __device__ __forceinline__ void flush(unsigned *K, int L, int lane, bool shared_k) {
+        if (tw >= 0) {
+            for (int q = 0; q < L; ++q) {
+                const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (8 * q)) & 0xffu);
+                if (lane == 0 && v) {
+                    if (shared_k) atomicAdd(&K[tw * kMaxL + q], v);
+                    else K[tw * kMaxL + q] += v;
+                }
+            }
         }
-        c += t_set_has(set, lgcap, (int32_t)(ent & (uint32_t)kIdMask)) ? 1u : 0u;
-    };
-    // four strided entries per lane per round, loads issued first (a lane's
-    // entries stay in list order, so its type runs stay in order)
-    for (int64_t sx = pb + lane; sx < pe; sx += 128) {
+        acc = 0;
+        since = 0;
+    }
+};
+
+// member w (type tw) of T: the whole warp scans N+(w)
+__device__ __forceinline__ void clique_member(const GraphView &g, int32_t w, int tw, const int4 *set, int lgnb,
+                                              CliqueAcc &a, unsigned *K, bool shared_k, int lane) {
+    if (tw != a.tw) {
+        a.flush(K, g.L, lane, shared_k);
+        a.tw = tw;
+    }
+    const int64_t pb = g.plus_off[w];
+    const int32_t np = (int32_t)(g.plus_off[w + 1] - pb);
+    for (int32_t r0 = 0; r0 < np; r0 += 128) {
         uint32_t ent[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ent[u] = sx + 32 * u < pe ? (uint32_t)g.plus_adj[sx + 32 * u] : 0u;
+        for (int u = 0; u < 4; ++u) {
+            const int32_t idx = r0 + 32 * u + lane;
+            ent[u] = idx < np ? (uint32_t)__ldg(g.plus_adj + pb + idx) : 0u;
+        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (sx + 32 * u < pe) take(ent[u]);
+        for (int u = 0; u < 4; ++u) {
+            const bool hit = r0 + 32 * u + lane < np && tset_has(set, lgnb, (int32_t)(ent[u] & (uint32_t)kIdMask));
+            a.acc += (unsigned long long)hit << (8u * (ent[u] >> kTypeShift));
+        }
+        if (++a.since == 63) a.flush(K, g.L, lane, shared_k);
     }
-    if (c) atomicAdd(&sK[tw * kMaxL + cur], c);
 }
 
-// 4-clique pairs of one edge by a group of `gsize` threads (whole warps):
-// adjacent pairs (w, x) of T, each counted once as (smaller id, larger id),
-// into sK[type of smaller][type of larger].  Few pairs: every pair checked
-// by a binary search in the smaller id's typed row.  Otherwise each warp
-// takes members w of T and its lanes scan N+(w) = the neighbours of higher
-// priority (all types flattened), looking each up in the set of T.
-__device__ void clique_pairs(const GraphView &g, const int32_t *T, int32_t nT, const int32_t *ts, unsigned *sK,
-                             int32_t *set, int lgcap, int gsize, int gr) {
+// few pairs: every pair (a, b) of T checked by a binary search in the
+// smaller id's typed row; K by (type of smaller, type of larger)
+__device__ void clique_pairs_search(const GraphView &g, const int32_t *T, int32_t nT, const int32_t *ts, unsigned *sK,
+                                    int gsize, int gr) {
     const int L = g.L;
-    const int lane = gr & 31, wid = gr >> 5, nwarp = gsize >> 5;
     const long long npair = (long long)nT * (nT - 1) / 2;
-    if (npair <= 2 * (long long)gsize) {
-        for (long long pk = gr; pk < npair; pk += gsize) {
-            int32_t a = 0;
-            long long rem = pk;
-            while (rem >= nT - 1 - a) { rem -= nT - 1 - a; ++a; }
-            const int32_t b = a + 1 + (int32_t)rem;
-            int32_t w = T[a], x = T[b];
-            int tw = type_of_index(ts, L, a), tx = type_of_index(ts, L, b);
-            if (x < w) { int32_t y = w; w = x; x = y; int ty = tw; tw = tx; tx = ty; }
-            const int64_t sb = seg_begin(g, w, tx), se = seg_end(g, w, tx);
-            const int64_t r = lower_bound_i32(g.adj, sb, se, x);
-            if (r < se && g.adj[r] == x) atomicAdd(&sK[tw * kMaxL + tx], 1u);
-        }
-        return;
+    for (long long pk = gr; pk < npair; pk += gsize) {
+        int32_t a = 0;
+        long long rem = pk;
+        while (rem >= nT - 1 - a) { rem -= nT - 1 - a; ++a; }
+        const int32_t b = a + 1 + (int32_t)rem;
+        int32_t w = T[a], x = T[b];
+        int tw = type_of_index(ts, L, a), tx = type_of_index(ts, L, b);
+        if (x < w) { int32_t y = w; w = x; x = y; int ty = tw; tw = tx; tx = ty; }
+        const int64_t sb = seg_begin(g, w, tx), se = seg_end(g, w, tx);
+        const int64_t r = lower_bound_i32(g.adj, sb, se, x);
+        if (r < se && g.adj[r] == x) atomicAdd(&sK[tw * kMaxL + tx], 1u);
     }
-    t_set_build(T, nT, set, lgcap, gsize, gr);
-    // members in blocks of 32 per warp: each lane scans N+ of its own member
-    // when it is short (4 loads in flight); long ones are scanned by the
-    // whole warp
-    for (int32_t base = wid * 32; base < nT; base += nwarp * 32) {
-        const int32_t k = base + lane;
-        const bool valid = k < nT;
-        const int32_t w = valid ? T[k] : 0;
-        const int32_t dplus = valid ? g.nplus[w] : 0;
-        if (valid && dplus <= kShort && dplus > 0) scan_short(g, w, dplus, type_of_index(ts, L, k), set, lgcap, sK);
-        unsigned longs = __ballot_sync(0xffffffffu, valid && dplus > kShort);
-        while (longs) {
-            const int src = __ffs(longs) - 1;
-            longs &= longs - 1;
-            scan_long(g, __shfl_sync(0xffffffffu, w, src), type_of_index(ts, L, base + src), set, lgcap, sK, lane);
-        }
-    }
+}
+
+// optional diagnostic work counters (bench): lookups of the scans, pair searches
+__device__ __forceinline__ void add_work(unsigned long long *work, int slot, unsigned long long v, int lane) {
+    if (work && lane == 0 && v) atomicAdd(&work[slot], v);
 }
 
 // Warp per edge (edges with |T| <= big_t): K into kmat.
+constexpr int kCliqueWarpSlots = 1024;       // per-warp set: 4 slots per member up to |T| = 256
 __global__ void __launch_bounds__(256, 6) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
     __shared__ unsigned sKw[8][kMaxL * kMaxL];
-    __shared__ int32_t setw[8][1024];
+    __shared__ int4 setw[8][kCliqueWarpSlots / 4];
     const int L = g.L, LL = L * L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned *sK = sKw[wid];
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long probes = 0, searches = 0;
     for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
         const int64_t er = e - e0;
         const int32_t nT = (int32_t)(cv.toffs[er + 1] - cv.toffs[er]);
@@ -1039,42 +1039,84 @@ __global__ void __launch_bounds__(256, 6) k_clique(GraphView g, CountView cv, in
         __syncwarp();
         int32_t ts[kMaxL + 1];
         t_bounds(cv, L, e, ts);
-        int lg = 1;
-        while ((1 << lg) < 4 * nT) ++lg;
-        clique_pairs(g, cv.tlist + cv.toffs[er], nT, ts, sK, setw[wid], lg, 32, lane);
+        const int32_t *T = cv.tlist + cv.toffs[er];
+        const long long npair = (long long)nT * (nT - 1) / 2;
+        if (npair <= 64) {
+            clique_pairs_search(g, T, nT, ts, sK, 32, lane);
+            searches += npair;
+        } else {
+            const int lgnb = tset_lgnb(nT, kCliqueWarpSlots);   // nT <= 256: 4 slots per member
+            if (lgnb < 0) {                                     // the options clamp big_t to 256
+                if (lane == 0) set_status(cv.status, ST_INTERNAL);
+                continue;
+            }
+            tset_build(T, nT, setw[wid], lgnb, 32, lane);
+            CliqueAcc a;
+            for (int32_t k = 0; k < nT; ++k) {
+                const int32_t w = T[k];
+                probes += (unsigned long long)g.nplus[w];
+                clique_member(g, w, type_of_index(ts, L, k), setw[wid], lgnb, a, sK, false, lane);
+            }
+            a.flush(sK, L, lane, false);
+        }
         __syncwarp();
         for (int k = lane; k < LL; k += 32) km[k] = sK[(k / L) * kMaxL + (k % L)];
         __syncwarp();
     }
+    add_work(cv.work, kWorkCliqueProbes, probes, lane);
+    add_work(cv.work, kWorkCliqueSearches, searches / 32, lane);
 }
 
-// CTA per edge for the listed edges with a large T; the set of T lives in
-// shared memory up to kBigSetSmem entries, else in this CTA's global slice.
-constexpr int kBigSetSmem = 1 << 12;
-__global__ void __launch_bounds__(256, 8) k_clique_big(GraphView g, CountView cv, int64_t e0,
-                                                   const int32_t *__restrict__ big_list,
-                                                   const unsigned long long *__restrict__ big_count,
-                                                   int32_t *set_scratch, int64_t set_stride) {
+// CTA per edge for the listed edges with a large T: warps take members of T
+// from a shared counter (in order, so each warp's member types only rise);
+// the set of T lives in shared memory up to kBigSetSmem slots, else in this
+// CTA's global slice (2 slots per member).
+constexpr int kBigSetSmem = 1 << 13;
+constexpr int kBigThreads = 256;
+__global__ void __launch_bounds__(kBigThreads, 6) k_clique_big(GraphView g, CountView cv, int64_t e0,
+                                                          const int32_t *__restrict__ big_list,
+                                                          const unsigned long long *__restrict__ big_count,
+                                                          int32_t *set_scratch, int64_t set_stride) {
     __shared__ unsigned sK[kMaxL * kMaxL];
-    extern __shared__ int32_t set_smem[];
+    __shared__ int s_next;
+    extern __shared__ int4 set_smem[];
     const int L = g.L, LL = L * L;
+    const int lane = threadIdx.x & 31;
     const int64_t nb = (int64_t)*big_count;
+    unsigned long long probes = 0;
     for (int64_t k = blockIdx.x; k < nb; k += gridDim.x) {
         const int64_t e = big_list[k];
         const int64_t er = e - e0;
         const int32_t nT = (int32_t)(cv.toffs[er + 1] - cv.toffs[er]);
         for (int x = threadIdx.x; x < kMaxL * kMaxL; x += blockDim.x) sK[x] = 0;
-        __syncthreads();
+        if (threadIdx.x == 0) s_next = 0;
         int32_t ts[kMaxL + 1];
         t_bounds(cv, L, e, ts);
-        int lg = 1;
-        while ((1 << lg) < 2 * nT) ++lg;
-        int32_t *set = (1 << lg) <= kBigSetSmem ? set_smem : set_scratch + (int64_t)blockIdx.x * set_stride;
-        clique_pairs(g, cv.tlist + cv.toffs[er], nT, ts, sK, set, lg, blockDim.x, threadIdx.x);
+        const int32_t *T = cv.tlist + cv.toffs[er];
+        int lgnb = tset_lgnb(nT, kBigSetSmem);
+        int4 *set = set_smem;
+        if (lgnb < 0) {                                     // global slice: 2^lg >= 2 nT slots
+            lgnb = 1;
+            while ((4 << lgnb) < 2 * nT) ++lgnb;
+            set = reinterpret_cast<int4 *>(set_scratch + (int64_t)blockIdx.x * set_stride);
+        }
+        tset_build(T, nT, set, lgnb, blockDim.x, threadIdx.x);   // ends with a barrier
+        CliqueAcc a;
+        for (;;) {
+            int32_t m = 0;
+            if (lane == 0) m = atomicAdd(&s_next, 1);
+            m = __shfl_sync(0xffffffffu, m, 0);
+            if (m >= nT) break;
+            const int32_t w = T[m];
+            probes += (unsigned long long)g.nplus[w];
+            clique_member(g, w, type_of_index(ts, L, m), set, lgnb, a, sK, true, lane);
+        }
+        a.flush(sK, L, lane, true);
         __syncthreads();
         for (int x = threadIdx.x; x < LL; x += blockDim.x) cv.kmat[er * LL + x] = sK[(x / L) * kMaxL + (x % L)];
         __syncthreads();
     }
+    add_work(cv.work, kWorkCliqueBigProbes, probes, lane);
 }
 
 // value of matrix entry k (0 <= k < L*L) held as (r0 on lane k, or r1 on lane k-32)
@@ -1714,7 +1756,7 @@ void prepare_edges(Graph &G, int k, cudaStream_t s) {
         // a set of capacity >= 2 max degree per CTA, for edges whose T exceeds shared memory
         int64_t cap = 1;
         while (cap < 2 * std::max<int64_t>(G.max_degree, 1)) cap <<= 1;
-        G.big_blocks = sm_count() * 8;
+        G.big_blocks = sm_count() * 6;
         G.set_stride = cap > kBigSetSmem ? cap : 1;
         G.set_scratch.alloc(sizeof(int32_t) * (size_t)(G.set_stride * G.big_blocks));
     }

@@ -145,6 +145,8 @@ struct Graph {
     // counting state
     DBuf C, tau, A, tables, gacc, status, tiles_full, stage_pe, stage_gl;
     DBuf tcount, toffs, tlist, tsum, kmat, big_list, big_count, scan_tmp, set_scratch;
+    DBuf work;                          // [kWorkSlots] work counters (tg_set_work_counting)
+    bool work_on = false;
     int64_t set_stride = 1;
     int32_t big_blocks = 1;
     int64_t n_tiles_full = 0, max_chunk_edges = 0, tlist_cap = 0;
@@ -208,6 +210,7 @@ struct Graph {
         c.table_stride = table_stride;
         c.gacc = gacc.as<unsigned long long>();
         c.status = status.as<uint32_t>();
+        c.work = work_on ? work.as<unsigned long long>() : nullptr;
         return c;
     }
     Graph() {
@@ -223,7 +226,7 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
+                             &set_scratch, &work, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
                 &pa_cls, &pa_gacc};
     }
     int64_t device_bytes() const {

@@ -31,6 +31,8 @@ constexpr int kWarp = 32;
 constexpr int kTypeShift = 29;                     // packed (type << 29 | id) sort keys
 constexpr int32_t kIdMask = (1 << kTypeShift) - 1;
 constexpr int kHeavyCap = 4096;                    // shared-memory hash rows of a heavy anchor
+// slots of the optional work counters (tg_set_work_counting; TG_WORK_*)
+enum : int { kWorkCliqueProbes = 0, kWorkCliqueSearches = 1, kWorkCliqueBigProbes = 2, kWorkSlots = 8 };
 constexpr int kHeavyFit = kHeavyCap / 4 * 3;       // its load limit (distinct wedge ends)
 
 // Read-only view of a built graph, passed to kernels by value.
@@ -73,6 +75,7 @@ struct CountView {
     int64_t table_stride;       // entries (uint32) per CTA table
     unsigned long long *gacc;   // [ngraphs*G] raw per-graphlet edge sums
     uint32_t *status;           // device status word
+    unsigned long long *work;   // [kWorkSlots] work counters, or nullptr (counting off)
 };
 
 __host__ __device__ inline int64_t npairs(int L) { return (int64_t)L * (L + 1) / 2; }

@@ -79,6 +79,8 @@ SIGNATURES = {
     "tg_abi_version": ([], _i32),
     "tg_count3_static": ([_i64, _i64, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
     "tg_set_timing": ([_vp, _i32], _i32),
+    "tg_set_work_counting": ([_vp, _i32], _i32),
+    "tg_get_work": ([_vp, _vp, _i32], _i32),
     "tg_get_timing": ([_vp, _i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], _i32),
 }
@@ -355,6 +357,22 @@ def tg_get_timing(g: Graph, max_entries: int = 32) -> dict:
     n = ctypes.c_int32(0)
     _check(load().tg_get_timing(g.handle, max_entries, names, ms, launches, ctypes.byref(n)), "tg_get_timing")
     return {names[i].decode(): (ms[i], int(launches[i])) for i in range(n.value)}
+
+
+WORK_SLOTS = {"clique_probes": 0, "clique_searches": 1, "clique_big_probes": 2}
+
+
+def tg_set_work_counting(g: "Graph", on: bool = True) -> None:
+    """Enables the diagnostic work counters of the counting kernels."""
+    _check(load().tg_set_work_counting(g.handle, 1 if on else 0), "tg_set_work_counting")
+
+
+def tg_get_work(g: "Graph") -> dict:
+    """Work counters accumulated since the last call (then cleared)."""
+    import numpy as np
+    out = np.zeros(8, dtype=np.int64)
+    _check(load().tg_get_work(g.handle, out.ctypes.data, 8), "tg_get_work")
+    return {name: int(out[k]) for name, k in WORK_SLOTS.items()}
 
 
 def tg_count3_static(row_ptr, col, node_types, L: int, per_edge_out=None, global_out=None, device_status=None,

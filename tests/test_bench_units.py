@@ -81,3 +81,85 @@ def test_count_only_split(bench):
     assert got == {"value": round(20_000_000 / 0.9084, 1), "unit": "edges/s", "count_ms": 908.4,
                    "build_and_free_ms": 34.3}
     assert bench.count_only(10, 0.0, 1.0) is None
+
+
+# ------------------------------------------------------- CPU-baseline estimator
+
+def test_edge_cost_proxy_is_its_definition(bench):
+    g = random_graph(14, 0.4, 3, 71)
+    src, dst, proxy = bench.edge_cost_proxy(g)
+    import oracle
+    s_o, d_o = oracle.edges(g)
+    np.testing.assert_array_equal(src, s_o)
+    np.testing.assert_array_equal(dst, d_o)
+    rp, col = g["row_ptr"], g["col"]
+    adj = [col[rp[x]:rp[x + 1]].tolist() for x in range(g["n"])]
+    for e, (u, v) in enumerate(zip(src, dst)):
+        want = len(adj[u]) + len(adj[v]) + sum(len(adj[w]) for w in adj[u]) + sum(len(adj[w]) for w in adj[v])
+        assert proxy[e] == want
+
+
+def test_oracle_design_partitions_the_edges(bench):
+    rng = np.random.default_rng(4)
+    proxy = np.exp(rng.normal(10, 2, 50_000))
+    strata = bench.oracle_design(proxy, budget_edges=400, heaviest=30, seed=9)
+    assert strata[0][0] == "heaviest" and strata[0][1] == 30
+    np.testing.assert_array_equal(np.sort(strata[0][2]), np.sort(np.argsort(-proxy)[:30]))
+    assert sum(N for _, N, _ in strata) == len(proxy)              # the strata cover every edge once
+    for _, N, pick in strata:
+        assert 1 <= len(pick) <= N and len(np.unique(pick)) == len(pick)
+    again = bench.oracle_design(proxy, budget_edges=400, heaviest=30, seed=9)
+    assert all(np.array_equal(a[2], b[2]) for a, b in zip(strata, again))    # seeded
+
+
+class _FakeOpen:
+    """Stands in for oracle.OpenGraph: every edge takes time c * proxy."""
+
+    def __init__(self, proxy, c):
+        self.proxy, self.c = proxy, c
+
+    def paper_edges(self, ids, k=4, nthreads=0, per_edge=False, times=False):
+        return None, None, self.c * self.proxy[ids]
+
+
+@pytest.mark.parametrize("thin", [1, 10])
+def test_estimator_is_exact_when_time_follows_the_proxy_within_strata(bench, thin):
+    # time proportional to the proxy: within a log2 stratum the per-edge
+    # times vary, so only the certainty stratum is exact; a constant time
+    # per stratum makes the Horvitz-Thompson sum exact
+    rng = np.random.default_rng(5)
+    proxy = np.floor(2.0 ** rng.uniform(3, 20, 20_000))
+    strata = bench.oracle_design(proxy, budget_edges=500, heaviest=50, seed=3)
+    bins = np.floor(np.log2(proxy))
+    flat = 2.0 ** bins                                              # one value per stratum
+    top = strata[0][2]
+    flat[top] = proxy[top]
+    r = bench.oracle_estimate(_FakeOpen(flat, 1e-6), strata, nthreads=4, thin=thin)
+    assert abs(r["work_thread_s"] - 1e-6 * flat.sum()) <= 1e-9 * flat.sum()
+    r2 = bench.oracle_estimate(_FakeOpen(proxy, 1e-6), strata, nthreads=4, thin=thin)
+    assert abs(r2["work_thread_s"] / (1e-6 * proxy.sum()) - 1) < 0.05    # unbiased up to sampling
+
+
+def test_w_alg_is_its_definition(bench):
+    import math
+
+    import oracle
+    g = graphgen.chung_lu(300, 1500, 2.1, 60.0, 3, 12)
+    pe, _ = oracle.paper(g, k=3)
+    L = g["L"]
+    tsize = pe[:, L:2 * L].sum(1)
+    rp, col = g["row_ptr"], g["col"]
+    adj = [col[rp[x]:rp[x + 1]].tolist() for x in range(g["n"])]
+    deg = [len(a) for a in adj]
+    lg = [math.ceil(math.log2(d)) if d > 1 else 0 for d in deg]
+    src, dst = oracle.edges(g)
+    S = 2 * L + 10 * L * (L + 1) // 2
+    want = 0
+    for e, (i, j) in enumerate(zip(src, dst)):
+        U = deg[i] + deg[j] - 2 - int(tsize[e])
+        want += 4 * (deg[i] + deg[j])
+        for x, other in ((i, j), (j, i)):
+            want += 4 * sum(min(deg[w], U * lg[w]) for w in adj[x] if w != other)
+    want += 4 * S * len(src)
+    got = bench.w_alg_bytes(g, tsize, S)["bytes"]
+    assert abs(got - want) <= 1e-9 * want
