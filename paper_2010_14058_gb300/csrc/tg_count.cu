@@ -862,15 +862,21 @@ __global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int6
 }
 
 // type boundaries of an edge's T list, from its typed triangle counts
+// (indices unrolled, so ts[] stays in registers)
 __device__ __forceinline__ void t_bounds(const CountView &cv, int L, int64_t e, int32_t *ts) {
     int32_t acc = 0;
-    for (int q = 0; q < L; ++q) { ts[q] = acc; acc += (int32_t)cv.C[e * L + q]; }
-    for (int q = L; q <= kMaxL; ++q) ts[q] = acc;
+#pragma unroll
+    for (int q = 0; q <= kMaxL; ++q) {
+        ts[q] = acc;
+        if (q < L) acc += (int32_t)cv.C[e * L + q];
+    }
 }
 
-__device__ __forceinline__ int type_of_index(const int32_t *ts, int L, int32_t k) {
+// type of T's member k (0 <= k < |T|): ts[q] = |T| > k for q >= L
+__device__ __forceinline__ int type_of_index(const int32_t *ts, int32_t k) {
     int t = 0;
-    for (int q = 1; q < L; ++q) t += ts[q] <= k ? 1 : 0;
+#pragma unroll
+    for (int q = 1; q < kMaxL; ++q) t += ts[q] <= k ? 1 : 0;
     return t;
 }
 
@@ -889,9 +895,11 @@ __device__ __forceinline__ int type_of_index(const int32_t *ts, int L, int32_t k
 // The scan: one whole warp per member, lanes striding over N+(w) (coalesced
 // loads, 4 in flight per lane) -- the lists behind almost all lookups are
 // tens to thousands of entries long.  Each lane counts its hits by type of
-// x in the 8-bit fields of one 64-bit register; the warp adds them up with
-// __reduce_add_sync when the member type t changes (T is sorted by type),
-// at the end, and before any field can reach 255.
+// x in the 8-bit fields of one 64-bit register (no warp-wide step inside
+// the scan, so a lane's four lookups overlap); the warp sums the fields
+// with __reduce_add_sync before any can reach 255 and when the member type
+// t changes (T is sorted by type), and lane q adds the count for x of type
+// q to K[t][q].
 
 __device__ __forceinline__ uint32_t t_hash(int32_t x, int lgnb) {      // lgnb >= 1
     return ((uint32_t)x * 2654435761u) >> (32 - lgnb);
@@ -921,14 +929,21 @@ __device__ void tset_build(const int32_t *T, int32_t nT, int4 *set, int lgnb, in
     group_sync(gsize);
 }
 
+__device__ __forceinline__ bool bucket_has(const int4 &k, int32_t x) {
+    return (k.x == x) | (k.y == x) | (k.z == x) | (k.w == x);
+}
+
 __device__ __forceinline__ bool tset_has(const int4 *set, int lgnb, int32_t x) {
-    const int nb = 1 << lgnb;
     uint32_t b = t_hash(x, lgnb);
-    for (int probe = 0; probe < nb; ++probe) {
-        const int4 k = set[b];
-        if (k.x == x || k.y == x || k.z == x || k.w == x) return true;
-        if (k.w == -1) return false;
+    int4 k = set[b];
+    if (bucket_has(k, x)) return true;
+    if (k.w == -1) return false;                            // the bucket is not full
+    const int nb = 1 << lgnb;                               // rare: continue in the next buckets
+    for (int probe = 1; probe < nb; ++probe) {
         b = (b + 1) & (nb - 1);
+        k = set[b];
+        if (bucket_has(k, x)) return true;
+        if (k.w == -1) return false;
     }
     return false;
 }
@@ -944,58 +959,60 @@ __device__ __forceinline__ int tset_lgnb(int32_t nT, int max_slots) {
     return (4 << lg) <= max_slots ? lg : -1;
 }
 
-// Per-lane hit counters of one warp: field q (8 bits) of `acc` counts hits
-// on entries of type q.  flush() adds the warp's fields to K[tw][.] and
-// clears them; every lane must call it (warp-uniform control flow).
+// Per-lane hit counters of one warp: field q (8 bits) of `acc` counts the
+// lane's hits on entries of type q; `since` counts scan rounds (at most 4
+// hits per field each) since the fields were last emptied into `kreg`, where
+// lane q holds the warp's count for type q.  Warp-uniform control flow.
 struct CliqueAcc {
-    unsigned long long acc = 0;
-    int since = 0;              // scan rounds since the last flush (<= 63: <= 252 hits per field)
-    int tw = -1;                // type of the members counted into acc
-    __device__ __forceinline__ void flush(unsigned *K, int L, int lane, bool shared_k) {
-        if (tw >= 0) {
-            for (int q = 0; q < L; ++q) {
-                const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (8 * q)) & 0xffu);
-                if (lane == 0 && v) {
-                    if (shared_k) atomicAdd(&K[tw * kMaxL + q], v);
-                    else K[tw * kMaxL + q] += v;
-                }
-            }
+    unsigned long long acc = 0, kreg = 0;
+    int since = 0;
+    __device__ __forceinline__ void drain(int L) {
+        for (int q = 0; q < L; ++q) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (8 * q)) & 0xffu);
+            kreg += (threadIdx.x & 31) == (unsigned)q ? (unsigned long long)v : 0ull;
         }
         acc = 0;
         since = 0;
     }
 };
 
-// member w (type tw) of T: the whole warp scans N+(w)
-__device__ __forceinline__ void clique_member(const GraphView &g, int32_t w, int tw, const int4 *set, int lgnb,
-                                              CliqueAcc &a, unsigned *K, bool shared_k, int lane) {
-    if (tw != a.tw) {
-        a.flush(K, g.L, lane, shared_k);
-        a.tw = tw;
+// lanes q < L add the warp's counts to K[tw][q]
+__device__ __forceinline__ void flush_k(CliqueAcc &a, int tw, unsigned long long *K, int L, int lane, bool shared_k) {
+    a.drain(L);
+    if (tw >= 0 && lane < L && a.kreg) {
+        if (shared_k) atomicAdd(&K[tw * kMaxL + lane], a.kreg);
+        else K[tw * kMaxL + lane] += a.kreg;
     }
+    a.kreg = 0;
+}
+
+// member w of T: the whole warp scans N+(w); returns |N+(w)|
+__device__ __forceinline__ int32_t scan_member(const GraphView &g, int32_t w, const int4 *set, int lgnb, CliqueAcc &a,
+                                               int lane) {
     const int64_t pb = g.plus_off[w];
     const int32_t np = (int32_t)(g.plus_off[w + 1] - pb);
+    const int32_t *src = g.plus_adj + pb;
     for (int32_t r0 = 0; r0 < np; r0 += 128) {
         uint32_t ent[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int32_t idx = r0 + 32 * u + lane;
-            ent[u] = idx < np ? (uint32_t)__ldg(g.plus_adj + pb + idx) : 0u;
+            ent[u] = idx < np ? (uint32_t)__ldg(src + idx) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool hit = r0 + 32 * u + lane < np && tset_has(set, lgnb, (int32_t)(ent[u] & (uint32_t)kIdMask));
             a.acc += (unsigned long long)hit << (8u * (ent[u] >> kTypeShift));
         }
-        if (++a.since == 63) a.flush(K, g.L, lane, shared_k);
+        if (++a.since == 63) a.drain(g.L);
     }
+    return np;
 }
 
 // few pairs: every pair (a, b) of T checked by a binary search in the
 // smaller id's typed row; K by (type of smaller, type of larger)
-__device__ void clique_pairs_search(const GraphView &g, const int32_t *T, int32_t nT, const int32_t *ts, unsigned *sK,
-                                    int gsize, int gr) {
-    const int L = g.L;
+__device__ void clique_pairs_search(const GraphView &g, const int32_t *T, int32_t nT, const int32_t *ts,
+                                    unsigned long long *sK, int gsize, int gr) {
     const long long npair = (long long)nT * (nT - 1) / 2;
     for (long long pk = gr; pk < npair; pk += gsize) {
         int32_t a = 0;
@@ -1003,11 +1020,11 @@ __device__ void clique_pairs_search(const GraphView &g, const int32_t *T, int32_
         while (rem >= nT - 1 - a) { rem -= nT - 1 - a; ++a; }
         const int32_t b = a + 1 + (int32_t)rem;
         int32_t w = T[a], x = T[b];
-        int tw = type_of_index(ts, L, a), tx = type_of_index(ts, L, b);
+        int tw = type_of_index(ts, a), tx = type_of_index(ts, b);
         if (x < w) { int32_t y = w; w = x; x = y; int ty = tw; tw = tx; tx = ty; }
         const int64_t sb = seg_begin(g, w, tx), se = seg_end(g, w, tx);
         const int64_t r = lower_bound_i32(g.adj, sb, se, x);
-        if (r < se && g.adj[r] == x) atomicAdd(&sK[tw * kMaxL + tx], 1u);
+        if (r < se && g.adj[r] == x) atomicAdd(&sK[tw * kMaxL + tx], 1ull);
     }
 }
 
@@ -1018,12 +1035,12 @@ __device__ __forceinline__ void add_work(unsigned long long *work, int slot, uns
 
 // Warp per edge (edges with |T| <= big_t): K into kmat.
 constexpr int kCliqueWarpSlots = 1024;       // per-warp set: 4 slots per member up to |T| = 256
-__global__ void __launch_bounds__(256, 6) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
-    __shared__ unsigned sKw[8][kMaxL * kMaxL];
+__global__ void __launch_bounds__(256, 5) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
+    __shared__ unsigned long long sKw[8][kMaxL * kMaxL];
     __shared__ int4 setw[8][kCliqueWarpSlots / 4];
     const int L = g.L, LL = L * L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned *sK = sKw[wid];
+    unsigned long long *sK = sKw[wid];
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long probes = 0, searches = 0;
     for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
@@ -1051,33 +1068,60 @@ __global__ void __launch_bounds__(256, 6) k_clique(GraphView g, CountView cv, in
                 continue;
             }
             tset_build(T, nT, setw[wid], lgnb, 32, lane);
-            CliqueAcc a;
+            CliqueAcc acc;
+            int tw = -1;
             for (int32_t k = 0; k < nT; ++k) {
-                const int32_t w = T[k];
-                probes += (unsigned long long)g.nplus[w];
-                clique_member(g, w, type_of_index(ts, L, k), setw[wid], lgnb, a, sK, false, lane);
+                const int t = type_of_index(ts, k);
+                if (t != tw) {
+                    flush_k(acc, tw, sK, L, lane, false);
+                    tw = t;
+                }
+                probes += (unsigned long long)scan_member(g, T[k], setw[wid], lgnb, acc, lane);
             }
-            a.flush(sK, L, lane, false);
+            flush_k(acc, tw, sK, L, lane, false);
         }
         __syncwarp();
         for (int k = lane; k < LL; k += 32) km[k] = sK[(k / L) * kMaxL + (k % L)];
         __syncwarp();
     }
     add_work(cv.work, kWorkCliqueProbes, probes, lane);
-    add_work(cv.work, kWorkCliqueSearches, searches / 32, lane);
+    add_work(cv.work, kWorkCliqueSearches, searches, lane);
 }
 
-// CTA per edge for the listed edges with a large T: warps take members of T
-// from a shared counter (in order, so each warp's member types only rise);
-// the set of T lives in shared memory up to kBigSetSmem slots, else in this
-// CTA's global slice (2 slots per member).
+// the members of T taken by the CTA's warps from a shared counter (in
+// order, so each warp's member types only rise)
+__device__ __forceinline__ unsigned long long big_members(const GraphView &g, const int32_t *T, int32_t nT,
+                                                          const int32_t *ts, const int4 *set, int lgnb,
+                                                          unsigned long long *sK, int *next, int lane) {
+    CliqueAcc acc;
+    unsigned long long probes = 0;
+    int tw = -1;
+    for (;;) {
+        int32_t m = 0;
+        if (lane == 0) m = atomicAdd(next, 1);
+        m = __shfl_sync(0xffffffffu, m, 0);
+        if (m >= nT) break;
+        const int t = type_of_index(ts, m);
+        if (t != tw) {
+            flush_k(acc, tw, sK, g.L, lane, true);
+            tw = t;
+        }
+        probes += (unsigned long long)scan_member(g, T[m], set, lgnb, acc, lane);
+    }
+    flush_k(acc, tw, sK, g.L, lane, true);
+    return probes;
+}
+
+// CTA per edge for the listed edges with a large T; the set of T lives in
+// shared memory up to kBigSetSmem slots, else in this CTA's global slice
+// (2 slots per member).
 constexpr int kBigSetSmem = 1 << 13;
 constexpr int kBigThreads = 256;
-__global__ void __launch_bounds__(kBigThreads, 6) k_clique_big(GraphView g, CountView cv, int64_t e0,
+__global__ void __launch_bounds__(kBigThreads, 5) k_clique_big(GraphView g, CountView cv, int64_t e0,
                                                           const int32_t *__restrict__ big_list,
                                                           const unsigned long long *__restrict__ big_count,
                                                           int32_t *set_scratch, int64_t set_stride) {
-    __shared__ unsigned sK[kMaxL * kMaxL];
+    __shared__ unsigned long long sK[kMaxL * kMaxL];
     __shared__ int s_next;
     extern __shared__ int4 set_smem[];
     const int L = g.L, LL = L * L;
@@ -1093,25 +1137,17 @@ __global__ void __launch_bounds__(kBigThreads, 6) k_clique_big(GraphView g, Coun
         int32_t ts[kMaxL + 1];
         t_bounds(cv, L, e, ts);
         const int32_t *T = cv.tlist + cv.toffs[er];
-        int lgnb = tset_lgnb(nT, kBigSetSmem);
-        int4 *set = set_smem;
-        if (lgnb < 0) {                                     // global slice: 2^lg >= 2 nT slots
-            lgnb = 1;
-            while ((4 << lgnb) < 2 * nT) ++lgnb;
-            set = reinterpret_cast<int4 *>(set_scratch + (int64_t)blockIdx.x * set_stride);
+        const int lgs = tset_lgnb(nT, kBigSetSmem);
+        if (lgs >= 0) {                                     // CTA-uniform
+            tset_build(T, nT, set_smem, lgs, blockDim.x, threadIdx.x);   // ends with a barrier
+            probes += big_members(g, T, nT, ts, set_smem, lgs, sK, &s_next, lane);
+        } else {                                            // global slice: 2^lg >= 2 nT slots
+            int lg = 1;
+            while ((4 << lg) < 2 * nT) ++lg;
+            int4 *set = reinterpret_cast<int4 *>(set_scratch + (int64_t)blockIdx.x * set_stride);
+            tset_build(T, nT, set, lg, blockDim.x, threadIdx.x);
+            probes += big_members(g, T, nT, ts, set, lg, sK, &s_next, lane);
         }
-        tset_build(T, nT, set, lgnb, blockDim.x, threadIdx.x);   // ends with a barrier
-        CliqueAcc a;
-        for (;;) {
-            int32_t m = 0;
-            if (lane == 0) m = atomicAdd(&s_next, 1);
-            m = __shfl_sync(0xffffffffu, m, 0);
-            if (m >= nT) break;
-            const int32_t w = T[m];
-            probes += (unsigned long long)g.nplus[w];
-            clique_member(g, w, type_of_index(ts, L, m), set, lgnb, a, sK, true, lane);
-        }
-        a.flush(sK, L, lane, true);
         __syncthreads();
         for (int x = threadIdx.x; x < LL; x += blockDim.x) cv.kmat[er * LL + x] = sK[(x / L) * kMaxL + (x % L)];
         __syncthreads();
@@ -1756,7 +1792,7 @@ void prepare_edges(Graph &G, int k, cudaStream_t s) {
         // a set of capacity >= 2 max degree per CTA, for edges whose T exceeds shared memory
         int64_t cap = 1;
         while (cap < 2 * std::max<int64_t>(G.max_degree, 1)) cap <<= 1;
-        G.big_blocks = sm_count() * 6;
+        G.big_blocks = sm_count() * 5;
         G.set_stride = cap > kBigSetSmem ? cap : 1;
         G.set_scratch.alloc(sizeof(int32_t) * (size_t)(G.set_stride * G.big_blocks));
     }
