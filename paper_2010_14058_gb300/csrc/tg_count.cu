@@ -609,19 +609,23 @@ __device__ __forceinline__ int64_t hub_find_item(const int64_t *__restrict__ wof
     return lo + (31 - __clz(b));
 }
 
-// One phase of the wedge pass over the wedges [w0, w1) of items [i0, i1)
-// (hubs h0 ...; hub h uses table h - h0).  Each warp takes one contiguous
-// run of wedges, 32 at a time, one wedge per lane.
-__global__ void __launch_bounds__(kHubThreads) k_wedge_hub(GraphView g, CountView cv, HubView hv, int64_t i0,
-                                                           int64_t i1, int64_t w0, int64_t w1, int32_t h0,
-                                                           int phase) {
+// One phase of the hub wedge pass over the wedges [x0r, x1r) of one group of
+// hubs (items [i0, i1), first hub h0; hub h's table at tbl + (h - h0) *
+// stride).  Warp wi of nwi takes one contiguous run of the range, 32 wedges
+// at a time, one wedge per lane.  Counters: kPacked = two 16-bit counters
+// per 32-bit word (types 2k and 2k+1; every count is at most the hub's
+// degree, below 2^16 when this layout is chosen), else one 32-bit counter
+// per type.  The tables are read and cleared at L2 (ld/st.cg): other CTAs of
+// the same launch update them, so no L1 copy may be trusted.
+template <bool kPacked>
+__device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubView &hv, int64_t i0, int64_t i1,
+                           int64_t x0r, int64_t x1r, int32_t h0, uint32_t *tbl, int64_t stride, int phase, int wi,
+                           int nwi, int lane) {
     const int L = g.L;
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t per = (((w1 - w0) + nw - 1) / nw + 31) & ~(int64_t)31;
-    int64_t x0 = w0 + gw * per;
-    const int64_t xe = min(w1, x0 + per);
+    const int RW = kPacked ? (L + 1) / 2 : L;               // words per table row
+    const int64_t per = (((x1r - x0r) + nwi - 1) / nwi + 31) & ~(int64_t)31;
+    int64_t x0 = x0r + wi * per;
+    const int64_t xe = min(x1r, x0 + per);
     if (x0 >= xe) return;                                   // warp-uniform
     const int64_t nnz = cv.a_stride;
     uint32_t *A = cv.A - cv.a_base;                         // indexed by absolute slot
@@ -655,20 +659,25 @@ __global__ void __launch_bounds__(kHubThreads) k_wedge_hub(GraphView g, CountVie
             svp = hv.sv[it];
             const int64_t pos = (int64_t)hv.vb[it] + (x - wstart);
             const int32_t w = g.adj[pos];
-            uint32_t *row = cv.tables + (int64_t)(hh - h0) * cv.table_stride + (w - hv.hub_base[hh]) * L;
+            uint32_t *row = tbl + (int64_t)(hh - h0) * stride + (w - hv.hub_base[hh]) * RW;
             if (phase == 0) {
-                atomicAdd(row + tv, 1u);
+                if (kPacked) atomicAdd(row + (tv >> 1), 1u << (16 * (tv & 1)));
+                else atomicAdd(row + tv, 1u);
             } else if (phase == 1) {
                 const int tu = g.ty[hv.hubs[hh]];
+                uint32_t words[kMaxL];
+#pragma unroll
+                for (int q = 0; q < kMaxL; ++q) words[q] = q < RW ? __ldcg(row + q) : 0u;
 #pragma unroll
                 for (int t = 0; t < kMaxL; ++t) {
                     if (t >= L) break;
-                    const uint32_t v = row[t] - (t == tv ? 1u : 0u);
+                    const uint32_t h = kPacked ? (words[t >> 1] >> (16 * (t & 1))) & 0xffffu : words[t];
+                    const uint32_t v = h - (t == tv ? 1u : 0u);
                     c[t] = v;
                     if (v) atomicAdd(&A[(int64_t)(tu * L + t) * nnz + pos], v);
                 }
             } else {
-                for (int t = 0; t < L; ++t) row[t] = 0;
+                for (int q = 0; q < RW; ++q) __stcg(row + q, 0u);
             }
         }
         if (phase == 1) {
@@ -696,6 +705,112 @@ __global__ void __launch_bounds__(kHubThreads) k_wedge_hub(GraphView g, CountVie
         }
         // first item of the next 32 wedges: the item of x0 + 32
         j = (wnext <= x0 + 32) ? j + k31 + 1 : j + k31;
+    }
+}
+
+// The hub pass as one persistent launch over a ticket queue.  The hubs are
+// cut into groups whose tables fit one of kHubBuffers table buffers; every
+// group has four kinds of tickets, each a range of its wedges or table
+// words: 0 fill the counters, 1 read them (4-cycle slot updates), 2 clear
+// them by walking the wedges again or 3 by zeroing the group's table words.
+// A CTA takes the next ticket from a device counter and, before working on
+// it, waits until the tickets it needs are done: reading needs the group's
+// fills, clearing its reads, and filling the clears of the group that used
+// the same buffer before (kHubBuffers groups back).  Tickets are queued so
+// that those are a few groups earlier, and a ticket is taken only by a
+// running CTA, so every wait ends; each wait is bounded all the same and
+// reports TG_ERR_TIMEOUT (the ticket is then skipped but still marked done,
+// so no other wait depends on it forever).
+
+constexpr int kHubBuffers = 3;
+constexpr int kHubKinds = 4;
+constexpr long long kSpinLimit = 1ll << 24;                // polls of 256 ns and more: several seconds
+
+// range of ticket `local` of a (group, kind) run: wedges for kinds 0-2,
+// table words of the group's buffer for kind 3
+__device__ __forceinline__ void hub_ticket_range(const HubGroup &gr, int kind, int64_t local, int64_t &x0, int64_t &x1) {
+    if (kind == 3) {
+        x0 = local * kHubTicketWords;
+        x1 = min(gr.zwords, x0 + kHubTicketWords);
+    } else {
+        x0 = gr.w0 + local * gr.tw;
+        x1 = min(gr.w1, x0 + gr.tw);
+    }
+}
+
+__device__ bool wait_done(const unsigned long long *ctr, unsigned long long target, uint32_t *status) {
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        if (*(volatile const unsigned long long *)ctr >= target) return true;
+        if (*(volatile const uint32_t *)status & ST_TIMEOUT) return false;   // another wait ran out: drain
+        __nanosleep(256);
+    }
+    set_status(status, ST_TIMEOUT);
+    return false;
+}
+
+template <bool kPacked>
+__global__ void __launch_bounds__(kHubThreads, 5) k_wedge_hub(GraphView g, CountView cv, HubView hv,
+                                                           const HubSegment *__restrict__ segs, int64_t n_segs,
+                                                           int64_t n_tickets, const HubGroup *__restrict__ groups,
+                                                           const int64_t *__restrict__ ntick,
+                                                           unsigned long long *ctr, uint32_t *tables, int64_t buf_words,
+                                                           int64_t stride) {
+    __shared__ int64_t s_t, s_x0, s_x1;
+    __shared__ int s_ok, s_group, s_kind;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    unsigned long long *next = ctr;                         // ticket counter
+    unsigned long long *done = ctr + 1;                     // [group][kind] tickets done
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t t = (int64_t)atomicAdd(next, 1ull);
+            bool ok = true;
+            if (t < n_tickets) {
+                int64_t lo = 0, hi = n_segs;                // the run holding ticket t: segs[lo].t0 <= t
+                while (hi - lo > 1) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (segs[mid].t0 <= t) lo = mid; else hi = mid;
+                }
+                const HubSegment sg = segs[lo];
+                int64_t x0, x1;
+                hub_ticket_range(groups[sg.group], sg.kind, t - sg.t0, x0, x1);
+                s_x0 = x0;
+                s_x1 = x1;
+                s_group = sg.group;
+                s_kind = sg.kind;
+                const int64_t q = sg.group;
+                if (sg.kind == 1) {
+                    ok = wait_done(&done[q * kHubKinds + 0], (unsigned long long)ntick[q * kHubKinds + 0], cv.status);
+                } else if (sg.kind >= 2) {
+                    ok = wait_done(&done[q * kHubKinds + 1], (unsigned long long)ntick[q * kHubKinds + 1], cv.status);
+                } else if (q >= kHubBuffers) {
+                    const int64_t p = q - kHubBuffers;
+                    ok = wait_done(&done[p * kHubKinds + 2], (unsigned long long)ntick[p * kHubKinds + 2], cv.status) &&
+                         wait_done(&done[p * kHubKinds + 3], (unsigned long long)ntick[p * kHubKinds + 3], cv.status);
+                }
+                __threadfence();
+            }
+            s_t = t;
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= n_tickets) break;                          // CTA-uniform
+        const int group = s_group, kind = s_kind;
+        const int64_t x0 = s_x0, x1 = s_x1;
+        const HubGroup gr = groups[group];
+        uint32_t *tbl = tables + (int64_t)gr.buf * buf_words;
+        if (s_ok) {
+            if (kind == 3) {
+                for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) __stcg(tbl + x, 0u);
+            } else {
+                hub_wedges<kPacked>(g, cv, hv, gr.i0, gr.i1, x0, x1, gr.h0, tbl, stride, kind, wid, nwarp, lane);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[(int64_t)group * kHubKinds + kind], 1ull);
+        }
     }
 }
 
@@ -779,17 +894,25 @@ __global__ void k_tcount(GraphView g, CountView cv, int64_t e0, int64_t e1, int6
 }
 
 // Warp per edge: T list and the triangle-node sums (Cor. 1; gathers of the
-// typed triangle counts of the edges (i,w), (j,w) and of d_w^t').
-// Acc = uint32_t when the maximum degree is below 2^16 (every sum here is at
-// most |T| x d < 2^32), else unsigned long long.
-__device__ __forceinline__ uint32_t warp_allsum(uint32_t v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// typed triangle counts of the edges (i,w), (j,w) and of d_w^t').  The
+// sums of one type t are held by lane t' (three registers per lane); each
+// round of 32 candidates adds the found nodes' terms with one warp
+// reduction per (sum, t').  Acc = uint32_t when the maximum degree is below
+// 2^16 (every sum here is then below 2^32 and a warp reduction of 32 terms
+// below 2^21), else unsigned long long (terms split into 16-bit halves for
+// the 32-bit reductions).
+__device__ __forceinline__ unsigned long long warp_total(uint32_t v, uint32_t) {
+    return __reduce_add_sync(0xffffffffu, v);
 }
-__device__ __forceinline__ unsigned long long warp_allsum(unsigned long long v) { return warp_allsum_u64(v); }
+__device__ __forceinline__ unsigned long long warp_total(uint32_t v, unsigned long long) {
+    const unsigned long long lo = __reduce_add_sync(0xffffffffu, v & 0xffffu);
+    const unsigned long long hi = __reduce_add_sync(0xffffffffu, v >> 16);
+    return lo + (hi << 16);
+}
 
 template <class Acc>
-__global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int64_t e0, int64_t e1) {
+__global__ void __launch_bounds__(256, sizeof(Acc) == 4 ? 6 : 4) k_tsum(GraphView g, CountView cv, int64_t e0,
+                                                                        int64_t e1) {
     const int L = g.L, LL = L * L;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -800,18 +923,8 @@ __global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int6
         unsigned long long *sum = cv.tsum + er * 3 * LL;
         int32_t pos = 0;
         for (int t = 0; t < L; ++t) {
-            if (cv.C[e * L + t] == 0) {                     // no triangle node of type t
-                if (lane < L) {
-                    sum[t * L + lane] = 0;
-                    sum[LL + t * L + lane] = 0;
-                    sum[2 * LL + t * L + lane] = 0;
-                }
-                continue;
-            }
-            Acc a1[kMaxL], a2[kMaxL], a3[kMaxL];
-#pragma unroll
-            for (int q = 0; q < kMaxL; ++q) { a1[q] = 0; a2[q] = 0; a3[q] = 0; }
-            {
+            Acc s1 = 0, s2 = 0, s3 = 0;                     // lane q < L: the sums over T^t for type q
+            if (cv.C[e * L + t] != 0) {
                 int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
                 int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
                 bool swapped = false;
@@ -831,31 +944,34 @@ __global__ void __launch_bounds__(256, 3) k_tsum(GraphView g, CountView cv, int6
                         found = r < ej && g.adj[r] == w;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, found);
+                    if (bal == 0) continue;                 // warp-uniform
+                    const uint32_t *ci = cv.C, *cj = cv.C;
+                    const int32_t *o = g.toff;
                     if (found) {
                         tl[pos + __popc(bal & ((1u << lane) - 1u))] = w;
-                        const uint32_t *ci = cv.C + (int64_t)g.slot_eid[swapped ? r : s] * L;
-                        const uint32_t *cj = cv.C + (int64_t)g.slot_eid[swapped ? s : r] * L;
-                        const int32_t *o = g.toff + (int64_t)w * (L + 1);
-#pragma unroll
-                        for (int q = 0; q < kMaxL; ++q)
-                            if (q < L) {
-                                a1[q] += ci[q];
-                                a2[q] += cj[q];
-                                a3[q] += (unsigned)(o[q + 1] - o[q]);
-                            }
+                        ci = cv.C + (int64_t)g.slot_eid[swapped ? r : s] * L;
+                        cj = cv.C + (int64_t)g.slot_eid[swapped ? s : r] * L;
+                        o = g.toff + (int64_t)w * (L + 1);
                     }
                     pos += __popc(bal);
+                    for (int q = 0; q < L; ++q) {
+                        const uint32_t v1 = found ? ci[q] : 0u;
+                        const uint32_t v2 = found ? cj[q] : 0u;
+                        const uint32_t v3 = found ? (uint32_t)(o[q + 1] - o[q]) : 0u;
+                        const unsigned long long t1 = warp_total(v1, Acc()), t2 = warp_total(v2, Acc());
+                        const unsigned long long t3 = warp_total(v3, Acc());
+                        if (lane == q) {
+                            s1 += (Acc)t1;
+                            s2 += (Acc)t2;
+                            s3 += (Acc)t3;
+                        }
+                    }
                 }
             }
-#pragma unroll
-            for (int q = 0; q < kMaxL; ++q) {
-                if (q >= L) break;
-                const Acc v1 = warp_allsum(a1[q]), v2 = warp_allsum(a2[q]), v3 = warp_allsum(a3[q]);
-                if (lane == q) {
-                    sum[t * L + q] = (unsigned long long)v1;
-                    sum[LL + t * L + q] = (unsigned long long)v2;
-                    sum[2 * LL + t * L + q] = (unsigned long long)v3;
-                }
+            if (lane < L) {
+                sum[t * L + lane] = (unsigned long long)s1;
+                sum[LL + t * L + lane] = (unsigned long long)s2;
+                sum[2 * LL + t * L + lane] = (unsigned long long)s3;
             }
         }
     }
@@ -1855,12 +1971,20 @@ static void ensure_t_sizes(Graph &G, cudaStream_t s) {
     }
 }
 
-// degree-priority wedges of the anchors of one chunk into A
-// hubs counted together: as many tables as fit the L2 share hub_l2_mb
-static int64_t hub_group_max(const Graph &G) {
-    const int64_t per = std::max<int64_t>(G.max_graph_nodes, 1) * G.L * (int64_t)sizeof(uint32_t);
-    return std::max<int64_t>(((int64_t)G.opt.hub_l2_mb << 20) / per, 1);
+// words of one hub's counter table (one row of L counters per node of its graph)
+static int64_t hub_words_per_table(const Graph &G) {
+    const int64_t rw = G.hub_packed ? (G.L + 1) / 2 : G.L;
+    return std::max<int64_t>(G.max_graph_nodes, 1) * rw;
 }
+
+// hubs of one group: their tables fill at most half of hub_l2_mb (the
+// persistent pass fills one group's tables while it reads the previous one's)
+static int64_t hub_group_max(const Graph &G) {
+    const int64_t per = hub_words_per_table(G) * (int64_t)sizeof(uint32_t);
+    return std::max<int64_t>(((int64_t)G.opt.hub_l2_mb << 20) / 2 / per, 1);
+}
+
+constexpr int kHubCtasPerSm = 5;                            // k_wedge_hub's launch bounds
 
 template <class T>
 static void exclusive_sum(const T *in, T *out, int64_t n, cudaStream_t s) {
@@ -1940,44 +2064,126 @@ static void prepare_hubs(Graph &G, cudaStream_t s) {
     G.hubs_ready = true;
 }
 
-// The hubs of chunk c, in groups of at most hub_group_max tables (and about
-// 2^22 wedges): phases 0 and 1 of k_wedge_hub per group, then the group's
-// tables are cleared by phase 2 or, when the group touches a large part of
-// them, by one memset.
-static int64_t launch_hubs(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
-    const int64_t hb0 = std::lower_bound(G.h_hub_id.begin(), G.h_hub_id.end(), (int32_t)c.n0) - G.h_hub_id.begin();
-    const int64_t hb1 = std::lower_bound(G.h_hub_id.begin(), G.h_hub_id.end(), (int32_t)std::min<int64_t>(c.n1, INT32_MAX)) -
-                        G.h_hub_id.begin();
-    const int64_t gmax = std::min<int64_t>(hub_group_max(G), G.n_tables);
-    const int64_t table_bytes = G.table_stride * (int64_t)sizeof(uint32_t);
+// Ticket queues of the persistent hub pass, one per chunk (graph invariant,
+// built before any capture): hubs in groups of at most hub_group_max tables
+// and about 2^22 wedges; per group, fill and read tickets of at least 2 per
+// CTA of the launch (1,024 to 8,192 wedges each) and clear tickets (zeroing
+// the group's table words when that is cheaper than walking its wedges
+// again).  Queue order: the clears of group s - 2, the reads of group s - 1,
+// the fills of group s, for s = 0, 1, ...: every ticket waits on tickets at
+// least one phase of another group earlier in the queue.
+static void plan_hubs(Graph &G, cudaStream_t s) {
+    const int64_t ctas = (int64_t)sm_count() * kHubCtasPerSm;
+    G.hub_packed = G.max_degree < 65536;
+    G.hub_stride = hub_words_per_table(G);
+    const int64_t gmax = hub_group_max(G);
+    G.hub_buf_words = gmax * G.hub_stride;
+    const size_t tbytes = sizeof(uint32_t) * (size_t)(kHubBuffers * G.hub_buf_words);
+    G.hub_tables.alloc(tbytes);
+    TG_CK(cudaMemsetAsync(G.hub_tables.p, 0, tbytes, s));
+    G.hub_plans.clear();
+    for (const Graph::Chunk &c : G.chunks) {
+        auto plan = std::make_unique<Graph::HubPlan>();
+        for (DBuf *d : {&plan->segs, &plan->groups, &plan->ntick, &plan->ctr}) d->owner = &G.stream;
+        const int64_t hb0 = std::lower_bound(G.h_hub_id.begin(), G.h_hub_id.end(), (int32_t)c.n0) - G.h_hub_id.begin();
+        const int64_t hb1 = std::lower_bound(G.h_hub_id.begin(), G.h_hub_id.end(),
+                                             (int32_t)std::min<int64_t>(c.n1, INT32_MAX)) - G.h_hub_id.begin();
+        std::vector<HubGroup> &groups = plan->h_groups;
+        std::vector<int64_t> &ntick = plan->h_ntick;
+        for (int64_t h = hb0; h < hb1;) {
+            int64_t h1 = h, wsum = 0;
+            while (h1 < hb1 && h1 - h < gmax && wsum < ((int64_t)1 << 22)) wsum += G.h_hub_wedges[h1++];
+            const int64_t w0 = G.h_hub_woff[h], w1 = G.h_hub_woff[h1];
+            if (w1 > w0) {
+                HubGroup gr;
+                gr.i0 = G.h_hub_item[h];
+                gr.i1 = G.h_hub_item[h1];
+                gr.w0 = w0;
+                gr.w1 = w1;
+                gr.tw = std::min<int64_t>(std::max<int64_t>((wsum / (2 * ctas) + 255) & ~(int64_t)255, 1024), 8192);
+                gr.zwords = (h1 - h) * G.hub_stride;
+                gr.h0 = (int32_t)h;
+                gr.buf = (int32_t)(groups.size() % kHubBuffers);
+                const int64_t nw = (w1 - w0 + gr.tw - 1) / gr.tw;
+                const bool zero = gr.zwords * (int64_t)sizeof(uint32_t) <= 32 * wsum;
+                ntick.push_back(nw);                                                     // fill
+                ntick.push_back(nw);                                                     // read
+                ntick.push_back(zero ? 0 : nw);                                          // clear by walking
+                ntick.push_back(zero ? (gr.zwords + kHubTicketWords - 1) / kHubTicketWords : 0);   // clear by zeroing
+                groups.push_back(gr);
+            }
+            h = h1;
+        }
+        const int64_t ng = (int64_t)groups.size();
+        std::vector<HubSegment> &segs = plan->h_segs;
+        int64_t nt = 0;
+        for (int64_t st = 0; st < ng + 2; ++st) {
+            auto emit = [&](int64_t q, int kind) {
+                if (q < 0 || q >= ng || ntick[q * kHubKinds + kind] == 0) return;
+                segs.push_back(HubSegment{nt, (int32_t)q, kind});
+                nt += ntick[q * kHubKinds + kind];
+            };
+            emit(st - 2, 2);
+            emit(st - 2, 3);
+            emit(st - 1, 1);
+            emit(st, 0);
+        }
+        // every run waits only on runs queued before it (so each wait ends:
+        // those tickets were taken by running CTAs)
+        {
+            std::vector<int64_t> pos((size_t)std::max<int64_t>(ng * kHubKinds, 1), -1);
+            for (int64_t k = 0; k < (int64_t)segs.size(); ++k) pos[(size_t)(segs[k].group * kHubKinds + segs[k].kind)] = k;
+            for (int64_t k = 0; k < (int64_t)segs.size(); ++k) {
+                const int64_t q = segs[k].group;
+                const int kind = segs[k].kind;
+                int64_t dep[2] = {-1, -1};
+                if (kind == 1) dep[0] = q * kHubKinds;
+                else if (kind >= 2) dep[0] = q * kHubKinds + 1;
+                else if (q >= kHubBuffers) { dep[0] = (q - kHubBuffers) * kHubKinds + 2; dep[1] = dep[0] + 1; }
+                for (int64_t d : dep)
+                    if (d >= 0 && pos[(size_t)d] >= k) throw Error{TG_ERR_INTERNAL, "hub ticket order"};
+            }
+        }
+        plan->n_groups = ng;
+        plan->n_segs = (int64_t)segs.size();
+        plan->n_tickets = nt;
+        if (ng > 0) {
+            plan->segs.alloc(sizeof(HubSegment) * segs.size());
+            plan->groups.alloc(sizeof(HubGroup) * groups.size());
+            plan->ntick.alloc(sizeof(int64_t) * ntick.size());
+            plan->ctr.alloc(sizeof(unsigned long long) * (size_t)(1 + ng * kHubKinds));
+            TG_CK(cudaMemcpyAsync(plan->segs.p, segs.data(), sizeof(HubSegment) * segs.size(), cudaMemcpyHostToDevice, s));
+            TG_CK(cudaMemcpyAsync(plan->groups.p, groups.data(), sizeof(HubGroup) * groups.size(),
+                                  cudaMemcpyHostToDevice, s));
+            TG_CK(cudaMemcpyAsync(plan->ntick.p, ntick.data(), sizeof(int64_t) * ntick.size(), cudaMemcpyHostToDevice,
+                                  s));
+        }
+        G.hub_plans.push_back(std::move(plan));
+    }
+}
+
+// The hubs of chunk ci: one persistent launch over the chunk's tickets.
+static int64_t launch_hubs(Graph &G, size_t ci, cudaStream_t s) {
+    Graph::HubPlan &P = *G.hub_plans[ci];
+    if (P.n_tickets == 0) return 0;
+    TG_CK(cudaMemsetAsync(P.ctr.p, 0, sizeof(unsigned long long) * (size_t)(1 + P.n_groups * kHubKinds), s));
     const GraphView gv = G.view();
     const CountView cv = G.cview();
     const HubView hv = hub_view(G);
-    const int grid = sm_count() * 6;                        // 40 registers: 6 CTAs of 256 per SM
-    int64_t launches = 0;
+    const int grid = sm_count() * kHubCtasPerSm;
     KernelTimer kt(G, s, "k_wedge_hub");
-    for (int64_t h = hb0; h < hb1;) {
-        int64_t h1 = h, wsum = 0;
-        while (h1 < hb1 && h1 - h < gmax && wsum < ((int64_t)1 << 22)) wsum += G.h_hub_wedges[h1++];
-        const int64_t i0 = G.h_hub_item[h], i1 = G.h_hub_item[h1];
-        const int64_t w0 = G.h_hub_woff[h], w1 = G.h_hub_woff[h1];
-        if (w1 > w0) {
-            for (int phase = 0; phase < 2; ++phase) {
-                k_wedge_hub<<<grid, kHubThreads, 0, s>>>(gv, cv, hv, i0, i1, w0, w1, (int32_t)h, phase);
-                ++launches;
-            }
-            const int64_t zbytes = (h1 - h) * table_bytes;
-            if (zbytes <= 32 * wsum) {
-                TG_CK(cudaMemsetAsync(G.tables.p, 0, (size_t)zbytes, s));
-            } else {
-                k_wedge_hub<<<grid, kHubThreads, 0, s>>>(gv, cv, hv, i0, i1, w0, w1, (int32_t)h, 2);
-                ++launches;
-            }
-            TG_CK(cudaGetLastError());
-        }
-        h = h1;
-    }
-    return launches;
+    if (G.hub_packed)
+        k_wedge_hub<true><<<grid, kHubThreads, 0, s>>>(gv, cv, hv, P.segs.as<HubSegment>(), P.n_segs, P.n_tickets,
+                                                       P.groups.as<HubGroup>(), P.ntick.as<int64_t>(),
+                                                       P.ctr.as<unsigned long long>(), G.hub_tables.as<uint32_t>(),
+                                                       G.hub_buf_words, G.hub_stride);
+    else
+        k_wedge_hub<false><<<grid, kHubThreads, 0, s>>>(gv, cv, hv, P.segs.as<HubSegment>(), P.n_segs, P.n_tickets,
+                                                        P.groups.as<HubGroup>(), P.ntick.as<int64_t>(),
+                                                        P.ctr.as<unsigned long long>(), G.hub_tables.as<uint32_t>(),
+                                                        G.hub_buf_words, G.hub_stride);
+    TG_CK(cudaGetLastError());
+    return 1;
 }
 
 static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
@@ -1999,7 +2205,7 @@ static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
             gv, cv, G.anchors_light.as<int32_t>(), G.n_anchors_light, cap, c.n0, c.n1);
         ++launches;
     }
-    if (G.n_hubs > 0) launches += launch_hubs(G, c, s);
+    if (G.n_hubs > 0) launches += launch_hubs(G, (size_t)(&c - G.chunks.data()), s);
     if (G.n_anchors_heavy > 0) {
         KernelTimer kt(G, s, "k_wedge_heavy");
         k_wedge_heavy<<<G.n_tables, kAnchorThreads, (size_t)kHeavyCap * (1 + L) * sizeof(int32_t), s>>>(
@@ -2097,11 +2303,12 @@ void prepare_counting(Graph &G, int k, cudaStream_t s) {
             G.scan_tmp_bytes = tb;
         }
         if (G.n_hubs > 0 && !G.hubs_ready) prepare_hubs(G, s);
-        if ((G.n_anchors_heavy > 0 || G.n_hubs > 0) && G.n_tables == 0) {
+        if (G.n_hubs > 0 && G.hub_plans.empty()) plan_hubs(G, s);
+        if (G.n_anchors_heavy > 0 && G.n_tables == 0) {
             const int64_t stride = std::max<int64_t>(G.max_graph_nodes, 1) * L;
             const int64_t per = stride * (int64_t)sizeof(uint32_t);
             int64_t budget = (int64_t)G.opt.anchor_table_budget_mb << 20;
-            const int64_t need = std::max<int64_t>(G.n_anchors_heavy, G.n_hubs > 0 ? hub_group_max(G) : 0);
+            const int64_t need = G.n_anchors_heavy;
             int64_t nt = std::min<int64_t>({(int64_t)2 * sm_count(), need, std::max<int64_t>(budget / per, 1)});
             G.tables.alloc((size_t)(nt * per));
             TG_CK(cudaMemsetAsync(G.tables.p, 0, (size_t)(nt * per), s));

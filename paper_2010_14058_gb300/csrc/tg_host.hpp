@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -142,6 +143,19 @@ struct Graph {
     std::vector<int64_t> h_hub_item;    // first item of each hub (n_hubs + 1)
     std::vector<int64_t> h_hub_woff;    // first wedge of each hub (n_hubs + 1)
     bool hubs_ready = false;
+    // persistent hub pass (tg_count.cu): per chunk, its ticket queue; the
+    // table buffers shared by all chunks
+    struct HubPlan {
+        DBuf segs, groups, ntick, ctr;
+        std::vector<HubGroup> h_groups;     // host copies (kept while the uploads may be in flight)
+        std::vector<HubSegment> h_segs;
+        std::vector<int64_t> h_ntick;       // tickets per (group, kind)
+        int64_t n_tickets = 0, n_groups = 0, n_segs = 0;
+    };
+    std::vector<std::unique_ptr<HubPlan>> hub_plans;
+    DBuf hub_tables;
+    int64_t hub_stride = 0, hub_buf_words = 0;  // words per hub table, per buffer
+    bool hub_packed = false;                    // two 16-bit counters per word
     // counting state
     DBuf C, tau, A, tables, gacc, status, tiles_full, stage_pe, stage_gl;
     DBuf tcount, toffs, tlist, tsum, kmat, big_list, big_count, scan_tmp, set_scratch;
@@ -226,7 +240,7 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch, &work, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
+                             &set_scratch, &work, &hub_tables, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
                 &pa_cls, &pa_gacc};
     }
     int64_t device_bytes() const {

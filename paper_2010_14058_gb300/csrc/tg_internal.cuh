@@ -35,6 +35,23 @@ constexpr int kHeavyCap = 4096;                    // shared-memory hash rows of
 enum : int { kWorkCliqueProbes = 0, kWorkCliqueSearches = 1, kWorkCliqueBigProbes = 2, kWorkSlots = 8 };
 constexpr int kHeavyFit = kHeavyCap / 4 * 3;       // its load limit (distinct wedge ends)
 
+// Persistent hub pass (tg_count.cu): a group of hubs whose counter tables
+// share one table buffer, and the ticket queue as runs of tickets of one
+// (group, kind) in queue order; kinds 0 fill, 1 read, 2 clear by walking the
+// wedges, 3 clear by zeroing the group's table words.
+struct HubGroup {
+    int64_t i0, i1;             // items
+    int64_t w0, w1;             // wedges
+    int64_t tw;                 // wedges per fill / read / walk-clear ticket
+    int64_t zwords;             // table words of the group (zeroing tickets: kHubTicketWords each)
+    int32_t h0, buf;            // first hub, table buffer
+};
+struct HubSegment {
+    int64_t t0;                 // first ticket of the run
+    int32_t group, kind;
+};
+constexpr int64_t kHubTicketWords = 1 << 16;
+
 // Read-only view of a built graph, passed to kernels by value.
 struct GraphView {
     int32_t ngraphs;
