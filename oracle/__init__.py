@@ -12,7 +12,9 @@ Three independent routes over the same output layout (see oracle.c):
 
 :func:`weights` gives the typed-graphlet weighted graph W and degree D of
 Alg. 5 by direct enumeration; :func:`position_aware` the position-aware
-typed counts of Sec. 5 (Def. 8), per edge and global.
+typed counts of Sec. 5 (Def. 8), per edge and global; :func:`directed3`
+and :func:`directed3_brute` the directed typed 3-node graphlets of Sec. 4.8
+(oriented graphs given by their out-neighbour CSR).
 
 All counts are exact int64.  Parity with these is the acceptance bar for
 the GPU path (bit-exact).
@@ -72,6 +74,12 @@ _SIGS = {
     "oracle_position_aware": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_position_aware_brute": ("i64 vp vp vp i32 vp", "i32"),
     "oracle_max_threads": ("", "i32"),
+    "oracle_directed_classes": ("i32", "i64"),
+    "oracle_directed_global_slots": ("i32", "i64"),
+    "oracle_directed_class": ("i32 vp vp", "i64"),
+    "oracle_directed3": ("i64 vp vp vp i32 vp vp", "i32"),
+    "oracle_directed3_brute": ("i64 vp vp vp i32 vp vp", "i32"),
+    "oracle_directed_edges": ("i64 vp vp vp i32 vp vp vp", "i32"),
     "oracle_graph_open": ("i64 vp vp vp i32 vp", "vp"),
     "oracle_graph_close": ("vp", "i32"),
     "oracle_graph_paper_edges": ("vp i32 vp i64 vp vp vp i32", "i32"),
@@ -261,6 +269,72 @@ def position_aware_brute(g, lib=None):
     gl = np.zeros(int(lib.oracle_pa_global_slots(g["L"])), dtype=np.int64)
     _check(lib.oracle_position_aware_brute(g["n"], _p(rp), _p(col), _p(ty), g["L"], _p(gl)))
     return gl
+
+
+# ---------------------------------------------------- directed (Sec. 4.8)
+
+def _dargs(g):
+    rp = np.ascontiguousarray(g["out_row_ptr"], dtype=np.int64)
+    col = np.ascontiguousarray(g["out_col"], dtype=np.int32)
+    ty = np.ascontiguousarray(g["types"], dtype=np.uint8)
+    return rp, col, ty
+
+
+def directed_classes(L: int, lib=None) -> int:
+    """Number of connected directed typed 3-node graphlets (isomorphism classes)."""
+    lib = lib or _load()
+    return int(lib.oracle_directed_classes(L))
+
+
+def directed_global_slots(L: int, lib=None) -> int:
+    lib = lib or _load()
+    return int(lib.oracle_directed_global_slots(L))
+
+
+def directed_class(L: int, types, arcs, lib=None) -> int:
+    """Class rank of the configuration (types of nodes 0,1,2; arc states of
+    pairs (0,1), (0,2), (1,2): 0 none, 1 lower -> higher, 2 higher -> lower),
+    -1 when it is not connected."""
+    lib = lib or _load()
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    a = np.ascontiguousarray(arcs, dtype=np.int32)
+    return int(lib.oracle_directed_class(L, _p(t), _p(a)))
+
+
+def directed_edges(g, lib=None):
+    """(src, dst, orientation) of the underlying undirected edges in edge-id
+    order (src < dst); orientation 0: src -> dst, 1: dst -> src."""
+    lib = lib or _load()
+    rp, col, ty = _dargs(g)
+    m = int(rp[-1])
+    s = np.empty(m, dtype=np.int64)
+    d = np.empty(m, dtype=np.int64)
+    o = np.empty(m, dtype=np.int8)
+    _check(lib.oracle_directed_edges(g["n"], _p(rp), _p(col), _p(ty), g["L"], _p(s), _p(d), _p(o)))
+    return s, d, o
+
+
+def _directed(fn, g, per_edge, lib):
+    rp, col, ty = _dargs(g)
+    L = g["L"]
+    m = int(rp[-1])
+    pe = np.zeros((m, 8 * L), dtype=np.int64) if per_edge else None
+    gl = np.zeros(directed_global_slots(L, lib), dtype=np.int64)
+    _check(fn(g["n"], _p(rp), _p(col), _p(ty), L, _p(pe), _p(gl)))
+    return pe, gl
+
+
+def directed3(g, per_edge: bool = True, lib=None):
+    """Alg. 1 with the typed sets split by direction (Sec. 4.8) ->
+    (per_edge int64 [m, 8L] or None, global int64 [L^2 + classes])."""
+    lib = lib or _load()
+    return _directed(lib.oracle_directed3, g, per_edge, lib)
+
+
+def directed3_brute(g, per_edge: bool = True, lib=None):
+    """Every 3-node subset of a small oriented graph -> same layout as directed3."""
+    lib = lib or _load()
+    return _directed(lib.oracle_directed3_brute, g, per_edge, lib)
 
 
 class OpenGraph:

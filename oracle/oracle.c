@@ -1251,3 +1251,323 @@ int oracle_position_aware_brute(int64_t n, const int64_t *row_ptr, const int32_t
     graph_close(&G);
     return rc;
 }
+
+/* ------------------------------------------- directed typed 3-node graphlets
+ *
+ * Sec. 4.8: in a directed graph every typed neighbourhood Gamma_i^t splits
+ * into the typed out-neighbours Gamma_i^{t,+} and in-neighbours
+ * Gamma_i^{t,-}, and so do T_ij^t, S_i^t and S_j^t.  The split is a
+ * partition, so the input is an oriented graph: arcs u -> v given as an
+ * out-neighbour CSR, no self-loops, no repeated arcs and no reciprocal pair
+ * (u -> v together with v -> u).
+ *
+ * Per edge {i, j} of the underlying undirected graph (edge ids as above:
+ * i < j, lexicographic), 8L slots, block b at b*L + t (t = type of the
+ * third node w; the sign is the direction of the arc between the endpoint
+ * and w, + when the endpoint is its tail):
+ *   0 S_i^{t,+}   1 S_i^{t,-}   2 S_j^{t,+}   3 S_j^{t,-}
+ *   4 T^{t}(+,+)  5 T^{t}(+,-)  6 T^{t}(-,+)  7 T^{t}(-,-)   (sign at i, sign at j)
+ * Global: block 0, directed typed edges (type of tail, type of head), L^2
+ * slots at tail*L + head; block 1, the connected directed typed 3-node
+ * graphlets, one slot per isomorphism class, ranked by canonical code.
+ * A labelled configuration on nodes 0, 1, 2 is the code (t0, t1, t2, a01,
+ * a02, a12) with a_xy = 0 (no arc), 1 (x -> y) or 2 (y -> x), read as one
+ * integer in mixed radix (L, L, L, 3, 3, 3); its class is represented by the
+ * smallest code over the 6 renumberings of the nodes. */
+
+static int64_t dir_code(int L, const int t[3], const int a[3]) {
+    return ((((int64_t)(t[0] * L + t[1]) * L + t[2]) * 3 + a[0]) * 3 + a[1]) * 3 + a[2];
+}
+
+/* arc state of pair (x, y), x != y, in a configuration: 0 none, 1 x -> y, 2 y -> x */
+static int dir_arc(const int a[3], int x, int y) {
+    int lo = x < y ? x : y, hi = x < y ? y : x;
+    int k = lo == 0 ? (hi == 1 ? 0 : 1) : 2;          /* pairs (0,1) (0,2) (1,2) */
+    int s = a[k];
+    if (s == 0 || x == lo) return s;
+    return 3 - s;
+}
+
+/* smallest code over the renumberings: new node q is old node p[q] */
+static int64_t dir_canonical(int L, const int t[3], const int a[3]) {
+    static const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    int64_t best = -1;
+    for (int k = 0; k < 6; ++k) {
+        const int *p = P[k];
+        int tt[3] = {t[p[0]], t[p[1]], t[p[2]]};
+        int aa[3] = {dir_arc(a, p[0], p[1]), dir_arc(a, p[0], p[2]), dir_arc(a, p[1], p[2])};
+        int64_t c = dir_code(L, tt, aa);
+        if (best < 0 || c < best) best = c;
+    }
+    return best;
+}
+
+/* sorted canonical codes of all connected classes (returns their number) */
+static int64_t dir_class_codes(int L, int64_t *codes) {
+    int64_t nc = 0;
+    for (int t0 = 0; t0 < L; ++t0) for (int t1 = 0; t1 < L; ++t1) for (int t2 = 0; t2 < L; ++t2)
+    for (int a0 = 0; a0 < 3; ++a0) for (int a1 = 0; a1 < 3; ++a1) for (int a2 = 0; a2 < 3; ++a2) {
+        int arcs = (a0 != 0) + (a1 != 0) + (a2 != 0);
+        if (arcs < 2) continue;                        /* 3 nodes are connected by 2 or 3 arcs */
+        int t[3] = {t0, t1, t2}, a[3] = {a0, a1, a2};
+        int64_t c = dir_code(L, t, a);
+        if (dir_canonical(L, t, a) != c) continue;     /* codes rise in loop order */
+        if (codes) codes[nc] = c;
+        ++nc;
+    }
+    return nc;
+}
+
+int64_t oracle_directed_classes(int L) {
+    if (L < 1 || L > OR_MAX_L) return -1;
+    return dir_class_codes(L, NULL);
+}
+
+int64_t oracle_directed_global_slots(int L) {
+    if (L < 1 || L > OR_MAX_L) return -1;
+    return (int64_t)L * L + dir_class_codes(L, NULL);
+}
+
+/* rank of the class of a labelled configuration, -1 if disconnected */
+static int64_t dir_rank(int L, const int64_t *codes, int64_t nc, const int t[3], const int a[3]) {
+    if ((a[0] != 0) + (a[1] != 0) + (a[2] != 0) < 2) return -1;
+    int64_t c = dir_canonical(L, t, a), lo = 0, hi = nc;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (codes[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return lo < nc && codes[lo] == c ? lo : -1;
+}
+
+int64_t oracle_directed_class(int L, const int32_t *t, const int32_t *a) {
+    if (L < 1 || L > OR_MAX_L) return -1;
+    int64_t nc = dir_class_codes(L, NULL);
+    int64_t *codes = (int64_t *)malloc((size_t)nc * sizeof(int64_t));
+    if (!codes) return -1;
+    dir_class_codes(L, codes);
+    int tt[3] = {t[0], t[1], t[2]}, aa[3] = {a[0], a[1], a[2]};
+    int64_t r = dir_rank(L, codes, nc, tt, aa);
+    free(codes);
+    return r;
+}
+
+typedef struct {
+    int64_t n, m;
+    int L;
+    const uint8_t *phi;
+    int64_t *rp;                /* symmetric rows, sorted by neighbour id */
+    int32_t *adj;
+    int8_t *sg;                 /* +1: the row node is the arc's tail, -1: its head */
+    int64_t *eu, *ev;           /* edges u < v, lexicographic */
+    int8_t *eo;                 /* 0: arc eu -> ev, 1: arc ev -> eu */
+} dgraph_t;
+
+static void dgraph_close(dgraph_t *D) { free(D->rp); free(D->adj); free(D->sg); free(D->eu); free(D->ev); free(D->eo); }
+
+typedef struct { int32_t v; int8_t s; } dent_t;
+static int cmp_dent(const void *x, const void *y) {
+    int32_t a = ((const dent_t *)x)->v, b = ((const dent_t *)y)->v;
+    return (a > b) - (a < b);
+}
+
+static int dgraph_open(dgraph_t *D, int64_t n, const int64_t *orp, const int32_t *ocol, const uint8_t *phi, int L) {
+    memset(D, 0, sizeof(*D));
+    if (n < 0 || L < 1 || L > OR_MAX_L) return ERR_ARG;
+    int64_t na = orp[n];
+    if (orp[0] != 0 || na < 0) return ERR_GRAPH;
+    for (int64_t v = 0; v < n; ++v) if (orp[v + 1] < orp[v] || phi[v] >= L) return ERR_GRAPH;
+    for (int64_t k = 0; k < na; ++k) if (ocol[k] < 0 || ocol[k] >= n) return ERR_GRAPH;
+    D->n = n; D->m = na; D->L = L; D->phi = phi;
+    D->rp = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    D->adj = (int32_t *)malloc((size_t)(2 * na > 0 ? 2 * na : 1) * sizeof(int32_t));
+    D->sg = (int8_t *)malloc((size_t)(2 * na > 0 ? 2 * na : 1));
+    D->eu = (int64_t *)malloc((size_t)(na > 0 ? na : 1) * sizeof(int64_t));
+    D->ev = (int64_t *)malloc((size_t)(na > 0 ? na : 1) * sizeof(int64_t));
+    D->eo = (int8_t *)malloc((size_t)(na > 0 ? na : 1));
+    dent_t *tmp = (dent_t *)malloc((size_t)(2 * na > 0 ? 2 * na : 1) * sizeof(dent_t));
+    int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!D->rp || !D->adj || !D->sg || !D->eu || !D->ev || !D->eo || !tmp || !fill) { free(tmp); free(fill); return ERR_MEM; }
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t k = orp[u]; k < orp[u + 1]; ++k) { D->rp[u + 1]++; D->rp[ocol[k] + 1]++; }
+    for (int64_t v = 0; v < n; ++v) D->rp[v + 1] += D->rp[v];
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t k = orp[u]; k < orp[u + 1]; ++k) {
+            int64_t v = ocol[k];
+            if (v == u) { free(tmp); free(fill); return ERR_GRAPH; }                 /* self-loop */
+            tmp[D->rp[u] + fill[u]++] = (dent_t){(int32_t)v, 1};
+            tmp[D->rp[v] + fill[v]++] = (dent_t){(int32_t)u, -1};
+        }
+    int rc = OK;
+    int64_t e = 0;
+    for (int64_t u = 0; u < n && rc == OK; ++u) {
+        qsort(tmp + D->rp[u], (size_t)(D->rp[u + 1] - D->rp[u]), sizeof(dent_t), cmp_dent);
+        for (int64_t k = D->rp[u]; k < D->rp[u + 1]; ++k) {
+            if (k > D->rp[u] && tmp[k - 1].v == tmp[k].v) { rc = ERR_GRAPH; break; }  /* repeated or reciprocal */
+            D->adj[k] = tmp[k].v;
+            D->sg[k] = tmp[k].s;
+            if (tmp[k].v > u) { D->eu[e] = u; D->ev[e] = tmp[k].v; D->eo[e] = tmp[k].s > 0 ? 0 : 1; ++e; }
+        }
+    }
+    free(tmp); free(fill);
+    if (rc == OK && e != na) rc = ERR_GRAPH;
+    return rc;
+}
+
+/* configuration of (i = 0, j = 1, w = 2) for an edge of orientation o and
+ * the third node's signs at i and j (0: not adjacent) */
+static void dir_config(int o, int si, int sj, int a[3]) {
+    a[0] = o == 0 ? 1 : 2;
+    a[1] = si == 0 ? 0 : (si > 0 ? 1 : 2);            /* i -> w when i is the tail */
+    a[2] = sj == 0 ? 0 : (sj > 0 ? 1 : 2);
+}
+
+/* per-edge slot block of a third node from its signs at i and j */
+static int dir_block(int si, int sj) {
+    if (si != 0 && sj != 0) return 4 + (si > 0 ? 0 : 2) + (sj > 0 ? 0 : 1);
+    if (si != 0) return si > 0 ? 0 : 1;
+    return sj > 0 ? 2 : 3;
+}
+
+/* Alg. 1 with the sets split by direction (Sec. 4.8): mark Gamma_i with
+ * the signs at i, scan Gamma_j, then the rest of Gamma_i.  per_edge_out:
+ * int64 [m][8L] or NULL; global_out: int64 [L^2 + classes] or NULL. */
+int oracle_directed3(int64_t n, const int64_t *out_row_ptr, const int32_t *out_col, const uint8_t *types, int L,
+                     int64_t *per_edge_out, int64_t *global_out) {
+    dgraph_t D;
+    int rc = dgraph_open(&D, n, out_row_ptr, out_col, types, L);
+    if (rc != OK) { dgraph_close(&D); return rc; }
+    const int64_t nc = dir_class_codes(L, NULL);
+    int64_t *codes = (int64_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int64_t));
+    int8_t *psi = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t *raw = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    if (!codes || !psi || !raw) { free(codes); free(psi); free(raw); dgraph_close(&D); return ERR_MEM; }
+    dir_class_codes(L, codes);
+    const int64_t S = 8 * (int64_t)L;
+    if (global_out) memset(global_out, 0, (size_t)(L * L + nc) * sizeof(int64_t));
+    int64_t row[8 * OR_MAX_L];
+    for (int64_t e = 0; e < D.m && rc == OK; ++e) {
+        const int64_t i = D.eu[e], j = D.ev[e];
+        const int o = D.eo[e];
+        memset(row, 0, sizeof(row));
+        for (int64_t k = D.rp[i]; k < D.rp[i + 1]; ++k) if (D.adj[k] != j) psi[D.adj[k]] = D.sg[k];
+        for (int64_t k = D.rp[j]; k < D.rp[j + 1]; ++k) {                  /* T and S_j */
+            int64_t w = D.adj[k];
+            if (w == i) continue;
+            int si = psi[w], sj = D.sg[k];
+            if (MUTANT(13) && si == 0) sj = -sj;                            /* planted: S_j signs flipped */
+            row[dir_block(si, sj) * L + types[w]] += 1;
+        }
+        for (int64_t k = D.rp[j]; k < D.rp[j + 1]; ++k) psi[D.adj[k]] = psi[D.adj[k]] ? 2 : 0;   /* 2: in T */
+        for (int64_t k = D.rp[i]; k < D.rp[i + 1]; ++k) {                  /* S_i */
+            int64_t w = D.adj[k];
+            if (w == j || psi[w] == 2) continue;
+            row[dir_block(D.sg[k], 0) * L + types[w]] += 1;
+        }
+        for (int64_t k = D.rp[i]; k < D.rp[i + 1]; ++k) psi[D.adj[k]] = 0;
+        for (int64_t k = D.rp[j]; k < D.rp[j + 1]; ++k) psi[D.adj[k]] = 0;
+        if (per_edge_out) memcpy(per_edge_out + e * S, row, (size_t)S * sizeof(int64_t));
+        if (global_out) {
+            const int tail = types[o == 0 ? i : j], head = types[o == 0 ? j : i];
+            global_out[tail * L + head] += 1;
+            for (int b = 0; b < 8; ++b)
+                for (int t = 0; t < L; ++t) {
+                    int64_t v = row[b * L + t];
+                    if (!v) continue;
+                    int si = b < 2 ? (b == 0 ? 1 : -1) : (b < 4 ? 0 : (b < 6 ? 1 : -1));
+                    int sj = b < 2 ? 0 : (b < 4 ? (b == 2 ? 1 : -1) : ((b & 1) ? -1 : 1));
+                    int a[3], tt[3] = {types[i], types[j], t};
+                    dir_config(MUTANT(14) ? 0 : o, si, sj, a);                /* planted: orientation dropped */
+                    int64_t r = dir_rank(L, codes, nc, tt, a);
+                    if (r < 0) { rc = ERR_REMAINDER; break; }
+                    raw[r] += v;
+                }
+        }
+    }
+    if (global_out && rc == OK)
+        for (int64_t r = 0; r < nc; ++r) {
+            /* a path is seen from its 2 arcs, a triangle from its 3 */
+            int64_t c = codes[r];
+            int a2 = (int)(c % 3), a1 = (int)(c / 3 % 3), a0 = (int)(c / 9 % 3);
+            int arcs = (a0 != 0) + (a1 != 0) + (a2 != 0);
+            if (raw[r] % arcs) { rc = ERR_REMAINDER; break; }
+            global_out[L * L + r] = raw[r] / arcs;
+        }
+    free(codes); free(psi); free(raw);
+    dgraph_close(&D);
+    return rc;
+}
+
+/* Every 3-node subset: its induced arcs; a connected one adds 1 to its class
+ * and, for each of its arcs, to the slot of that edge keyed by the third
+ * node.  Small graphs only. */
+int oracle_directed3_brute(int64_t n, const int64_t *out_row_ptr, const int32_t *out_col, const uint8_t *types, int L,
+                           int64_t *per_edge_out, int64_t *global_out) {
+    dgraph_t D;
+    int rc = dgraph_open(&D, n, out_row_ptr, out_col, types, L);
+    if (rc != OK) { dgraph_close(&D); return rc; }
+    const int64_t nc = dir_class_codes(L, NULL);
+    int64_t *codes = (int64_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int64_t));
+    if (!codes) { dgraph_close(&D); return ERR_MEM; }
+    dir_class_codes(L, codes);
+    const int64_t S = 8 * (int64_t)L;
+    if (per_edge_out) memset(per_edge_out, 0, (size_t)(D.m * S) * sizeof(int64_t));
+    if (global_out) memset(global_out, 0, (size_t)(L * L + nc) * sizeof(int64_t));
+    for (int64_t e = 0; e < D.m; ++e)
+        if (global_out) {
+            const int64_t i = D.eu[e], j = D.ev[e];
+            const int tail = types[D.eo[e] == 0 ? i : j], head = types[D.eo[e] == 0 ? j : i];
+            global_out[tail * L + head] += 1;
+        }
+    for (int64_t x = 0; x < n && rc == OK; ++x)
+        for (int64_t y = x + 1; y < n && rc == OK; ++y)
+            for (int64_t z = y + 1; z < n && rc == OK; ++z) {
+                int64_t v[3] = {x, y, z};
+                int s[3][3] = {{0}};
+                for (int p = 0; p < 3; ++p)
+                    for (int q = 0; q < 3; ++q)
+                        if (p != q) {
+                            int64_t lo = D.rp[v[p]], hi = D.rp[v[p] + 1];
+                            while (lo < hi) {
+                                int64_t mid = (lo + hi) / 2;
+                                if (D.adj[mid] < v[q]) lo = mid + 1; else hi = mid;
+                            }
+                            if (lo < D.rp[v[p] + 1] && D.adj[lo] == v[q]) s[p][q] = D.sg[lo];
+                        }
+                int t[3] = {types[x], types[y], types[z]};
+                int a[3] = {s[0][1] == 0 ? 0 : (s[0][1] > 0 ? 1 : 2), s[0][2] == 0 ? 0 : (s[0][2] > 0 ? 1 : 2),
+                            s[1][2] == 0 ? 0 : (s[1][2] > 0 ? 1 : 2)};
+                int64_t r = dir_rank(L, codes, nc, t, a);
+                if (r < 0) continue;                                      /* disconnected */
+                if (global_out) global_out[L * L + r] += 1;
+                if (!per_edge_out) continue;
+                for (int p = 0; p < 3; ++p)
+                    for (int q = p + 1; q < 3; ++q) {
+                        if (!s[p][q]) continue;
+                        int w = 3 - p - q;                                /* v[p] < v[q]: i = v[p], j = v[q] */
+                        int64_t lo = 0, hi = D.m;
+                        while (lo < hi) {
+                            int64_t mid = (lo + hi) / 2;
+                            if (D.eu[mid] < v[p] || (D.eu[mid] == v[p] && D.ev[mid] < v[q])) lo = mid + 1; else hi = mid;
+                        }
+                        per_edge_out[lo * S + dir_block(s[p][w], s[q][w]) * L + t[w]] += 1;
+                    }
+            }
+    free(codes);
+    dgraph_close(&D);
+    return rc;
+}
+
+/* Edges of the underlying undirected graph in edge-id order (u < v) and
+ * their orientation (0: u -> v, 1: v -> u). */
+int oracle_directed_edges(int64_t n, const int64_t *out_row_ptr, const int32_t *out_col, const uint8_t *types, int L,
+                          int64_t *src, int64_t *dst, int8_t *orient) {
+    dgraph_t D;
+    int rc = dgraph_open(&D, n, out_row_ptr, out_col, types, L);
+    if (rc == OK) {
+        memcpy(src, D.eu, (size_t)D.m * sizeof(int64_t));
+        memcpy(dst, D.ev, (size_t)D.m * sizeof(int64_t));
+        memcpy(orient, D.eo, (size_t)D.m);
+    }
+    dgraph_close(&D);
+    return rc;
+}

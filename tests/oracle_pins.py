@@ -378,3 +378,167 @@ def merge_pa_global(L, gl_pa):
             out[sum(typed_sizes[:b]) + ms_rank[tuple(sorted(rep))]] += gl_pa[s + r]
         s += sizes[b]
     return out
+
+
+# ------------------------------------------------- directed graphs (Sec. 4.8)
+
+def oriented_graph(n, arcs, types, L):
+    """Out-neighbour CSR of an oriented graph from its arcs (u, v) = u -> v."""
+    rp = np.zeros(n + 1, dtype=np.int64)
+    for u, _ in arcs:
+        rp[u + 1] += 1
+    rp = np.cumsum(rp)
+    col = np.zeros(len(arcs), dtype=np.int32)
+    fill = rp[:-1].copy()
+    for u, v in arcs:
+        col[fill[u]] = v
+        fill[u] += 1
+    return {"n": n, "L": L, "out_row_ptr": rp, "out_col": col, "types": np.asarray(types, dtype=np.uint8),
+            "m": len(arcs)}
+
+
+def random_oriented(n, p, L, seed, tournament=False):
+    rng = np.random.default_rng(seed)
+    arcs = []
+    for a in range(n):
+        for b in range(a + 1, n):
+            if tournament or rng.random() < p:
+                arcs.append((a, b) if rng.random() < 0.5 else (b, a))
+    return oriented_graph(n, arcs, rng.integers(0, L, n), L)
+
+
+def underlying(g):
+    """The undirected graph of an oriented graph (symmetric CSR)."""
+    arcs = [(u, int(v)) for u in range(g["n"]) for v in g["out_col"][g["out_row_ptr"][u]:g["out_row_ptr"][u + 1]]]
+    return graph_from_edges(g["n"], arcs, g["types"], g["L"])
+
+
+def directed_burnside(L):
+    """Connected oriented 3-node graphs with L node types up to isomorphism:
+    (1/6)(20 L^3 + 3 * 2 L^2 + 2 * 2 L) -- identity: 20 connected arc
+    patterns; a transposition fixes 2 patterns (no arc between the swapped
+    nodes, equal arcs to the third) with L^2 typings; a rotation fixes the
+    2 cyclic triangles with L typings."""
+    return (20 * L**3 + 6 * L**2 + 4 * L) // 6
+
+
+REVERSE_BLOCK = [1, 0, 3, 2, 7, 6, 5, 4]          # per-edge blocks under reversal of every arc
+
+
+def directed_class_maps(L, lib=None):
+    """For every class: its undirected graphlet (1 path, 2 triangle) and
+    sorted type triple, and the class of the reversed configuration."""
+    import oracle
+    nc = oracle.directed_classes(L, lib)
+    und, rev = [None] * nc, [None] * nc
+    for t in itertools.product(range(L), repeat=3):
+        for a in itertools.product(range(3), repeat=3):
+            r = oracle.directed_class(L, t, a, lib)
+            if r < 0:
+                continue
+            arcs = sum(x != 0 for x in a)
+            und[r] = (1 if arcs == 2 else 2, tuple(sorted(t)))
+            rev[r] = oracle.directed_class(L, t, [(0, 2, 1)[x] for x in a], lib)
+    return und, rev
+
+
+def directed_pins(lib=None):
+    """Names of the directed-graphlet pins that fail for an oracle build."""
+    import oracle
+    failed = []
+
+    def check(name, fn):
+        try:
+            if not fn():
+                failed.append(name)
+        except oracle.OracleError:
+            failed.append(name + " (error)")
+
+    check("class count = Burnside", lambda: all(oracle.directed_classes(L, lib) == directed_burnside(L)
+                                                   for L in range(1, 9)))
+    for seed in range(6):
+        L = [1, 2, 3][seed % 3]
+        g = random_oriented(7 + seed, 0.55, L, 700 + seed)
+
+        def vs_brute(g=g):
+            pe, gl = oracle.directed3(g, lib=lib)
+            pb, gb = oracle.directed3_brute(g, lib=lib)
+            return np.array_equal(pe, pb) and np.array_equal(gl, gb)
+        check(f"brute seed={seed}", vs_brute)
+
+        def sums_to_undirected(g=g, L=L):
+            pe, gl = oracle.directed3(g, lib=lib)
+            u = underlying(g)
+            pu, gu = oracle.paper(u, k=3, lib=lib)
+            rows = np.concatenate([pe[:, 0:4 * L].reshape(-1, 4, L).sum(1), pe[:, 4 * L:].reshape(-1, 4, L).sum(1)], 1)
+            und, _ = directed_class_maps(L, lib)
+            glob = np.zeros_like(gu)
+            tail_head = gl[:L * L].reshape(L, L)
+            for a in range(L):
+                for b in range(L):
+                    glob[oracle.multiset_rank(L, sorted((a, b)), lib)] += tail_head[a, b]
+            off3 = oracle.global_slots(L, 3, lib) - 2 * len(list(itertools.combinations_with_replacement(range(L), 3)))
+            n3 = len(list(itertools.combinations_with_replacement(range(L), 3)))
+            for r, v in enumerate(gl[L * L:]):
+                h, ts = und[r]
+                glob[off3 + (h - 1) * n3 + oracle.multiset_rank(L, list(ts), lib)] += v
+            return np.array_equal(rows, pu) and np.array_equal(glob, gu)
+        check(f"direction sums seed={seed}", sums_to_undirected)
+
+        def reversal(g=g, L=L):
+            pe, gl = oracle.directed3(g, lib=lib)
+            arcs = [(int(v), u) for u in range(g["n"]) for v in g["out_col"][g["out_row_ptr"][u]:g["out_row_ptr"][u + 1]]]
+            h = oriented_graph(g["n"], arcs, g["types"], L)
+            pr, gr = oracle.directed3(h, lib=lib)
+            want = pe.reshape(-1, 8, L)[:, REVERSE_BLOCK, :].reshape(pe.shape)
+            _, rev = directed_class_maps(L, lib)
+            wg = np.zeros_like(gl)
+            wg[:L * L] = gl[:L * L].reshape(L, L).T.ravel()
+            for r, v in enumerate(gl[L * L:]):
+                wg[L * L + rev[r]] += v
+            return np.array_equal(pr, want) and np.array_equal(gr, wg)
+        check(f"reversal seed={seed}", reversal)
+
+    def transitive_tournament():
+        n = 9
+        g = oriented_graph(n, [(a, b) for a in range(n) for b in range(a + 1, n)], [0] * n, 1)
+        pe, gl = oracle.directed3(g, lib=lib)
+        src, dst, _ = oracle.directed_edges(g, lib=lib)
+        want = np.zeros_like(pe)
+        for e, (i, j) in enumerate(zip(src, dst)):
+            want[e, 7] = i                 # w < i: w -> i and w -> j
+            want[e, 5] = j - i - 1         # i < w < j: i -> w, w -> j
+            want[e, 4] = n - 1 - j         # w > j: i -> w, j -> w
+        transitive = oracle.directed_class(1, [0, 0, 0], [1, 1, 1], lib)
+        wg = np.zeros_like(gl)
+        wg[0] = n * (n - 1) // 2
+        wg[1 + transitive] = n * (n - 1) * (n - 2) // 6
+        return np.array_equal(pe, want) and np.array_equal(gl, wg)
+    check("transitive tournament", transitive_tournament)
+
+    def cyclic_triangles():
+        # Kendall and Babington Smith: a tournament on n nodes has
+        # C(n,3) - sum_v C(out_v, 2) cyclic triangles
+        ok = True
+        for seed in range(3):
+            g = random_oriented(12, 1.0, 1, 800 + seed, tournament=True)
+            _, gl = oracle.directed3(g, per_edge=False, lib=lib)
+            outd = np.diff(g["out_row_ptr"])
+            cyc = oracle.directed_class(1, [0, 0, 0], [1, 2, 1], lib)
+            ok &= gl[1 + cyc] == 12 * 11 * 10 // 6 - sum(int(d) * (int(d) - 1) // 2 for d in outd)
+        return ok
+    check("cyclic triangles of tournaments", cyclic_triangles)
+
+    def stars():
+        k = 6
+        out = oriented_graph(k + 1, [(0, x) for x in range(1, k + 1)], [0] * (k + 1), 1)
+        inn = oriented_graph(k + 1, [(x, 0) for x in range(1, k + 1)], [0] * (k + 1), 1)
+        po, go = oracle.directed3(out, lib=lib)
+        pi, gi = oracle.directed3(inn, lib=lib)
+        out_star = oracle.directed_class(1, [0, 0, 0], [1, 1, 0], lib)   # 0 -> 1, 0 -> 2
+        in_star = oracle.directed_class(1, [0, 0, 0], [2, 2, 0], lib)
+        return ((po[:, 0] == k - 1).all() and po[:, 1:].sum() == 0 and (pi[:, 1] == k - 1).all()
+                and go[1 + out_star] == k * (k - 1) // 2 and gi[1 + in_star] == k * (k - 1) // 2
+                and go[1:].sum() == go[1 + out_star] and gi[1:].sum() == gi[1 + in_star])
+    check("directed stars", stars)
+    return failed

@@ -7,7 +7,9 @@ in Alg. 3, an unsorted type multiset, a missing 1/2 in Lemma 2, a lost
 exclusion of i and j in Alg. 2; in the weighted graph of Alg. 5, tailed
 triangles booked as 4-cycles and D missing one endpoint of each edge; in
 the position-aware counts of Sec. 5, the two sides of a 4-cycle key swapped
-and the degree-3 side of a tailed triangle swapped.  The pin battery here (closed forms,
+and the degree-3 side of a tailed triangle swapped; in the directed counts
+of Sec. 4.8, the signs of S_j flipped and the edge's own orientation
+dropped from the class key.  The pin battery here (closed forms,
 layout enumeration, the brute-force and networkx-free subset count) must
 reject every one of them, on the CPU.
 """
@@ -18,8 +20,9 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_pins import (BLOCK_EDGES, burnside, expected_clique, expected_complete_bipartite, expected_cycle,
-                         expected_star, global_slot_pa, graph_from_edges, multisets, random_graph, slot_instance)
+from oracle_pins import (BLOCK_EDGES, burnside, directed_pins, expected_clique, expected_complete_bipartite,
+                         expected_cycle, expected_star, global_slot_pa, graph_from_edges, multisets, random_graph,
+                         slot_instance)
 
 MUTANTS = {
     1: "Lemma 1 without the 4-cycle term",
@@ -34,6 +37,8 @@ MUTANTS = {
     10: "Alg. 5 degree adds each edge's weight to one endpoint only",
     11: "Sec. 5 4-cycle key (lo's neighbour, hi's neighbour) transposed",
     12: "Sec. 5 tailed-triangle edge at the degree-3 node booked on the other side",
+    13: "Sec. 4.8 S_j counted with the opposite arc direction",
+    14: "Sec. 4.8 class key without the edge's own orientation",
 }
 
 
@@ -116,6 +121,7 @@ def _battery(lib) -> list:
             return all(np.array_equal(raw[off[b]:off[b + 1]], BLOCK_EDGES[b] * gl[off[b]:off[b + 1]])
                        for b in range(9))
         check(f"position-aware seed={seed}", pa_sums)
+    failed += directed_pins(lib)
     return failed
 
 
