@@ -356,6 +356,64 @@ tg_status tg_set_timing(tg_graph *g, int32_t on);
 tg_status tg_get_timing(tg_graph *g, int32_t max, const char **names, double *ms, int64_t *launches,
                         int32_t *n);
 
+/* ---------------------------------------------------------------------
+ * Directed typed 3-node graphlets (Sec. 4.8: every typed set split into
+ * typed out-neighbours Gamma^{t,+} and in-neighbours Gamma^{t,-}).
+ *
+ * Input: an oriented graph -- arcs u -> v as an out-neighbour CSR
+ * (out_row_ptr int64 [n+1], out_col int32 [n_arcs], rows in any order),
+ * node types uint8 [n] in [0, L).  The split is a partition, so a graph
+ * with a reciprocal pair (u -> v and v -> u), a repeated arc or a
+ * self-loop is rejected (TG_ERR_INVALID_GRAPH).  Host or device pointers;
+ * the handle keeps its own copies.
+ *
+ * Edges are those of the underlying undirected graph, numbered like
+ * tg_build's (lexicographic (u, v), u < v, caller ids).  For edge {i, j},
+ * i < j, and each third node w, the sign of w at an endpoint is + when the
+ * endpoint is the tail of the arc between them.  Per edge, 8L uint32 slots,
+ * block b at b*L + t (t = type of w):
+ *   0 S_i^{t,+}  1 S_i^{t,-}  2 S_j^{t,+}  3 S_j^{t,-}
+ *   4 T^t(+,+)   5 T^t(+,-)   6 T^t(-,+)   7 T^t(-,-)   (sign at i, sign at j)
+ * (S_i excludes j, S_j excludes i, as for the undirected counts.)
+ * Global, int64: block 0, directed typed edges, L*L slots at
+ * tail_type*L + head_type; block 1, one slot per connected directed typed
+ * 3-node graphlet (isomorphism class).  A configuration on nodes 0, 1, 2 is
+ * the code (t0, t1, t2, a01, a02, a12), a_xy = 0 no arc, 1 x -> y, 2 y -> x,
+ * read as one integer in mixed radix (L, L, L, 3, 3, 3); a class is
+ * represented by the smallest code over the 6 renumberings of the nodes,
+ * and classes are ranked by that code.  Their number is
+ * (20 L^3 + 6 L^2 + 4 L) / 6 (Burnside). */
+typedef struct {
+    int32_t L;
+    int64_t per_edge_slots;           /* 8L */
+    int64_t global_slots;             /* L*L + classes */
+    int64_t classes;                  /* connected directed typed 3-node graphlets */
+} tg_directed_layout_t;
+
+/* Pure host function.  Errors: TG_ERR_TOO_MANY_TYPES, TG_ERR_INVALID_ARG. */
+tg_status tg_directed_layout(int32_t L, tg_directed_layout_t *out);
+
+/* Representative configuration of class `rank`: types3[3] and arcs3[3]
+ * (host; arc states of pairs (0,1), (0,2), (1,2)).  Pure host function.
+ * Errors: TG_ERR_TOO_MANY_TYPES, TG_ERR_INVALID_ARG (rank, NULL). */
+tg_status tg_directed_class_code(int32_t L, int64_t rank, int32_t *types3, int32_t *arcs3);
+
+/* Builds a handle for directed counting from an oriented graph (above).
+ * Stream-ordered; synchronises to validate.  Errors: TG_ERR_INVALID_ARG,
+ * TG_ERR_TOO_MANY_TYPES, TG_ERR_INVALID_GRAPH, TG_ERR_TOO_LARGE,
+ * TG_ERR_OOM, TG_ERR_CUDA.  The handle also serves tg_count and the other
+ * undirected calls, on the underlying undirected graph. */
+tg_status tg_build_directed(int64_t n, int64_t n_arcs, const int64_t *out_row_ptr, const int32_t *out_col,
+                            const uint8_t *node_types, int32_t L, const tg_options *opt, void *stream,
+                            tg_graph **out);
+
+/* Directed typed 3-node counts of a tg_build_directed handle: per_edge_out
+ * uint32 [m][8L] (may be NULL), global_out int64 [global_slots] (may be
+ * NULL); host or device.  Device-detected errors through tg_query_status.
+ * Errors: TG_ERR_INVALID_ARG (not a directed handle), TG_ERR_OOM,
+ * TG_ERR_CUDA. */
+tg_status tg_count_directed3(tg_graph *g, uint32_t *per_edge_out, int64_t *global_out, void *stream);
+
 /* Work counters (diagnostics for the benchmark's roofline; no effect on the
  * counts).  While enabled, the counting kernels add the units of work they
  * did to per-handle counters, slot TG_WORK_*: the hash-set lookups of the

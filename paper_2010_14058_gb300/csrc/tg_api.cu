@@ -194,6 +194,88 @@ tg_status tg_build_batch(int32_t ngraphs, const int64_t *node_off, int64_t n, in
     return guarded([&] { build_common(ngraphs, node_off, n, nnz, row_ptr, col, node_types, L, opt, stream, out); });
 }
 
+tg_status tg_directed_layout(int32_t L, tg_directed_layout_t *out) {
+    return guarded([&] {
+        check_types(L);
+        if (!out) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        tg_directed_layout_t r;
+        std::memset(&r, 0, sizeof(r));
+        r.L = L;
+        r.per_edge_slots = 8 * (int64_t)L;
+        r.classes = tg::directed_classes(L);
+        r.global_slots = (int64_t)L * L + r.classes;
+        *out = r;
+    });
+}
+
+tg_status tg_directed_class_code(int32_t L, int64_t rank, int32_t *types3, int32_t *arcs3) {
+    return guarded([&] {
+        check_types(L);
+        if (!types3 || !arcs3) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        if (!tg::directed_class_code(L, rank, types3, arcs3)) throw Error{TG_ERR_INVALID_ARG, "rank"};
+    });
+}
+
+tg_status tg_build_directed(int64_t n, int64_t n_arcs, const int64_t *out_row_ptr, const int32_t *out_col,
+                            const uint8_t *node_types, int32_t L, const tg_options *opt, void *stream, tg_graph **out) {
+    return guarded([&] {
+        if (!out) throw Error{TG_ERR_INVALID_ARG, "out"};
+        *out = nullptr;
+        check_types(L);
+        if (n < 0 || n_arcs < 0 || !out_row_ptr || (n_arcs > 0 && !out_col) || (n > 0 && !node_types))
+            throw Error{TG_ERR_INVALID_ARG, "sizes"};
+        if (2 * n_arcs >= ((int64_t)1 << 31) || n >= ((int64_t)1 << tg::kTypeShift))
+            throw Error{TG_ERR_TOO_LARGE, "index width"};
+        cudaStream_t s = (cudaStream_t)stream;
+        // row pointers checked on the host; arcs on the device
+        std::vector<int64_t> orp((size_t)n + 1);
+        const bool dev_rp = tg::is_device_pointer(out_row_ptr), dev_col = tg::is_device_pointer(out_col);
+        TG_CK(cudaMemcpyAsync(orp.data(), out_row_ptr, sizeof(int64_t) * (n + 1),
+                              dev_rp ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+        TG_CK(cudaStreamSynchronize(s));
+        if (orp[0] != 0 || orp[(size_t)n] != n_arcs) throw Error{TG_ERR_INVALID_GRAPH, "row pointers"};
+        for (int64_t v = 0; v < n; ++v)
+            if (orp[(size_t)v + 1] < orp[(size_t)v]) throw Error{TG_ERR_INVALID_GRAPH, "row pointers"};
+        tg::TBuf drp(sizeof(int64_t) * (n + 1), s), dcol(sizeof(int32_t) * std::max<int64_t>(n_arcs, 1), s);
+        TG_CK(cudaMemcpyAsync(drp.p, orp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+        if (n_arcs > 0)
+            TG_CK(cudaMemcpyAsync(dcol.p, out_col, sizeof(int32_t) * n_arcs,
+                                  dev_col ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        tg::TBuf srp(sizeof(int64_t) * (n + 1), s), scol(sizeof(int32_t) * std::max<int64_t>(2 * n_arcs, 1), s),
+            src(sizeof(int32_t) * std::max<int64_t>(n_arcs, 1), s);
+        tg::symmetrize_arcs(n, n_arcs, drp.as<int64_t>(), dcol.as<int32_t>(), srp.as<int64_t>(), scol.as<int32_t>(),
+                            src.as<int32_t>(), s);
+        const int64_t off[2] = {0, n};
+        tg_graph *h = nullptr;
+        build_common(1, off, n, 2 * n_arcs, srp.as<int64_t>(), scol.as<int32_t>(), node_types, L, opt, stream, &h);
+        try {
+            tg::prepare_directed(h->g, n_arcs, src.as<int32_t>(), dcol.as<int32_t>(), s);
+        } catch (...) {
+            tg_free(h);
+            throw;
+        }
+        *out = h;
+    });
+}
+
+tg_status tg_count_directed3(tg_graph *gh, uint32_t *per_edge_out, int64_t *global_out, void *stream) {
+    return guarded([&] {
+        if (!gh || !gh->g.directed) throw Error{TG_ERR_INVALID_ARG, "not a directed handle"};
+        Graph &G = gh->g;
+        cudaStream_t s = (cudaStream_t)stream;
+        G.stream = s;
+        const size_t pe_bytes = (size_t)G.m * 8 * G.L * sizeof(uint32_t);
+        const size_t gl_bytes = (size_t)G.d_global * sizeof(int64_t);
+        bool pe_staged = false, gl_staged = false;
+        uint32_t *pe = device_out(per_edge_out, pe_bytes, G.stage_pe, pe_staged);
+        int64_t *gl = device_out(global_out, gl_bytes, G.stage_gl, gl_staged);
+        G.last_launches = tg::run_directed3(G, pe, gl, s);
+        if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
+        if (gl_staged) TG_CK(cudaMemcpyAsync(global_out, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
+        if (pe_staged || gl_staged) TG_CK(cudaStreamSynchronize(s));
+    });
+}
+
 void tg_free(tg_graph *g) {
     if (!g) return;
     cudaStreamSynchronize(g->g.stream);

@@ -154,6 +154,10 @@ struct Graph {
     };
     std::vector<std::unique_ptr<HubPlan>> hub_plans;
     DBuf hub_tables;
+    // directed counts (tg_directed.cu): slot signs, typed out-degrees, class tables
+    DBuf dsign, doutdeg, dcls, darcs, dgacc;
+    int64_t d_global = 0;
+    bool directed = false;
     int64_t hub_stride = 0, hub_buf_words = 0;  // words per hub table, per buffer
     bool hub_packed = false;                    // two 16-bit counters per word
     // counting state
@@ -240,7 +244,7 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch, &work, &hub_tables, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
+                             &set_scratch, &work, &hub_tables, &dsign, &doutdeg, &dcls, &darcs, &dgacc, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
                 &pa_cls, &pa_gacc};
     }
     int64_t device_bytes() const {
@@ -321,6 +325,13 @@ int64_t launch_finalize_pa(Graph &G, int64_t *global_out, cudaStream_t s);
 // Typed-graphlet weighted graph (tg_weights.cu).
 void launch_weights(Graph &G, int k, const uint32_t *rows, int block, int64_t rank, int64_t *weights,
                     int64_t *degree, cudaStream_t s);
+// Directed typed 3-node graphlets (tg_directed.cu).
+int64_t directed_classes(int L);
+bool directed_class_code(int L, int64_t rank, int32_t *types3, int32_t *arcs3);
+void symmetrize_arcs(int64_t n, int64_t na, const int64_t *orp, const int32_t *ocol, int64_t *srp, int32_t *scol,
+                     int32_t *src, cudaStream_t s);
+void prepare_directed(Graph &G, int64_t na, const int32_t *src, const int32_t *ocol, cudaStream_t s);
+int64_t run_directed3(Graph &G, uint32_t *per_edge_out, int64_t *global_out, cudaStream_t s);
 // Sparse per-edge counts (tg_sparse.cu): returns the number of nonzero
 // pairs; writes them only while they fit `cap` (fits = false otherwise).
 int64_t count_sparse(Graph &G, int k, int64_t *row_off, uint16_t *slot, uint32_t *value, int64_t cap, bool &fits,

@@ -41,6 +41,11 @@ class tg_pa_layout_t(ctypes.Structure):
                 ("global_block_size", ctypes.c_int64 * 9), ("graphlet_edges", ctypes.c_int32 * 9)]
 
 
+class tg_directed_layout_t(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("per_edge_slots", ctypes.c_int64), ("global_slots", ctypes.c_int64),
+                ("classes", ctypes.c_int64)]
+
+
 class tg_options(ctypes.Structure):
     _fields_ = [("light_edge_max_degree", ctypes.c_int32), ("light_anchor_max_wedges", ctypes.c_int32),
                 ("anchor_table_budget_mb", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
@@ -67,6 +72,11 @@ SIGNATURES = {
     "tg_finalize_global": ([_i32, _i32, _i32, _vp, _vp], _i32),
     "tg_count_batch": ([_vp, _i32, _vp, _vp, _vp], _i32),
     "tg_pa_layout": ([_i32, ctypes.POINTER(tg_pa_layout_t)], _i32),
+    "tg_directed_layout": ([_i32, ctypes.POINTER(tg_directed_layout_t)], _i32),
+    "tg_directed_class_code": ([_i32, _i64, _vp, _vp], _i32),
+    "tg_build_directed": ([_i64, _i64, _vp, _vp, _vp, _i32, ctypes.POINTER(tg_options), _vp, ctypes.POINTER(_vp)],
+                          _i32),
+    "tg_count_directed3": ([_vp, _vp, _vp, _vp], _i32),
     "tg_pa_labelling": ([_i32, _i32, _i64, _vp], _i32),
     "tg_pa_slot_class": ([_i32, _i32, _i32, _i64, ctypes.POINTER(_i64)], _i32),
     "tg_count_position_aware": ([_vp, _vp, _vp, _vp], _i32),
@@ -249,6 +259,36 @@ def tg_build_batch(node_off, row_ptr, col, node_types, L: int, options: dict | N
                                  _ptr(node_types), L, _options(options), _stream(stream), ctypes.byref(h)),
            "tg_build_batch")
     return Graph(h.value)
+
+
+def tg_build_directed(out_row_ptr, out_col, node_types, L: int, options: dict | None = None, stream=None) -> Graph:
+    """Handle of an oriented graph given by its out-neighbour CSR (Sec. 4.8)."""
+    n = int(out_row_ptr.shape[0]) - 1
+    na = int(out_col.shape[0])
+    h = _vp()
+    _check(load().tg_build_directed(n, na, _ptr(out_row_ptr), _ptr(out_col), _ptr(node_types), L, _options(options),
+                                    _stream(stream), ctypes.byref(h)), "tg_build_directed")
+    return Graph(h.value)
+
+
+def tg_directed_layout(L: int) -> dict:
+    lay = tg_directed_layout_t()
+    _check(load().tg_directed_layout(L, ctypes.byref(lay)), "tg_directed_layout")
+    return {"L": lay.L, "per_edge_slots": lay.per_edge_slots, "global_slots": lay.global_slots,
+            "classes": lay.classes}
+
+
+def tg_directed_class_code(L: int, rank: int) -> tuple:
+    """(types of nodes 0,1,2; arc states of pairs (0,1), (0,2), (1,2)) of class `rank`."""
+    t = np.zeros(3, dtype=np.int32)
+    a = np.zeros(3, dtype=np.int32)
+    _check(load().tg_directed_class_code(L, rank, t.ctypes.data, a.ctypes.data), "tg_directed_class_code")
+    return tuple(int(x) for x in t), tuple(int(x) for x in a)
+
+
+def tg_count_directed3(g: Graph, per_edge_out=None, global_out=None, stream=None) -> None:
+    _check(load().tg_count_directed3(g.handle, _ptr(per_edge_out), _ptr(global_out), _stream(stream)),
+           "tg_count_directed3")
 
 
 def tg_free(g: Graph) -> None:

@@ -147,3 +147,17 @@ def test_pa_host_functions_reject_bad_arguments(lib):
                  lambda: tg.tg_pa_slot_class(3, 3, 0, 0), lambda: tg.tg_pa_slot_class(3, 0, 0, 127)):
         with pytest.raises(tg.TGError):
             call()
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 8])
+def test_directed_layout_and_class_codes_match_oracle(L, lib):
+    import paper_2010_14058_gb300 as tg
+    lay = tg.tg_directed_layout(L)
+    assert lay["per_edge_slots"] == 8 * L
+    assert lay["classes"] == oracle.directed_classes(L)
+    assert lay["global_slots"] == oracle.directed_global_slots(L)
+    for r in range(lay["classes"]):
+        t, a = tg.tg_directed_class_code(L, r)
+        assert oracle.directed_class(L, t, a) == r          # each representative is in its class
+    with pytest.raises(tg.TGError):
+        tg.tg_directed_class_code(L, lay["classes"])
