@@ -72,6 +72,9 @@ def parse():
                     help="batched / serve: oracle time budget of that check (0: no limit)")
     ap.add_argument("--position-aware", action="store_true",
                     help="plain mode: also time the position-aware count (Sec. 5) of the same graph")
+    ap.add_argument("--directed", action="store_true",
+                    help="plain mode: also time the directed typed 3-node count (Sec. 4.8) of the workload's "
+                         "edges oriented by a seeded coin")
     return ap.parse_args()
 
 
@@ -371,6 +374,74 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     value = world * m * args.steps / (ms_max / 1e3)
 
+    # end-to-end figures first, right after the timed region (before the
+    # roofline work below allocates anything)
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        h_rp = torch.from_numpy(np.ascontiguousarray(g["row_ptr"])).pin_memory()
+        h_col = torch.from_numpy(np.ascontiguousarray(g["col"])).pin_memory()
+        h_ty = torch.from_numpy(np.ascontiguousarray(g["types"])).pin_memory()
+        h_pe = torch.empty((m, S), dtype=torch.int32).pin_memory()
+        h_gl = torch.empty(G, dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
+            tg.tg_count(h, 4, h_pe, h_gl, stream=stream)
+            h.free()
+
+        for _ in range(max(1, min(args.warmup, 2))):     # untimed: staging buffers, first touch of pinned pages
+            e2e_step()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        bi = h_rp.numel() * 8 + h_col.numel() * 4 + h_ty.numel()
+        bo = h_pe.numel() * 4 + h_gl.numel() * 8
+        e2e = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo)}
+
+    # the same end to end with the sparse per-edge form (only nonzero counts
+    # cross PCIe: row offsets, uint16 slots, uint32 counts)
+    e2e_sparse = None
+    if not args.no_e2e and rank == 0:
+        h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
+        d_off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+        nnz = tg.tg_count_sparse(h, 4, d_off, stream=stream)
+        h.free()
+        d_slot = torch.empty(nnz, dtype=torch.int16, device=dev)
+        d_val = torch.empty(nnz, dtype=torch.int32, device=dev)
+        d_gl = torch.empty(G, dtype=torch.int64, device=dev)
+        p_off = torch.empty(m + 1, dtype=torch.int64).pin_memory()
+        p_slot = torch.empty(nnz, dtype=torch.int16).pin_memory()
+        p_val = torch.empty(nnz, dtype=torch.int32).pin_memory()
+
+        def e2e_sparse_step():
+            h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
+            tg.tg_count_sparse(h, 4, d_off, d_slot, d_val, d_gl, stream=stream)
+            with torch.cuda.stream(stream):
+                p_off.copy_(d_off, non_blocking=True)
+                p_slot.copy_(d_slot, non_blocking=True)
+                p_val.copy_(d_val, non_blocking=True)
+                h_gl.copy_(d_gl, non_blocking=True)
+            h.free()
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            e2e_sparse_step()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_sparse_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        bo = p_off.numel() * 8 + nnz * 6 + G * 8
+        e2e_sparse = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+                      "d2h_bytes_per_step": int(bo), "nonzero_pairs": int(nnz),
+                      "pairs_per_edge": round(nnz / max(m, 1), 2)}
+
+
     # roofline: algorithmic bytes of each count kernel per step over its
     # CUDA-event time per step (k_clique and k_clique_big share one bound)
     peak, peak_kind = load_peaks()
@@ -439,59 +510,6 @@ def run_ours(args):
         walg["note"] = "effective algorithmic bandwidth W_alg / T_count; may exceed HBM (L2 and shared-memory reuse)"
     kernel_share = {k: round(v[0] / sum(x[0] for x in kernel_ms.values()), 4) for k, v in kernel_ms.items()}
 
-    # end to end through host buffers
-    e2e = None
-    if not args.no_e2e and rank == 0:
-        h_rp = torch.from_numpy(np.ascontiguousarray(g["row_ptr"])).pin_memory()
-        h_col = torch.from_numpy(np.ascontiguousarray(g["col"])).pin_memory()
-        h_ty = torch.from_numpy(np.ascontiguousarray(g["types"])).pin_memory()
-        h_pe = torch.empty((m, S), dtype=torch.int32).pin_memory()
-        h_gl = torch.empty(G, dtype=torch.int64).pin_memory()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
-            tg.tg_count(h, 4, h_pe, h_gl, stream=stream)
-            h.free()
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t
-        bi = h_rp.numel() * 8 + h_col.numel() * 4 + h_ty.numel()
-        bo = h_pe.numel() * 4 + h_gl.numel() * 8
-        e2e = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
-               "d2h_bytes_per_step": int(bo)}
-
-    # the same end to end with the sparse per-edge form (only nonzero counts
-    # cross PCIe: row offsets, uint16 slots, uint32 counts)
-    e2e_sparse = None
-    if not args.no_e2e and rank == 0:
-        h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
-        d_off = torch.empty(m + 1, dtype=torch.int64, device=dev)
-        nnz = tg.tg_count_sparse(h, 4, d_off, stream=stream)
-        h.free()
-        d_slot = torch.empty(nnz, dtype=torch.int16, device=dev)
-        d_val = torch.empty(nnz, dtype=torch.int32, device=dev)
-        d_gl = torch.empty(G, dtype=torch.int64, device=dev)
-        p_off = torch.empty(m + 1, dtype=torch.int64).pin_memory()
-        p_slot = torch.empty(nnz, dtype=torch.int16).pin_memory()
-        p_val = torch.empty(nnz, dtype=torch.int32).pin_memory()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            h = tg.tg_build(h_rp, h_col, h_ty, L, stream=stream)
-            tg.tg_count_sparse(h, 4, d_off, d_slot, d_val, d_gl, stream=stream)
-            with torch.cuda.stream(stream):
-                p_off.copy_(d_off, non_blocking=True)
-                p_slot.copy_(d_slot, non_blocking=True)
-                p_val.copy_(d_val, non_blocking=True)
-                h_gl.copy_(d_gl, non_blocking=True)
-            h.free()
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t
-        bo = p_off.numel() * 8 + nnz * 6 + G * 8
-        e2e_sparse = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
-                      "d2h_bytes_per_step": int(bo), "nonzero_pairs": int(nnz),
-                      "pairs_per_edge": round(nnz / max(m, 1), 2)}
-
     # position-aware counts (Sec. 5) of the same graph: same gathering
     # passes, position-aware epilogue, rows of S_pa slots
     position_aware = None
@@ -532,6 +550,54 @@ def run_ours(args):
                           "k_epi4_ms_per_step": round(kernel_ms.get("k_epi4", [0.0])[0] / args.steps, 3),
                           "step": "tg_build + tg_count_position_aware + tg_free, device-resident"}
 
+    # directed typed 3-node counts (Sec. 4.8) of the same edges, each oriented
+    # by a seeded coin: tg_build_directed + tg_count_directed3 per step
+    directed = None
+    if args.directed and rank == 0:
+        src_e, dst_e = edge_list(g)
+        flip = np.random.default_rng(CPU_SEED + 48).random(len(src_e)) < 0.5
+        tail = np.where(flip, dst_e, src_e)
+        head = np.where(flip, src_e, dst_e)
+        order = np.argsort(tail, kind="stable")
+        d_rp = torch.as_tensor(np.concatenate([[0], np.cumsum(np.bincount(tail, minlength=g["n"]))]).astype(np.int64),
+                               device=dev)
+        d_col = torch.as_tensor(head[order].astype(np.int32), device=dev)
+        lay_d = tg.tg_directed_layout(L)
+        pe_d = torch.empty((m, lay_d["per_edge_slots"]), dtype=torch.int32, device=dev)
+        gl_d = torch.empty(lay_d["global_slots"], dtype=torch.int64, device=dev)
+        d_ms = {}
+
+        def d_step(timing: bool):
+            h = tg.tg_build_directed(d_rp, d_col, ty, L, stream=stream)
+            if timing:
+                tg.tg_set_timing(h, True)
+            tg.tg_count_directed3(h, pe_d, gl_d, stream=stream)
+            if timing:
+                for name, (kms, nl) in tg.tg_get_timing(h).items():
+                    d_ms[name] = d_ms.get(name, 0.0) + kms
+            st = tg.tg_query_status(h) if timing else 0
+            h.free()
+            return st
+
+        for _ in range(args.warmup):
+            d_step(False)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        d_status = 0
+        for _ in range(args.steps):
+            d_status = d_status or d_step(True)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        dms = b0.elapsed_time(b1)
+        directed = {"value": round(m * args.steps / (dms / 1e3), 1), "unit": UNIT,
+                    "ms_per_step": round(dms / args.steps, 3), "status": tg.STATUS[d_status],
+                    "per_edge_slots": lay_d["per_edge_slots"], "global_slots": lay_d["global_slots"],
+                    "k_directed3_ms_per_step": round(d_ms.get("k_directed3", 0.0) / args.steps, 3),
+                    "step": "tg_build_directed + tg_count_directed3 + tg_free, device-resident; each edge of the "
+                            "workload oriented by a seeded coin"}
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(g)
@@ -554,6 +620,8 @@ def run_ours(args):
         }
         if position_aware is not None:
             line["position_aware"] = position_aware
+        if directed is not None:
+            line["directed"] = directed
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -582,6 +650,16 @@ def run_ours(args):
 # stratum sample) to stay within the time budget.
 
 CPU_SEED = 20201029
+
+
+def edge_list(g: dict):
+    """(src, dst) of every edge in edge-id order (u < v, lexicographic)."""
+    rp, col, n = g["row_ptr"], g["col"].astype(np.int64), g["n"]
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    up = col > rows
+    src, dst = rows[up], col[up]
+    order = np.lexsort((dst, src))
+    return src[order], dst[order]
 
 
 def edge_cost_proxy(g: dict):
