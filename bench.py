@@ -393,15 +393,18 @@ def run_ours(args):
         for _ in range(max(1, min(args.warmup, 2))):     # untimed: staging buffers, first touch of pinned pages
             e2e_step()
         torch.cuda.synchronize()
+        step_ms = []
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
-            e2e_step()
+            t_s = time.perf_counter()
+            e2e_step()                                   # returns after its rows are in host memory
+            step_ms.append(round(1e3 * (time.perf_counter() - t_s), 1))
         torch.cuda.synchronize()
         el = time.perf_counter() - t
         bi = h_rp.numel() * 8 + h_col.numel() * 4 + h_ty.numel()
         bo = h_pe.numel() * 4 + h_gl.numel() * 8
         e2e = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
-               "d2h_bytes_per_step": int(bo)}
+               "d2h_bytes_per_step": int(bo), "step_ms": step_ms}
 
     # the same end to end with the sparse per-edge form (only nonzero counts
     # cross PCIe: row offsets, uint16 slots, uint32 counts)

@@ -124,9 +124,13 @@ typedef struct {
                                          array would exceed it is counted in chunks of whole graphs */
     int32_t hub_min_wedges;           /* anchors with more wedges than this are hubs: each is counted
                                          by the whole GPU against one node table shared by all CTAs */
-    int32_t hub_l2_mb;                /* MB of hub node tables in use at once (about the L2 size:
-                                         more hubs per launch, fewer launches) */
-    int32_t reserved;
+    int32_t hub_l2_mb;                /* MB of hub node tables of the persistent hub pass: one group
+                                         of hubs fills at most half of it (about the L2 size) */
+    int32_t isect_modes;              /* typed set intersection per bucket of the shorter segment's
+                                         length (buckets [1,32) [32,128) [128,512) [512,inf), two bits
+                                         each from bit 0): 0 default = 1, 1 binary search of each
+                                         shorter entry in the longer segment, 2 warp-wide merge of
+                                         both segments, 3 whichever a dependent-load count favours */
 } tg_options;
 
 /* ---- layout ---------------------------------------------------------- */

@@ -14,7 +14,12 @@ them"); they pick which kernel variant takes which part of the work:
                            table-versus-hash choice per degree bucket
   ctas_per_sm              resident CTAs per SM of the orbit epilogue
   hub_l2_mb                hub node tables counted together (more hubs per
-                           launch against L2 pressure)
+                           group against L2 pressure)
+  isect_bucket_0 .. 3      typed set intersection per bucket of the shorter
+                           segment's length ([1,32) [32,128) [128,512)
+                           [512,inf)): 1 binary search, 2 warp-wide merge,
+                           3 a dependent-load count picks per pair; packed
+                           into tg_options.isect_modes
 
 tune() measures tg_count (CUDA events on the given stream) for one graph or
 batch handle per candidate, by coordinate descent from the defaults, and
@@ -40,9 +45,25 @@ SPACE = {
     "hub_min_wedges": [1 << 14, 1 << 16, 1 << 18, 1 << 20],
     "ctas_per_sm": [2, 3, 4],
     "hub_l2_mb": [64, 128, 256],
+    "isect_bucket_0": [1, 2, 3],
+    "isect_bucket_1": [1, 2, 3],
+    "isect_bucket_2": [1, 2, 3],
+    "isect_bucket_3": [1, 2, 3],
 }
 DEFAULTS = {"light_edge_max_degree": 256, "light_anchor_max_wedges": 64, "hub_min_wedges": 1 << 16, "ctas_per_sm": 3,
-            "hub_l2_mb": 128}
+            "hub_l2_mb": 128, "isect_bucket_0": 1, "isect_bucket_1": 1, "isect_bucket_2": 1, "isect_bucket_3": 1}
+
+
+def library_options(options: dict) -> dict:
+    """tg_options fields of a knob setting: the per-bucket intersection modes
+    packed into isect_modes (two bits per bucket)."""
+    out = {k: v for k, v in options.items() if not k.startswith("isect_bucket_")}
+    if len(out) < len(options):
+        modes = 0
+        for b in range(4):
+            modes |= (int(options.get(f"isect_bucket_{b}", 1)) & 3) << (2 * b)
+        out["isect_modes"] = modes
+    return out
 
 CACHE_PATH = os.environ.get("TG_AUTOTUNE_CACHE", os.path.join(os.path.dirname(__file__), ".autotune.json"))
 _lock = threading.Lock()
@@ -119,9 +140,10 @@ def tune(row_ptr, col, types, L: int, node_off=None, space: dict | None = None, 
     G = tg.tg_layout(L, 4)["global_slots"]
 
     def build(options):
+        opts = library_options(options)
         if node_off is None:
-            return tg.tg_build(row_ptr, col, types, L, options=options, stream=stream)
-        return tg.tg_build_batch(node_off, row_ptr, col, types, L, options=options, stream=stream)
+            return tg.tg_build(row_ptr, col, types, L, options=opts, stream=stream)
+        return tg.tg_build_batch(node_off, row_ptr, col, types, L, options=opts, stream=stream)
 
     best = {k: DEFAULTS[k] for k in space}
     best_ms, ref = _time_count(build, best, L, G, ngraphs, stream, reps)
@@ -141,7 +163,7 @@ def tune(row_ptr, col, types, L: int, node_off=None, space: dict | None = None, 
                 trials.append({"options": dict(cand), "ms": round(ms, 3)})
                 if ms < best_ms:
                     best, best_ms = cand, ms
-    entry = {"options": best, "ms": round(best_ms, 3), "default_ms": round(default_ms, 3), "signature": sig,
+    entry = {"options": library_options(best), "knobs": best, "ms": round(best_ms, 3), "default_ms": round(default_ms, 3), "signature": sig,
              "n": n, "m": m, "max_degree": dmax, "ngraphs": ngraphs, "trials": trials}
     if store:
         _store(sig, entry, path)

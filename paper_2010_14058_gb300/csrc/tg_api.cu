@@ -69,6 +69,7 @@ void build_common(int32_t ngraphs, const int64_t *node_off, int64_t n, int64_t n
         if (opt->cycle_budget_mb > 0) o.cycle_budget_mb = opt->cycle_budget_mb;
         if (opt->hub_min_wedges > 0) o.hub_min_wedges = opt->hub_min_wedges;
         if (opt->hub_l2_mb > 0) o.hub_l2_mb = opt->hub_l2_mb;
+        if (opt->isect_modes > 0) o.isect_modes = opt->isect_modes & 0xff;
     }
     o.hub_min_wedges = std::max(o.hub_min_wedges, o.light_anchor_max_wedges);
     o.light_edge_max_degree = std::min(o.light_edge_max_degree, 256);     // warp T list capacity

@@ -105,8 +105,9 @@ __device__ __forceinline__ int pair_idx(int L, int t, int u) {   // t <= u
 }
 
 // ------------------------------------------------------------------ k_tri
-// Warp per edge: c_e^t = |Gamma_i^t cap Gamma_j^t| by searching each element
-// of the shorter typed segment in the longer one (Cor. 1; Thm. 2's O(Delta)).
+// Warp per edge: c_e^t = |Gamma_i^t cap Gamma_j^t| (Cor. 1; Thm. 2's O(Delta)),
+// each typed pair by binary search or merge (isect).
+template <bool kMerge>
 __global__ void __launch_bounds__(256) k_tri(GraphView g, CountView cv) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -124,10 +125,15 @@ __global__ void __launch_bounds__(256) k_tri(GraphView g, CountView cv) {
                 x = ei; ei = ej; ej = x;
             }
             unsigned cnt = 0;
-            for (int64_t s = bi + lane; s < ei; s += 32) {
-                int32_t w = g.adj[s];
-                int64_t r = lower_bound_i32(g.adj, bj, ej, w);
-                cnt += (r < ej && g.adj[r] == w) ? 1u : 0u;
+            if (kMerge && isect_use_merge(g.isect_modes, ei - bi, ej - bj)) {
+                isect_merge(g.adj, bi, ei, bj, ej, lane,
+                            [&](bool found, int64_t, int64_t, int32_t) { cnt += found ? 1u : 0u; });
+            } else {
+                for (int64_t s = bi + lane; s < ei; s += 32) {
+                    const int32_t w = g.adj[s];
+                    const int64_t r = lower_bound_i32(g.adj, bj, ej, w);
+                    cnt += (r < ej && g.adj[r] == w) ? 1u : 0u;
+                }
             }
             cnt = warp_sum_u32(cnt);
             if (lane == 0) cv.C[e * g.L + t] = cnt;
@@ -910,7 +916,7 @@ __device__ __forceinline__ unsigned long long warp_total(uint32_t v, unsigned lo
     return lo + (hi << 16);
 }
 
-template <class Acc>
+template <class Acc, bool kMerge>
 __global__ void __launch_bounds__(256, sizeof(Acc) == 4 ? 6 : 4) k_tsum(GraphView g, CountView cv, int64_t e0,
                                                                         int64_t e1) {
     const int L = g.L, LL = L * L;
@@ -933,18 +939,10 @@ __global__ void __launch_bounds__(256, sizeof(Acc) == 4 ? 6 : 4) k_tsum(GraphVie
                     x = ei; ei = ej; ej = x;
                     swapped = true;
                 }
-                for (int64_t r0 = bi; r0 < ei; r0 += 32) {
-                    const int64_t s = r0 + lane;
-                    bool found = false;
-                    int64_t r = 0;
-                    int32_t w = 0;
-                    if (s < ei) {
-                        w = g.adj[s];
-                        r = lower_bound_i32(g.adj, bj, ej, w);
-                        found = r < ej && g.adj[r] == w;
-                    }
+                isect<kMerge>(g.adj, g.isect_modes, bi, ei, bj, ej, lane, [&](bool found, int64_t s, int64_t r,
+                                                                                 int32_t w) {
                     const unsigned bal = __ballot_sync(0xffffffffu, found);
-                    if (bal == 0) continue;                 // warp-uniform
+                    if (bal == 0) return;                   // warp-uniform
                     const uint32_t *ci = cv.C, *cj = cv.C;
                     const int32_t *o = g.toff;
                     if (found) {
@@ -966,7 +964,7 @@ __global__ void __launch_bounds__(256, sizeof(Acc) == 4 ? 6 : 4) k_tsum(GraphVie
                             s3 += (Acc)t3;
                         }
                     }
-                }
+                });
             }
             if (lane < L) {
                 sum[t * L + lane] = (unsigned long long)s1;
@@ -1932,7 +1930,8 @@ static int64_t launch_triangles(Graph &G, cudaStream_t s) {
     int64_t launches = 0;
     if (G.m > 0) {
         KernelTimer kt(G, s, "k_tri");
-        k_tri<<<grid_for(G.m, 8, sms * 16), 256, 0, s>>>(gv, cv);
+        if (isect_any_merge(G.opt.isect_modes)) k_tri<true><<<grid_for(G.m, 8, sms * 16), 256, 0, s>>>(gv, cv);
+        else k_tri<false><<<grid_for(G.m, 8, sms * 16), 256, 0, s>>>(gv, cv);
         ++launches;
     }
     if (G.n > 0) {
@@ -2242,8 +2241,15 @@ static int64_t launch_edges4(Graph &G, int64_t b, int64_t e, const Tile *tiles, 
                                         ne + 1, s));
     {
         KernelTimer kt(G, s, "k_tsum");
-        if (G.max_degree < (1 << 16)) k_tsum<uint32_t><<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e);
-        else k_tsum<unsigned long long><<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e);
+        const unsigned grid = (unsigned)grid_for(ne, 8, sms * 32);
+        const bool merge = isect_any_merge(G.opt.isect_modes);
+        if (G.max_degree < (1 << 16)) {
+            if (merge) k_tsum<uint32_t, true><<<grid, 256, 0, s>>>(gv, cv, b, e);
+            else k_tsum<uint32_t, false><<<grid, 256, 0, s>>>(gv, cv, b, e);
+        } else {
+            if (merge) k_tsum<unsigned long long, true><<<grid, 256, 0, s>>>(gv, cv, b, e);
+            else k_tsum<unsigned long long, false><<<grid, 256, 0, s>>>(gv, cv, b, e);
+        }
         ++launches;
     }
     {
@@ -2275,6 +2281,7 @@ static int64_t launch_edges4(Graph &G, int64_t b, int64_t e, const Tile *tiles, 
     TG_CK(cudaGetLastError());
     return launches;
 }
+
 
 // Allocates the working arrays of a count with this k (kept by the handle).
 void prepare_counting(Graph &G, int k, cudaStream_t s) {

@@ -7,8 +7,8 @@
 // rows by (type, id), per-type segments) plus one sign per adjacency slot
 // (+1 when the row's node is the arc's tail) and the typed out-degrees of
 // every node.  Per edge {i, j}, one warp intersects the typed segments of i
-// and j; each triangle node w falls into T^t(sign at i, sign at j), counted
-// with ballots; the S sets follow from the typed out- and in-degrees by
+// and j (binary search or merge, isect); each triangle node w falls into
+// T^t(sign at i, sign at j), counted with ballots; the S sets follow from the typed out- and in-degrees by
 // Cor. 1-2: |S_i^{t,+}| = d_i^{t,+} - |T^t(+,.)| - [phi_j = t, i -> j] and
 // so on.  Per-edge layout and class ranks: include/tg.h.
 #include <algorithm>
@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(256) k_out_degree(GraphView g, const int8_t *_
 // Warp per edge {i, j} (i the smaller caller id): T^t by signs at i and j
 // with ballots (lane t keeps type t's four counts), then S^t from the
 // typed out- and in-degrees, the row, and the per-CTA class histogram.
+template <bool kMerge>
 __global__ void __launch_bounds__(256) k_directed3(GraphView g, const int8_t *__restrict__ sign,
                                                    const int32_t *__restrict__ outdeg,
                                                    const int32_t *__restrict__ old_of,
@@ -200,23 +201,18 @@ __global__ void __launch_bounds__(256) k_directed3(GraphView g, const int8_t *__
             const bool i_short = ei - bi <= ej - bj;
             const int64_t sb = i_short ? bi : bj, se = i_short ? ei : ej;
             const int64_t lb = i_short ? bj : bi, le = i_short ? ej : ei;
-            for (int64_t r0 = sb; r0 < se; r0 += 32) {
-                const int64_t s = r0 + lane;
+            isect<kMerge>(g.adj, g.isect_modes, sb, se, lb, le, lane, [&](bool found, int64_t s, int64_t r, int32_t) {
                 int q = -1;
-                if (s < se) {
-                    const int32_t w = g.adj[s];
-                    const int64_t r = lower_bound_i32(g.adj, lb, le, w);
-                    if (r < le && g.adj[r] == w) {
-                        const int8_t at_i = sign[i_short ? s : r], at_j = sign[i_short ? r : s];
-                        q = (at_i > 0 ? 0 : 2) + (at_j > 0 ? 0 : 1);
-                    }
+                if (found) {
+                    const int8_t at_i = sign[i_short ? s : r], at_j = sign[i_short ? r : s];
+                    q = (at_i > 0 ? 0 : 2) + (at_j > 0 ? 0 : 1);
                 }
                 const unsigned n0 = __popc(__ballot_sync(0xffffffffu, q == 0));
                 const unsigned n1 = __popc(__ballot_sync(0xffffffffu, q == 1));
                 const unsigned n2 = __popc(__ballot_sync(0xffffffffu, q == 2));
                 const unsigned n3 = __popc(__ballot_sync(0xffffffffu, q == 3));
                 if (lane == t) { c0 += n0; c1 += n1; c2 += n2; c3 += n3; }
-            }
+            });
         }
         if (lane < L) {
             const int t = lane;
@@ -330,13 +326,21 @@ int64_t run_directed3(Graph &G, uint32_t *per_edge_out, int64_t *global_out, cud
     const int Gs = (int)G.d_global;
     TG_CK(cudaMemsetAsync(G.dgacc.p, 0, sizeof(unsigned long long) * (size_t)Gs, s));
     const size_t smem = sizeof(unsigned long long) * (size_t)Gs;
-    raise_smem_limit((const void *)k_directed3, smem);
+    const bool merge = isect_any_merge(G.opt.isect_modes);
+    const void *fn = merge ? (const void *)k_directed3<true> : (const void *)k_directed3<false>;
+    raise_smem_limit(fn, smem);
     int64_t launches = 0;
     if (G.m > 0) {
         KernelTimer kt(G, s, "k_directed3");
-        k_directed3<<<(unsigned)std::min<int64_t>((G.m + 7) / 8, (int64_t)sm_count() * 16), 256, smem, s>>>(
-            G.view(), G.dsign.as<int8_t>(), G.doutdeg.as<int32_t>(), G.old_of.as<int32_t>(), G.dcls.as<int32_t>(), Gs,
-            per_edge_out, G.dgacc.as<unsigned long long>(), G.status.as<uint32_t>());
+        const unsigned grid = (unsigned)std::min<int64_t>((G.m + 7) / 8, (int64_t)sm_count() * 16);
+        if (merge)
+            k_directed3<true><<<grid, 256, smem, s>>>(G.view(), G.dsign.as<int8_t>(), G.doutdeg.as<int32_t>(),
+                                                       G.old_of.as<int32_t>(), G.dcls.as<int32_t>(), Gs, per_edge_out,
+                                                       G.dgacc.as<unsigned long long>(), G.status.as<uint32_t>());
+        else
+            k_directed3<false><<<grid, 256, smem, s>>>(G.view(), G.dsign.as<int8_t>(), G.doutdeg.as<int32_t>(),
+                                                        G.old_of.as<int32_t>(), G.dcls.as<int32_t>(), Gs, per_edge_out,
+                                                        G.dgacc.as<unsigned long long>(), G.status.as<uint32_t>());
         ++launches;
     }
     if (global_out) {

@@ -194,6 +194,7 @@ struct Graph {
     GraphView view() const {
         GraphView v;
         v.ngraphs = ngraphs; v.L = L; v.n = n; v.nnz = nnz; v.m = m;
+        v.isect_modes = opt.isect_modes;
         v.node_off = node_off.as<int64_t>();
         v.edge_off = edge_off.as<int64_t>();
         v.rp = rp.as<int64_t>();

@@ -56,6 +56,7 @@ constexpr int64_t kHubTicketWords = 1 << 16;
 struct GraphView {
     int32_t ngraphs;
     int32_t L;
+    int32_t isect_modes;       // tg_options::isect_modes
     int64_t n, nnz, m;
     const int64_t *node_off;   // [ngraphs+1] internal node id ranges per graph
     const int64_t *edge_off;   // [ngraphs+1] edge id ranges per graph
@@ -129,6 +130,83 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *__restrict__ a
         n -= half;
     }
     return (base - a) + (__ldg(base) < key ? 1 : 0);
+}
+
+// Typed set intersection of two sorted, duplicate-free segments A =
+// adj[sa, ea) and B = adj[sb, eb), |A| <= |B|, by one warp.  fn(found, s,
+// r, w) is called by every lane once per round (warp-uniform): lane s's
+// entry w = adj[s] of A, found in B at r when `found`.  Rounds visit A's
+// entries in order, so the found entries come out sorted.
+//   binary: 32 entries of A per round, each searched in B (ceil(log2 |B|)
+//           dependent loads);
+//   merge:  a window of 32 entries of A against a window of 32 of B per
+//           round (both loads coalesced), each A entry searched in the B
+//           window by shuffles; the window with the smaller last entry
+//           moves on (both when equal), so an equal pair always meets.
+// isect_use_merge picks per bucket of |A| (tg_options::isect_modes); binary
+// search unless a bucket asks for merge or for the dependent-load count.
+__device__ __forceinline__ bool isect_use_merge(int32_t modes, int64_t a, int64_t b) {
+    const int bucket = a < 32 ? 0 : (a < 128 ? 1 : (a < 512 ? 2 : 3));
+    const int mode = (modes >> (2 * bucket)) & 3;
+    if (mode != 3) return mode == 2;                        // 0 (default) and 1: binary search
+    const int64_t lg = 64 - __clzll((unsigned long long)(b > 2 ? b - 1 : 1));   // ceil(log2 b)
+    return (a + b + 31) / 32 < ((a + 31) / 32) * lg;                            // dependent-load rounds
+}
+
+template <class F>
+__device__ __forceinline__ void isect_merge(const int32_t *__restrict__ adj, int64_t sa, int64_t ea, int64_t sb,
+                                            int64_t eb, int lane, F fn) {
+    int64_t pa = sa, pb = sb;
+    while (pa < ea && pb < eb) {                            // warp-uniform
+        const int64_t ia = pa + lane, ib = pb + lane;
+        const int32_t av = ia < ea ? __ldg(adj + ia) : INT32_MAX;
+        const int32_t bv = ib < eb ? __ldg(adj + ib) : INT32_MAX;
+        const int na = (int)(ea - pa < 32 ? ea - pa : 32), nb = (int)(eb - pb < 32 ? eb - pb : 32);
+        const int32_t alast = __shfl_sync(0xffffffffu, av, na - 1);
+        const int32_t blast = __shfl_sync(0xffffffffu, bv, nb - 1);
+        int k = 0;                                          // last B entry <= av (B window in registers)
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int32_t c = __shfl_sync(0xffffffffu, bv, k + st);
+            if (c <= av) k += st;
+        }
+        const int32_t bk = __shfl_sync(0xffffffffu, bv, k);
+        fn(ia < ea && bk == av, ia, pb + k, av);
+        if (alast <= blast) pa += 32;
+        if (blast <= alast) pb += 32;
+    }
+}
+
+template <class F>
+__device__ __forceinline__ void isect_binary(const int32_t *__restrict__ adj, int64_t sa, int64_t ea, int64_t sb,
+                                             int64_t eb, int lane, F fn) {
+    for (int64_t r0 = sa; r0 < ea; r0 += 32) {
+        const int64_t s = r0 + lane;
+        bool found = false;
+        int64_t r = 0;
+        int32_t w = 0;
+        if (s < ea) {
+            w = adj[s];
+            r = lower_bound_i32(adj, sb, eb, w);
+            found = r < eb && adj[r] == w;
+        }
+        fn(found, s, r, w);
+    }
+}
+
+// kMerge: the kernel was instantiated for options that may ask for merge
+// (isect_any_merge); without it only binary search is compiled in.
+template <bool kMerge, class F>
+__device__ __forceinline__ void isect(const int32_t *__restrict__ adj, int32_t modes, int64_t sa, int64_t ea,
+                                      int64_t sb, int64_t eb, int lane, F fn) {
+    if (kMerge && isect_use_merge(modes, ea - sa, eb - sb)) isect_merge(adj, sa, ea, sb, eb, lane, fn);
+    else isect_binary(adj, sa, ea, sb, eb, lane, fn);
+}
+
+__host__ __device__ inline bool isect_any_merge(int32_t modes) {
+    for (int b = 0; b < 4; ++b)
+        if (((modes >> (2 * b)) & 3) >= 2) return true;
+    return false;
 }
 
 __device__ __forceinline__ int64_t seg_begin(const GraphView &g, int64_t x, int t) {

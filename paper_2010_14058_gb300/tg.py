@@ -50,7 +50,7 @@ class tg_options(ctypes.Structure):
     _fields_ = [("light_edge_max_degree", ctypes.c_int32), ("light_anchor_max_wedges", ctypes.c_int32),
                 ("anchor_table_budget_mb", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("cycle_budget_mb", ctypes.c_int32), ("hub_min_wedges", ctypes.c_int32),
-                ("hub_l2_mb", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("hub_l2_mb", ctypes.c_int32), ("isect_modes", ctypes.c_int32)]
 
 
 SIGNATURES = {

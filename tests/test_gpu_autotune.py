@@ -42,3 +42,20 @@ def test_tune_batch():
     entry = autotune.tune(rp, col, ty, 3, node_off=u["node_off"], space=space, reps=1, store=False)
     new_values = sum(len([v for v in vals if v != autotune.DEFAULTS[k]]) for k, vals in space.items())
     assert entry["ngraphs"] == 6 and len(entry["trials"]) == 1 + new_values
+
+
+def test_tune_intersection_modes_per_bucket():
+    # the per-bucket intersection choice (binary search / merge / cost model)
+    # never changes a count; the tuned choice gives the oracle's totals
+    g = graphgen.chung_lu(4000, 40000, 2.1, 1500.0, 3, 23, type_zipf=1.2)
+    rp, col, ty = tg.to_device(g)
+    space = {f"isect_bucket_{b}": [1, 2, 3] for b in range(4)}
+    entry = autotune.tune(rp, col, ty, g["L"], space=space, reps=1, store=False)
+    assert len(entry["trials"]) == 1 + 4 * 2
+    assert 0 <= entry["options"]["isect_modes"] < 256
+    h = tg.tg_build(rp, col, ty, g["L"], options=entry["options"])
+    gl = torch.zeros(tg.tg_layout(g["L"], 4)["global_slots"], dtype=torch.int64, device="cuda")
+    tg.tg_count(h, 4, None, gl)
+    assert tg.tg_query_status(h) == 0
+    h.free()
+    np.testing.assert_array_equal(gl.cpu().numpy(), oracle.paper(g)[1])

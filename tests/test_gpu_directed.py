@@ -20,7 +20,7 @@ if not torch.cuda.is_available():
 import paper_2010_14058_gb300 as tg  # noqa: E402
 
 
-def gpu_directed(g, host=False):
+def gpu_directed(g, host=False, options=None):
     L = g["L"]
     lay = tg.tg_directed_layout(L)
     if host:
@@ -36,7 +36,7 @@ def gpu_directed(g, host=False):
     rp = torch.as_tensor(np.ascontiguousarray(g["out_row_ptr"], dtype=np.int64), device="cuda")
     col = torch.as_tensor(np.ascontiguousarray(g["out_col"], dtype=np.int32), device="cuda")
     ty = torch.as_tensor(np.ascontiguousarray(g["types"], dtype=np.uint8), device="cuda")
-    h = tg.tg_build_directed(rp, col, ty, L)
+    h = tg.tg_build_directed(rp, col, ty, L, options=options)
     pe = torch.zeros((h.m, lay["per_edge_slots"]), dtype=torch.int32, device="cuda")
     gl = torch.zeros(lay["global_slots"], dtype=torch.int64, device="cuda")
     tg.tg_count_directed3(h, pe, gl)
@@ -45,8 +45,8 @@ def gpu_directed(g, host=False):
     return pe.cpu().numpy().view(np.uint32).astype(np.int64), gl.cpu().numpy(), st
 
 
-def assert_directed_parity(g, reference="paper", host=False):
-    pe, gl, st = gpu_directed(g, host=host)
+def assert_directed_parity(g, reference="paper", host=False, options=None):
+    pe, gl, st = gpu_directed(g, host=host, options=options)
     assert st == 0, tg.STATUS[st]
     pe_o, gl_o = (oracle.directed3_brute if reference == "brute" else oracle.directed3)(g)
     np.testing.assert_array_equal(pe, pe_o)
@@ -119,3 +119,10 @@ def test_invalid_oriented_graphs_are_rejected(arcs):
     with pytest.raises(tg.TGError) as e:
         gpu_directed(g, host=True)
     assert e.value.name == "TG_ERR_INVALID_GRAPH"
+
+
+@pytest.mark.parametrize("modes", [0b01010101, 0b10101010])
+def test_intersection_methods(modes):
+    # every typed intersection by binary search, then by merge
+    u = graphgen.chung_lu(5000, 50000, 2.1, 1500.0, 3, 91, type_zipf=1.2)
+    assert_directed_parity(oriented_from_undirected(u, 92), options={"isect_modes": modes})

@@ -98,6 +98,21 @@ def test_chung_lu_with_hubs(options):
     assert_parity(g, options=options)
 
 
+# typed set intersection forced to one method in every length bucket
+ALL_BINARY = {"isect_modes": 0b01010101}
+ALL_MERGE = {"isect_modes": 0b10101010}
+
+
+@pytest.mark.parametrize("options", [ALL_BINARY, ALL_MERGE])
+def test_intersection_methods(options):
+    # hubs give long typed segments on both sides (merge windows advance on
+    # either side, equal last entries, ragged windows), leaves short ones
+    assert_parity(graphgen.chung_lu(4000, 30000, 2.1, 1200.0, 5, 77, type_zipf=1.2), options=options)
+    assert_parity(graphgen.erdos_renyi(300, 20000, 2, 78), options=options)            # dense: |A| ~ |B|
+    for seed in range(4):
+        assert_parity(random_graph(12 + seed, 0.7, 2, 9300 + seed), options=options, reference="brute")
+
+
 def test_global_t_list_path():
     # edge (0,1) has |T| = 9000 > the shared-memory T list of a CTA
     a = 9000
