@@ -64,8 +64,12 @@ def parse():
     ap.add_argument("--tune-graphs", type=int, default=256,
                     help="batched: graphs of the sub-batch the autotuner measures (0: library defaults)")
     ap.add_argument("--rate", type=float, default=200_000 / 60, help="serving: Poisson arrivals per second")
-    ap.add_argument("--duration", type=float, default=1.0, help="serving: seconds of arrivals")
-    ap.add_argument("--pool", type=int, default=128, help="serving: distinct request graphs")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of measured arrivals")
+    ap.add_argument("--serve-warmup", type=float, default=10.0,
+                    help="serving: seconds of arrivals before the measured window")
+    ap.add_argument("--plain-seconds", type=float, default=10.0,
+                    help="serving: measured seconds of the trace replayed by the plain sequential server")
+    ap.add_argument("--pool", type=int, default=1024, help="serving: distinct request graphs")
     ap.add_argument("--oracle-fraction", type=float, default=0.02,
                     help="batched / serve: fraction of graphs (requests) whose totals the CPU oracle checks")
     ap.add_argument("--oracle-seconds", type=float, default=240.0,
@@ -733,6 +737,9 @@ def cpu_baseline(g: dict, budget_edges: int = 1000, heaviest: int = 100, thin: i
     import oracle
     m = g["m"]
     _, _, proxy = edge_cost_proxy(g)
+    full = m <= 20_000                                  # small graphs: every edge timed, nothing extrapolated
+    if full:
+        budget_edges, thin = m, 1
     strata = oracle_design(proxy, budget_edges, heaviest)
     t = time.perf_counter()
     og = oracle.OpenGraph(g)
@@ -745,6 +752,12 @@ def cpu_baseline(g: dict, budget_edges: int = 1000, heaviest: int = 100, thin: i
     t_all = t_open + allc["work_thread_s"] / cores
     t_one = t_open + one["work_thread_s"]
     n_sample = sum(len(x[2]) for x in strata)
+    if full:
+        return {"value": round(m / t_all, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+                "value_1thread": round(m / t_one, 2), "full_graph_s": round(t_all, 3),
+                "full_graph_s_1thread": round(t_one, 3), "open_s": round(t_open, 3),
+                "sample": f"all {m} edges timed (no extrapolation): all cores in {allc['sample_wall_s']:.2f} s, "
+                          f"one thread in {one['sample_wall_s']:.2f} s, plus the graph preparation"}
     return {"value": round(m / t_all, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
             "value_1thread": round(m / t_one, 2), "full_graph_s_estimate": round(t_all, 1),
             "full_graph_s_estimate_1thread": round(t_one, 1), "rel_se": round(allc["work_rel_se"], 4),
@@ -769,7 +782,8 @@ def run_reference(args):
     g = graphgen.workload(args.workload)
     m = g["m"]
     _, _, proxy = edge_cost_proxy(g)
-    strata = oracle_design(proxy)
+    full = m <= 20_000                                  # small graphs: every edge timed, as in cpu_baseline
+    strata = oracle_design(proxy, m if full else 1000)
     t = time.perf_counter()
     og = oracle.OpenGraph(g)
     t_open = time.perf_counter() - t
@@ -782,7 +796,7 @@ def run_reference(args):
         ests.append(t_open + r["work_thread_s"] / cores)
         walls.append(r["sample_wall_s"])
         ses.append(r["work_rel_se"])
-    one = oracle_estimate(og, strata, 1, thin=10)
+    one = oracle_estimate(og, strata, 1, thin=1 if full else 10)
     og.close()
     t_full = float(np.mean(ests))
     value = m / t_full
@@ -968,48 +982,74 @@ def run_batched(args):
 def run_serve(args):
     """Serving form: open-loop Poisson arrivals of typed graphs (Chung-Lu
     gamma = 2.2, edges log-uniform in [100, 1e6], n = m/5, L uniform 3..8)
-    drawn from a seeded pool, served with admission by a 40 GB device budget,
-    micro-batching and 4 overlapped workers; the same trace through a plain
-    sequential server (one worker, no batching).  Reports p50/p99 latency
-    and sustained edges/s of both, and whether every result is identical."""
+    drawn from a seeded pool, for a warm-up and then the measured window;
+    served with admission by a 40 GB device budget, micro-batching and 4
+    overlapped workers, with and without 16 GB of resident handles.  The
+    plain sequential server (one worker, no micro-batching, the same resident
+    cache) replays the trace up to warm-up + plain_seconds.  Reports p50/p99
+    latency and sustained edges/s of each over its measured window, and
+    whether every result is identical."""
     import torch
 
     from paper_2010_14058_gb300 import build as tgbuild
     from paper_2010_14058_gb300 import serve
     torch.cuda.set_device(0)
     tgbuild.build()
+
+    def log(msg):
+        print(f"[serve] {msg}", file=sys.stderr, flush=True)
+
     t = time.perf_counter()
     pool = serve.request_pool(args.pool, seed=20201029 + 5)
     gen_s = time.perf_counter() - t
-    trace = serve.poisson_trace(pool, args.rate, args.duration, seed=20201029 + 5)
-    warm = serve.poisson_trace(pool, 200.0, 0.2, seed=1)
-    serve.Server(workers=4).run(warm)
-    srv = serve.Server(budget_bytes=40 << 30, workers=4, resident_bytes=16 << 30)
-    served = srv.run(trace)
+    w0 = args.serve_warmup
+    trace = serve.poisson_trace(pool, args.rate, w0 + args.duration, seed=20201029 + 5)
+    log(f"pool of {len(pool)} graphs in {gen_s:.1f} s; {len(trace)} requests, "
+        f"{sum(r.m for r in trace)} edges")
+    serve.Server(workers=4).run(serve.poisson_trace(pool, 200.0, 0.2, seed=1))      # first launches, pool
+    runs = {}
+    for name, resident in (("served", 16 << 30), ("served_no_resident", 0)):
+        t = time.perf_counter()
+        srv = serve.Server(budget_bytes=40 << 30, workers=4, resident_bytes=resident)
+        runs[name] = srv.run(trace)
+        srv.close()
+        log(f"{name}: {time.perf_counter() - t:.1f} s")
+    prefix = [r for r in trace if r.arrival < w0 + args.plain_seconds]
+    t = time.perf_counter()
+    srv = serve.Server(budget_bytes=40 << 30, workers=1, batching=False, resident_bytes=16 << 30)
+    plain = srv.run(prefix)
     srv.close()
-    plain = serve.Server(budget_bytes=40 << 30, workers=1, batching=False).run(trace)
-    same = all(np.array_equal(a.totals, b.totals) and a.status == 0 and b.status == 0 for a, b in zip(served, plain))
+    log(f"plain sequential on {len(prefix)} requests: {time.perf_counter() - t:.1f} s")
+    by_rid = {name: {r.rid: r for r in res} for name, res in runs.items()}
+    same = all(r.status == 0 for res in runs.values() for r in res) and all(r.status == 0 for r in plain)
+    same = same and all(np.array_equal(a.totals, by_rid["served_no_resident"][a.rid].totals) for a in runs["served"])
+    same = same and all(np.array_equal(p.totals, by_rid["served"][p.rid].totals) for p in plain)
     # CPU baseline: the oracle on a seeded 2% sample of the requests, which
     # also checks their totals
     rng = np.random.default_rng(CPU_SEED + 5)
     k_s = max(1, int(np.ceil(args.oracle_fraction * len(trace))))
     sample = np.sort(rng.choice(len(trace), size=min(k_s, len(trace)), replace=False)).tolist()
-    by_rid = {r.rid: r for r in served}
 
     def request_graph(x):
         r = trace[x]
         return {"n": r.n, "m": r.m, "L": r.L, "row_ptr": r.row_ptr, "col": r.col, "types": r.types}
 
-    cpu = cpu_baseline_sample(request_graph, lambda x: by_rid[trace[x].rid].totals, sample,
+    cpu = cpu_baseline_sample(request_graph, lambda x: by_rid["served"][trace[x].rid].totals, sample,
                               [trace[x].m for x in sample], args.oracle_seconds)
-    s1, s0 = serve.summarize(served, trace), serve.summarize(plain, trace)
-    line = {"metric": METRIC + ", serving form", "value": s1["edges_per_s"], "unit": UNIT, "n_gpus": 1,
+    summ = {name: serve.summarize(res, trace, window_start=w0) for name, res in runs.items()}
+    s0 = serve.summarize(plain, prefix, window_start=w0)
+    line = {"metric": METRIC + ", serving form", "value": summ["served"]["edges_per_s"], "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "poisson_requests", "rate_per_s": args.rate, "arrival_seconds": args.duration,
-                       "requests": len(trace), "edges": s1["edges"], "pool_graphs": args.pool,
+            "config": {"workload": "poisson_requests", "rate_per_s": args.rate, "warmup_seconds": w0,
+                       "arrival_seconds": args.duration, "requests": len(trace),
+                       "edges": int(sum(r.m for r in trace)), "pool_graphs": args.pool,
                        "request_mix": "Chung-Lu gamma=2.2, m log-uniform [100, 1e6], n=m/5, L uniform 3..8",
-                       "budget_gb": 40, "resident_gb": 16, "workers": 4, "pool_generation_s": round(gen_s, 1)},
-            "served": s1, "plain_sequential": s0, "results_identical": bool(same), "cpu_baseline": cpu}
+                       "budget_gb": 40, "resident_gb": 16, "workers": 4, "pool_generation_s": round(gen_s, 1),
+                       "plain_sequential_trace": f"arrivals before {w0 + args.plain_seconds:.0f} s "
+                                                 f"({len(prefix)} requests), one worker, no micro-batching, "
+                                                 f"the same 16 GB resident cache"},
+            "served": summ["served"], "served_no_resident": summ["served_no_resident"], "plain_sequential": s0,
+            "results_identical": bool(same), "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 

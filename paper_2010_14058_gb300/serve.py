@@ -303,12 +303,16 @@ class Server:
         return sorted(results, key=lambda r: r.rid)
 
 
-def summarize(results: list, requests: list) -> dict:
-    """Latency percentiles and throughput of a served trace."""
+def summarize(results: list, requests: list, window_start: float = 0.0) -> dict:
+    """Latency percentiles and throughput of a served trace, over the
+    requests that arrived at or after `window_start` seconds (the ones
+    before it warm the server up): edges of those requests / (last
+    completion - window_start)."""
     m_of = {r.rid: r.m for r in requests}
+    results = [r for r in results if r.arrival >= window_start]
     lat = np.array([r.latency for r in results])
     edges = sum(m_of[r.rid] for r in results)
-    span = max(r.done for r in results) - min(r.arrival for r in results)
+    span = max(r.done for r in results) - max(window_start, min(r.arrival for r in results))
     return {"requests": len(results), "edges": int(edges), "span_s": round(float(span), 3),
             "edges_per_s": round(edges / span, 1), "p50_ms": round(float(np.percentile(lat, 50) * 1e3), 3),
             "p99_ms": round(float(np.percentile(lat, 99) * 1e3), 3), "mean_ms": round(float(lat.mean() * 1e3), 3),
