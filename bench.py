@@ -135,6 +135,48 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+def gpu_local_cpus(index: int) -> list | None:
+    """Host CPUs attached to GPU `index` (its PCI device's local_cpulist),
+    or None when that cannot be read."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{dom[-4:].lower()}:{rest.lower()}/local_cpulist"
+        with open(path) as f:
+            spec = f.read().strip()
+        cpus = []
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus += list(range(int(a), int(b or a) + 1))
+        allowed = os.sched_getaffinity(0)
+        cpus = [c for c in cpus if c in allowed]
+        return cpus or None
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None
+
+
+class NearGpu:
+    """Runs a block on the host CPUs attached to the GPU, so that pinned
+    buffers allocated inside it are placed in that CPU's memory (first touch)
+    and host-device copies take the direct link; restores the affinity."""
+
+    def __init__(self, index: int):
+        self.cpus = gpu_local_cpus(index)
+        self.saved = None
+
+    def __enter__(self):
+        if self.cpus:
+            self.saved = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, self.cpus)
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
+        return False
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -380,8 +422,11 @@ def run_ours(args):
 
     # end-to-end figures first, right after the timed region (before the
     # roofline work below allocates anything)
-    # end to end through host buffers
+    # end to end through host buffers (pinned buffers in the memory of the
+    # host CPUs attached to this GPU)
     e2e = None
+    near = NearGpu(torch.cuda.current_device())
+    near.__enter__()
     if not args.no_e2e and rank == 0:
         h_rp = torch.from_numpy(np.ascontiguousarray(g["row_ptr"])).pin_memory()
         h_col = torch.from_numpy(np.ascontiguousarray(g["col"])).pin_memory()
@@ -447,6 +492,10 @@ def run_ours(args):
         e2e_sparse = {"value": round(m * args.e2e_steps / el, 1), "unit": UNIT, "h2d_bytes_per_step": int(bi),
                       "d2h_bytes_per_step": int(bo), "nonzero_pairs": int(nnz),
                       "pairs_per_edge": round(nnz / max(m, 1), 2)}
+    near.__exit__(None, None, None)
+    if e2e is not None:
+        e2e["host_cpus"] = (f"{len(near.cpus)} CPUs attached to the GPU ({near.cpus[0]}-{near.cpus[-1]})"
+                            if near.cpus else "unpinned (no local CPU list)")
 
 
     # roofline: algorithmic bytes of each count kernel per step over its

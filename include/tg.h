@@ -328,6 +328,16 @@ tg_status tg_count_position_aware(tg_graph *g, uint32_t *per_edge_out, int64_t *
 tg_status tg_count_batch(tg_graph *g, int32_t k, uint32_t *per_edge_out, int64_t *global_out,
                          void *stream);
 
+/* The list form of the batched call (Problem 2 for several graphs the
+ * caller already holds as handles): counts handles gs[0..ngraphs-1] (each a
+ * single graph or a batch, any L) on one stream, global totals only, into
+ * global_out int64 (host or device): handle h's totals, ngraphs_h *
+ * global_slots(L_h, k) values, follow those of handles 0..h-1.  Per-edge
+ * rows: call tg_count per handle.  Device-detected errors go to each
+ * handle's status word (tg_query_status).  Errors: TG_ERR_INVALID_ARG
+ * (NULL, k, ngraphs < 0), TG_ERR_OOM, TG_ERR_CUDA. */
+tg_status tg_count_handles(tg_graph *const *gs, int32_t ngraphs, int32_t k, int64_t *global_out, void *stream);
+
 /* Synchronises the handle's last stream and returns the first error
  * recorded in its device status word (TG_OK if none), then clears it. */
 tg_status tg_query_status(tg_graph *g);

@@ -44,14 +44,14 @@ SPACE = {
     "light_anchor_max_wedges": [64, 256, 1024, 2048],
     "hub_min_wedges": [1 << 14, 1 << 16, 1 << 18, 1 << 20],
     "ctas_per_sm": [2, 3, 4],
-    "hub_l2_mb": [64, 128, 256],
+    "hub_l2_mb": [96, 192, 256],
     "isect_bucket_0": [1, 2, 3],
     "isect_bucket_1": [1, 2, 3],
     "isect_bucket_2": [1, 2, 3],
     "isect_bucket_3": [1, 2, 3],
 }
-DEFAULTS = {"light_edge_max_degree": 256, "light_anchor_max_wedges": 64, "hub_min_wedges": 1 << 16, "ctas_per_sm": 3,
-            "hub_l2_mb": 128, "isect_bucket_0": 1, "isect_bucket_1": 1, "isect_bucket_2": 1, "isect_bucket_3": 1}
+DEFAULTS = {"light_edge_max_degree": 256, "light_anchor_max_wedges": 64, "hub_min_wedges": 1 << 14, "ctas_per_sm": 3,
+            "hub_l2_mb": 192, "isect_bucket_0": 1, "isect_bucket_1": 1, "isect_bucket_2": 1, "isect_bucket_3": 1}
 
 
 def library_options(options: dict) -> dict:

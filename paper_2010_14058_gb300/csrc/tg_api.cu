@@ -342,6 +342,22 @@ tg_status tg_count(tg_graph *gh, int32_t k, uint32_t *per_edge_out, int64_t *glo
     });
 }
 
+tg_status tg_count_handles(tg_graph *const *gs, int32_t ngraphs, int32_t k, int64_t *global_out, void *stream) {
+    return guarded([&] {
+        if (ngraphs < 0 || (ngraphs > 0 && (!gs || !global_out)) || (k != 3 && k != 4))
+            throw Error{TG_ERR_INVALID_ARG, "args"};
+        for (int32_t h = 0; h < ngraphs; ++h)
+            if (!gs[h]) throw Error{TG_ERR_INVALID_ARG, "NULL handle"};
+        int64_t off = 0;
+        for (int32_t h = 0; h < ngraphs; ++h) {
+            const Graph &G = gs[h]->g;
+            const tg_status st = tg_count(gs[h], k, nullptr, global_out + off, stream);
+            if (st != TG_OK) throw Error{st, "tg_count"};
+            off += (int64_t)G.ngraphs * tg::global_slots(G.L, k);
+        }
+    });
+}
+
 tg_status tg_count_position_aware(tg_graph *gh, uint32_t *per_edge_out, int64_t *global_out, void *stream) {
     return guarded([&] {
         if (!gh) throw Error{TG_ERR_INVALID_ARG, "NULL"};

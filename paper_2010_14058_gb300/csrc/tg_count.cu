@@ -53,7 +53,7 @@ namespace {
 
 constexpr int kAnchorThreads = 512;         // k_wedge_heavy: one anchor per CTA
 constexpr int kLightAnchorWarps = 4;        // k_wedge_light: one anchor per warp
-constexpr int kTile = 2048;                 // edges per tile of k_epi4 and k_edge3
+constexpr int kTile = 2048;                 // most edges per tile of k_epi4 and k_edge3 (tile_edges)
 
 __device__ __forceinline__ unsigned warp_sum_u32(unsigned v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1766,11 +1766,21 @@ int grid_for(int64_t items, int per_block, int cap) {
 
 }  // namespace
 
+// Edges per tile: kTile, or fewer for a small handle so that its tiles
+// still fill the GPU (at least about 12 tiles per SM, 64 edges or more each).
+static int64_t tile_edges(const Graph &G) {
+    const int64_t want = (G.m + (int64_t)sm_count() * 12 - 1) / ((int64_t)sm_count() * 12);
+    int64_t t = 64;
+    while (t < want && t < kTile) t <<= 1;
+    return t;
+}
+
 static std::vector<Tile> make_tiles(const Graph &G, int64_t e_begin, int64_t e_end) {
     std::vector<Tile> tiles;
+    const int64_t te = tile_edges(G);
     for (int gi = 0; gi < G.ngraphs; ++gi) {
         int64_t b = std::max(e_begin, G.h_edge_off[gi]), e = std::min(e_end, G.h_edge_off[gi + 1]);
-        for (int64_t x = b; x < e; x += kTile) tiles.push_back(Tile{x, std::min(e, x + kTile), gi, 0});
+        for (int64_t x = b; x < e; x += te) tiles.push_back(Tile{x, std::min(e, x + te), gi, 0});
     }
     return tiles;
 }
@@ -1789,8 +1799,9 @@ static void plan_chunks(Graph &G) {
     };
     // tile index ranges follow graph boundaries (make_tiles emits graph after graph)
     std::vector<int64_t> tile_off(G.ngraphs + 1, 0);
+    const int64_t te = tile_edges(G);
     for (int gi = 0; gi < G.ngraphs; ++gi)
-        tile_off[gi + 1] = tile_off[gi] + (G.h_edge_off[gi + 1] - G.h_edge_off[gi] + kTile - 1) / kTile;
+        tile_off[gi + 1] = tile_off[gi] + (G.h_edge_off[gi + 1] - G.h_edge_off[gi] + te - 1) / te;
     int g0 = 0;
     int64_t widest = 0;
     while (g0 < G.ngraphs) {

@@ -294,8 +294,8 @@ inline void fill_defaults(tg_options *o) {
     o->anchor_table_budget_mb = 4096;
     o->ctas_per_sm = 3;
     o->cycle_budget_mb = 16384;
-    o->hub_min_wedges = 1 << 16;
-    o->hub_l2_mb = 128;
+    o->hub_min_wedges = 1 << 14;
+    o->hub_l2_mb = 192;
 }
 
 // number of SMs of the current device

@@ -77,6 +77,7 @@ SIGNATURES = {
     "tg_build_directed": ([_i64, _i64, _vp, _vp, _vp, _i32, ctypes.POINTER(tg_options), _vp, ctypes.POINTER(_vp)],
                           _i32),
     "tg_count_directed3": ([_vp, _vp, _vp, _vp], _i32),
+    "tg_count_handles": ([_vp, _i32, _i32, _vp, _vp], _i32),
     "tg_pa_labelling": ([_i32, _i32, _i64, _vp], _i32),
     "tg_pa_slot_class": ([_i32, _i32, _i32, _i64, ctypes.POINTER(_i64)], _i32),
     "tg_count_position_aware": ([_vp, _vp, _vp, _vp], _i32),
@@ -289,6 +290,13 @@ def tg_directed_class_code(L: int, rank: int) -> tuple:
 def tg_count_directed3(g: Graph, per_edge_out=None, global_out=None, stream=None) -> None:
     _check(load().tg_count_directed3(g.handle, _ptr(per_edge_out), _ptr(global_out), _stream(stream)),
            "tg_count_directed3")
+
+
+def tg_count_handles(graphs: list, k: int, global_out, stream=None) -> None:
+    """Global totals of several handles on one stream, concatenated in order
+    (handle h: ngraphs_h x global_slots(L_h, k) values)."""
+    arr = (_vp * max(len(graphs), 1))(*[g.handle for g in graphs])
+    _check(load().tg_count_handles(arr, len(graphs), k, _ptr(global_out), _stream(stream)), "tg_count_handles")
 
 
 def tg_free(g: Graph) -> None:

@@ -75,9 +75,15 @@ def test_degenerate_graphs():
                       options=opt)
 
 
+def test_large_tiles_and_ragged_tail():
+    # 60,001 edges: 2,048-edge epilogue tiles at this size (29 full, one ragged)
+    assert_parity(graphgen.erdos_renyi(4000, 60001, 3, 93), k=3)
+    assert_parity(graphgen.erdos_renyi(4000, 60001, 3, 93))
+
+
 @pytest.mark.parametrize("L", [1, 2, 5, 8])
 def test_er_several_tiles_and_ragged_tail(L):
-    # 9,123 edges: 4 full tiles of 2,048 edges plus a ragged one
+    # 9,123 edges: 142 full epilogue tiles plus a ragged one (64-edge tiles at this size on 152 SMs)
     g = graphgen.erdos_renyi(1500, 9123, L, 31 + L)
     assert_parity(g)
 
@@ -294,3 +300,24 @@ def test_degree_above_65535_uses_wide_sums():
     ids = np.array([0, 5, 59, 60, 61, 5000, 70_059, nc + leaves, nc + leaves + 7, g["m"] - 1])
     rows_o, _ = oracle.paper_edges(g, ids)
     np.testing.assert_array_equal(pe[ids], rows_o)
+
+
+def test_count_handles_list_form():
+    # several handles the caller holds (single graphs of different L and a
+    # batch), counted on one stream into one concatenated totals array
+    singles = [graphgen.erdos_renyi(300, 1500, 3, 501), graphgen.chung_lu(2000, 9000, 2.1, 400.0, 5, 502)]
+    parts = [graphgen.erdos_renyi(80 + 20 * x, 300 + 100 * x, 2, 510 + x) for x in range(3)]
+    node_off, rp, col, ty = concat_graphs(parts)
+    handles = [tg.tg_build(*tg.to_device(g), g["L"]) for g in singles]
+    handles.append(tg.tg_build_batch(node_off, torch.as_tensor(rp, device="cuda"), torch.as_tensor(col, device="cuda"),
+                                     torch.as_tensor(ty, device="cuda"), 2))
+    want = [oracle.paper(g)[1] for g in singles] + [oracle.paper(g)[1] for g in parts]
+    total = sum(len(w) for w in want)
+    for host in (False, True):
+        out = np.zeros(total, dtype=np.int64) if host else torch.zeros(total, dtype=torch.int64, device="cuda")
+        tg.tg_count_handles(handles, 4, out)
+        got = out if host else out.cpu().numpy()
+        np.testing.assert_array_equal(got, np.concatenate(want))
+    assert all(tg.tg_query_status(h) == 0 for h in handles)
+    for h in handles:
+        h.free()

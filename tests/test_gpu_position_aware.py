@@ -1,6 +1,6 @@
 """Position-aware typed graphlets (Sec. 5, Def. 8) on the GPU, through the C
 ABI, bit-exact against the oracle: per-edge rows (uint32) and per-class
-totals (int64) on tiny graphs, graphs spanning several 2,048-edge tiles with
+totals (int64) on tiny graphs, graphs spanning many epilogue tiles with
 a ragged tail (L = 2, 5, 8), a skewed Chung-Lu graph with every wedge anchor
 routed through each kernel variant, a batch handle, host buffers; and, on a
 larger graph, the position-aware rows and totals merge into the typed ones of
@@ -68,7 +68,7 @@ def test_degenerate_graphs():
 
 @pytest.mark.parametrize("L", [2, 5, 8])
 def test_er_several_tiles_and_ragged_tail(L):
-    # 9,123 edges: 4 full tiles of 2,048 edges plus a ragged one
+    # 9,123 edges: 142 full epilogue tiles plus a ragged one (64-edge tiles at this size on 152 SMs)
     assert_pa(graphgen.erdos_renyi(1500, 9123, L, 31 + L))
 
 
