@@ -503,6 +503,9 @@ __global__ void __launch_bounds__(kAnchorThreads, 2) k_wedge_heavy(GraphView g, 
 // number of type-t neighbours v of u below u that are adjacent to w),
 // phase 1 adds h_u[w][t] - [t = t_v] to the 4-cycle slot of (v, w) and the
 // per-(v, type of w) sums to the slot of (u, v), phase 2 clears the rows.
+// All hubs of a chunk run in one persistent launch (k_wedge_hub below):
+// hubs in groups, every (group, phase) cut into tickets, ticket waits on the
+// phases it depends on.
 
 struct HubView {
     const int32_t *hubs;        // hub node ids
