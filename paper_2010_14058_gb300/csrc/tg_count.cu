@@ -2089,7 +2089,9 @@ static void plan_hubs(Graph &G, cudaStream_t s) {
     const int64_t ctas = (int64_t)sm_count() * kHubCtasPerSm;
     G.hub_packed = G.max_degree < 65536;
     G.hub_stride = hub_words_per_table(G);
-    const int64_t gmax = hub_group_max(G);
+    // no more tables per buffer than there are hubs (a small graph's budget
+    // would otherwise reserve hub_l2_mb for a few hubs)
+    const int64_t gmax = std::min<int64_t>(hub_group_max(G), std::max<int64_t>(G.n_hubs, 1));
     G.hub_buf_words = gmax * G.hub_stride;
     const size_t tbytes = sizeof(uint32_t) * (size_t)(kHubBuffers * G.hub_buf_words);
     G.hub_tables.alloc(tbytes);
