@@ -189,12 +189,14 @@ def load_peaks():
 # DRAM bytes (read + write) per launch of a kernel, from the ncu capture
 # summarised under profiles/ for that workload and the current kernel code
 # (an entry is removed when its kernel changes).
-TRAFFIC = {("cl_large", "k_clique_big"): 2.581471e9}
+TRAFFIC = {}
 
 # Issue-limited peak of the 4-clique lookups: 152 SMs x 4 schedulers x 32
 # lanes x the maximum SM clock give the lane-instruction rate; one lookup
-# (load the N+ entry, hash, one 16-byte shared-memory bucket load, four
-# compares, the typed hit count) takes at least LOOKUP_INSTR of them.
+# (load the N+ entry, mask its id, distance to the largest member clamped
+# to the window, word index, one 32-bit shared-memory load, bit extract,
+# the typed hit count in three, the hash-range check in three) takes at
+# least LOOKUP_INSTR of them.
 LOOKUP_INSTR = 15
 
 
@@ -542,7 +544,7 @@ def run_ours(args):
                         "peak_kind": f"derived: 152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock under "
                                      f"load) / {LOOKUP_INSTR} lane instructions per lookup",
                         "unit": "Glookups/s", "frac": round(ach / pk_alu, 5), "algorithmic_ops": lookups[top],
-                        "ops": "hash-set lookups of the 4-clique scan, sum over edges of sum_{w in T} |N+(w)|",
+                        "ops": "set-of-T lookups of the 4-clique scan, sum over edges of sum_{w in T} |N+(w)|",
                         "ms_per_step": round(ms_k, 3), "traffic": TRAFFIC.get((args.workload, top))}
         elif top in per_kernel and "achieved_gbs" in per_kernel[top]:
             pk = per_kernel[top]

@@ -1002,21 +1002,35 @@ __device__ __forceinline__ int type_of_index(const int32_t *ts, int32_t k) {
 // t and x of type t', each pair once, from its lower-priority node w: x is
 // then one of w's higher-priority neighbours N+(w) (a contiguous list of
 // (type << 29 | id) entries grouped by type, built once per graph).  So
-// every member w of T scans N+(w) and looks each entry up in a hash set of
-// T: sum_{w in T} |N+(w)| lookups, most of them hits.
+// every member w of T scans N+(w) and looks each entry up in a set of T:
+// sum_{w in T} |N+(w)| lookups.
 //
-// The set: buckets of 4 slots (one 16-byte load per lookup), slots taken
-// in order by atomicCAS, -1 when empty, so a bucket whose last slot is
-// empty is not full and a lookup stops there; with at least 4 slots per
-// member almost every lookup reads one bucket.
+// The set.  Ids are degree ranks, and on power-law graphs the members of T
+// and the entries of their N+ lists crowd at the top of the id range: the
+// members within B below the largest member tmax (B = 2^13 for a warp's
+// edge, 2^15 for a CTA's) take over 98% of the lookups on the graphs
+// measured.  When at least 3/4 of the members lie in that window, they are
+// a bitmap indexed by tmax - x (one 32-bit shared-memory load per lookup)
+// and the members below it a hash set, looked up only by entries between
+// the smallest member and the window.  Otherwise all members are in the
+// hash set.  The hash set: buckets of 4 slots (one 16-byte load per
+// lookup), slots taken in order by atomicCAS, -1 when empty, so a bucket
+// whose last slot is empty is not full and a lookup stops there; with at
+// least 4 slots per member almost every lookup reads one bucket.  The
+// bitmap is all zero between edges: the words of an edge's members are
+// cleared after its scan.
 // The scan: one whole warp per member, lanes striding over N+(w) (coalesced
 // loads, 4 in flight per lane) -- the lists behind almost all lookups are
-// tens to thousands of entries long.  Each lane counts its hits by type of
-// x in the 8-bit fields of one 64-bit register (no warp-wide step inside
-// the scan, so a lane's four lookups overlap); the warp sums the fields
-// with __reduce_add_sync before any can reach 255 and when the member type
-// t changes (T is sorted by type), and lane q adds the count for x of type
-// q to K[t][q].
+// tens to thousands of entries long.  A window lookup has no branch; the
+// hash lookups (entries between the smallest member and the window, and
+// every entry within T's range in the hash form) are taken by the lanes
+// that need them, once per round of four, when any lane of the warp
+// does.  Each lane counts its hits by
+// type of x in the fields of one register (no warp-wide step inside the
+// scan, so a lane's four lookups overlap); the warp sums the fields with
+// __reduce_add_sync before any can overflow and when the member type t
+// changes (T is sorted by type), and lane q adds the count for x of type q
+// to K[t][q].
 
 __device__ __forceinline__ uint32_t t_hash(int32_t x, int lgnb) {      // lgnb >= 1
     return ((uint32_t)x * 2654435761u) >> (32 - lgnb);
@@ -1026,14 +1040,15 @@ __device__ __forceinline__ void group_sync(int gsize) {
     if (gsize > 32) __syncthreads(); else __syncwarp();
 }
 
-// the set of T (nT distinct ids) in 2^lgnb buckets, built by the group
-__device__ void tset_build(const int32_t *T, int32_t nT, int4 *set, int lgnb, int gsize, int gr) {
+// the members x <= xmax of T (nT distinct ids) in 2^lgnb buckets, built by the group
+__device__ void tset_build(const int32_t *T, int32_t nT, int4 *set, int lgnb, int gsize, int gr, int32_t xmax) {
     const int nb = 1 << lgnb;
     int32_t *slot = reinterpret_cast<int32_t *>(set);
     for (int k = gr; k < 4 * nb; k += gsize) slot[k] = -1;
     group_sync(gsize);
     for (int32_t k = gr; k < nT; k += gsize) {
         const int32_t x = T[k];
+        if (x > xmax) continue;
         uint32_t b = t_hash(x, lgnb);
         bool done = false;
         for (int probe = 0; probe < nb && !done; ++probe) {   // 4 nb >= 2 nT: a free slot exists
@@ -1076,16 +1091,69 @@ __device__ __forceinline__ int tset_lgnb(int32_t nT, int max_slots) {
     return (4 << lg) <= max_slots ? lg : -1;
 }
 
-// Per-lane hit counters of one warp: field q (8 bits) of `acc` counts the
+// T of one edge: the window bitmap and the hash set
+struct TWin {
+    const uint32_t *bm;         // bit d: member tmax - d, for d < wbits; word wbits / 32 is zero
+    const int4 *set;            // the members below the window (all of them in the hash form)
+    int32_t tmax, tmin, lowmax; // lowmax: the largest id the hash set may hold, else -1
+    uint32_t wbits;             // the window's width: B, or 0 in the hash form
+    uint32_t lowspan;           // ids tmin .. tmin + lowspan - 1 are looked up in the hash set
+    int lgnb;
+};
+
+// smallest and largest member of T (each type's run is in increasing id order)
+__device__ __forceinline__ void t_range(const int32_t *T, const int32_t *ts, int L, int32_t &tmin, int32_t &tmax) {
+    tmin = INT32_MAX;
+    tmax = -1;
+#pragma unroll
+    for (int q = 0; q < kMaxL; ++q) {
+        if (q < L && ts[q + 1] > ts[q]) {
+            tmin = min(tmin, T[ts[q]]);
+            tmax = max(tmax, T[ts[q + 1] - 1]);
+        }
+    }
+}
+
+// members of the group (strided by gsize from gr) below the window of B
+template <int B>
+__device__ __forceinline__ int32_t twin_below(const int32_t *T, int32_t nT, int32_t tmax, int gsize, int gr) {
+    int32_t low = 0;
+    for (int32_t k = gr; k < nT; k += gsize) low += (uint32_t)(tmax - T[k]) >= (uint32_t)B ? 1 : 0;
+    return low;
+}
+
+// sets (or, set = false, clears the words of) the window bits of the group's members
+template <int B>
+__device__ __forceinline__ void twin_bits(const int32_t *T, int32_t nT, int32_t tmax, uint32_t *bm, int gsize, int gr,
+                                          bool set) {
+    for (int32_t k = gr; k < nT; k += gsize) {
+        const uint32_t d = (uint32_t)(tmax - T[k]);
+        if (d < (uint32_t)B) {
+            if (set) atomicOr(&bm[d >> 5], 1u << (d & 31u));
+            else bm[d >> 5] = 0u;
+        }
+    }
+}
+
+// Per-lane hit counters of one warp: field q (F bits of `acc`) counts the
 // lane's hits on entries of type q; `since` counts scan rounds (at most 4
-// hits per field each) since the fields were last emptied into `kreg`, where
-// lane q holds the warp's count for type q.  Warp-uniform control flow.
+// hits per field each) since the fields were last emptied into `kreg`,
+// where lane q holds the warp's count for type q.  Two layouts: 6-bit
+// fields in 32 bits for L <= 5 (emptied every 15 rounds), 8-bit fields in
+// 64 bits otherwise (every 63).  Warp-uniform control flow.
+template <class A>
 struct CliqueAcc {
-    unsigned long long acc = 0, kreg = 0;
+    static constexpr int F = sizeof(A) == 4 ? 6 : 8;
+    static constexpr int R = ((1 << F) - 1) / 4;
+    A acc = 0;
+    unsigned long long kreg = 0;
     int since = 0;
+    __device__ __forceinline__ void add(bool hit, uint32_t ent) {
+        acc += (A)hit << (F * (ent >> kTypeShift));
+    }
     __device__ __forceinline__ void drain(int L) {
         for (int q = 0; q < L; ++q) {
-            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (8 * q)) & 0xffu);
+            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (F * q)) & ((1u << F) - 1u));
             kreg += (threadIdx.x & 31) == (unsigned)q ? (unsigned long long)v : 0ull;
         }
         acc = 0;
@@ -1094,7 +1162,8 @@ struct CliqueAcc {
 };
 
 // lanes q < L add the warp's counts to K[tw][q]
-__device__ __forceinline__ void flush_k(CliqueAcc &a, int tw, unsigned long long *K, int L, int lane, bool shared_k) {
+template <class A>
+__device__ __forceinline__ void flush_k(CliqueAcc<A> &a, int tw, unsigned long long *K, int L, int lane, bool shared_k) {
     a.drain(L);
     if (tw >= 0 && lane < L && a.kreg) {
         if (shared_k) atomicAdd(&K[tw * kMaxL + lane], a.kreg);
@@ -1103,27 +1172,85 @@ __device__ __forceinline__ void flush_k(CliqueAcc &a, int tw, unsigned long long
     a.kreg = 0;
 }
 
-// member w of T: the whole warp scans N+(w); returns |N+(w)|
-__device__ __forceinline__ int32_t scan_member(const GraphView &g, int32_t w, const int4 *set, int lgnb, CliqueAcc &a,
+// one lookup of entry `ent` (slot u of a round): the window bit (d is
+// clamped to wbits, whose word and bit are always zero) counted at once,
+// and bit u of `slow` set when the entry falls in the hash set's range
+template <class A>
+__device__ __forceinline__ void look(const TWin &tw, uint32_t ent, CliqueAcc<A> &a, unsigned &slow, int u) {
+    const int32_t x = (int32_t)(ent & (uint32_t)kIdMask);
+    const uint32_t d = min((uint32_t)(tw.tmax - x), tw.wbits);
+    const uint32_t word = tw.bm[d >> 5];
+    a.add(((word >> (d & 31u)) & 1u) != 0u, ent);
+    slow |= ((uint32_t)(x - tw.tmin) < tw.lowspan ? 1u : 0u) << u;
+}
+
+// the hash lookups of the round's slow entries, when any lane has one
+template <class A>
+__device__ __forceinline__ void look_slow(const TWin &tw, const uint32_t *ent, CliqueAcc<A> &a, unsigned slow) {
+    if (__any_sync(0xffffffffu, slow != 0u)) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if ((slow >> u) & 1u) a.add(tset_has(tw.set, tw.lgnb, (int32_t)(ent[u] & (uint32_t)kIdMask)), ent[u]);
+    }
+}
+
+// member w of T: the whole warp scans N+(w), 128 entries a round (full
+// rounds without bounds checks, then the partial one); returns |N+(w)|
+template <class A>
+__device__ __forceinline__ int32_t scan_member(const GraphView &g, int32_t w, const TWin &tw, CliqueAcc<A> &a,
                                                int lane) {
     const int64_t pb = g.plus_off[w];
     const int32_t np = (int32_t)(g.plus_off[w + 1] - pb);
-    const int32_t *src = g.plus_adj + pb;
-    for (int32_t r0 = 0; r0 < np; r0 += 128) {
+    const int32_t *p = g.plus_adj + pb + lane;
+    int32_t r0 = 0;
+    for (; r0 + 128 <= np; r0 += 128, p += 128) {
         uint32_t ent[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int32_t idx = r0 + 32 * u + lane;
-            ent[u] = idx < np ? (uint32_t)__ldg(src + idx) : 0u;
-        }
+        for (int u = 0; u < 4; ++u) ent[u] = (uint32_t)__ldg(p + 32 * u);
+        unsigned slow = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) look(tw, ent[u], a, slow, u);
+        look_slow(tw, ent, a, slow);
+        if (++a.since == CliqueAcc<A>::R) a.drain(g.L);
+    }
+    if (r0 < np) {
+        // entries past the list are looked up as id kIdMask of type 0, above
+        // every member: no hit, and not in the hash set's range
+        uint32_t ent[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ent[u] = r0 + 32 * u + lane < np ? (uint32_t)__ldg(p + 32 * u) : 0u;
+        unsigned slow = 0, valid = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const bool hit = r0 + 32 * u + lane < np && tset_has(set, lgnb, (int32_t)(ent[u] & (uint32_t)kIdMask));
-            a.acc += (unsigned long long)hit << (8u * (ent[u] >> kTypeShift));
+            const bool v = r0 + 32 * u + lane < np;
+            valid |= (v ? 1u : 0u) << u;
+            uint32_t e = v ? ent[u] : (uint32_t)kIdMask;    // an id above every member: no hit, not slow
+            look(tw, e, a, slow, u);
         }
-        if (++a.since == 63) a.drain(g.L);
+        look_slow(tw, ent, a, slow & valid);
+        if (++a.since == CliqueAcc<A>::R) a.drain(g.L);
     }
     return np;
+}
+
+// the members of T, warp-serially, into K (sK) by member type
+template <class A>
+__device__ __forceinline__ unsigned long long scan_members_warp(const GraphView &g, const int32_t *T, int32_t nT,
+                                                                const int32_t *ts, const TWin &tw,
+                                                                unsigned long long *sK, int lane) {
+    CliqueAcc<A> acc;
+    unsigned long long probes = 0;
+    int t = -1;
+    for (int32_t k = 0; k < nT; ++k) {
+        const int tk = type_of_index(ts, k);
+        if (tk != t) {
+            flush_k(acc, t, sK, g.L, lane, false);
+            t = tk;
+        }
+        probes += (unsigned long long)scan_member(g, T[k], tw, acc, lane);
+    }
+    flush_k(acc, t, sK, g.L, lane, false);
+    return probes;
 }
 
 // few pairs: every pair (a, b) of T checked by a binary search in the
@@ -1150,16 +1277,25 @@ __device__ __forceinline__ void add_work(unsigned long long *work, int slot, uns
     if (work && lane == 0 && v) atomicAdd(&work[slot], v);
 }
 
-// Warp per edge (edges with |T| <= big_t): K into kmat.
+// the window form when at least 3/4 of the members lie in the window
+__device__ __forceinline__ bool use_window(int32_t nlow, int32_t nT) { return 4 * nlow <= nT; }
+
+// Warp per edge (edges with |T| <= big_t): K into kmat.  A = the counter
+// register type (uint32_t for L <= 5).
 constexpr int kCliqueWarpSlots = 1024;       // per-warp set: 4 slots per member up to |T| = 256
+constexpr int kCliqueWarpWin = 1 << 13;      // per-warp window bits (1 KB)
+template <class A>
 __global__ void __launch_bounds__(256, 5) k_clique(GraphView g, CountView cv, int64_t e0, int64_t e1, int64_t big_t) {
     __shared__ unsigned long long sKw[8][kMaxL * kMaxL];
     __shared__ int4 setw[8][kCliqueWarpSlots / 4];
+    __shared__ uint32_t bmw[8][kCliqueWarpWin / 32 + 1];   // + the zero word of clamped lookups
     const int L = g.L, LL = L * L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long *sK = sKw[wid];
+    uint32_t *bm = bmw[wid];
+    for (int k = lane; k <= kCliqueWarpWin / 32; k += 32) bm[k] = 0u;
+    __syncwarp();
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long probes = 0, searches = 0;
     for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
         const int64_t er = e - e0;
         const int32_t nT = (int32_t)(cv.toffs[er + 1] - cv.toffs[er]);
@@ -1177,96 +1313,129 @@ __global__ void __launch_bounds__(256, 5) k_clique(GraphView g, CountView cv, in
         const long long npair = (long long)nT * (nT - 1) / 2;
         if (npair <= 64) {
             clique_pairs_search(g, T, nT, ts, sK, 32, lane);
-            searches += npair;
+            add_work(cv.work, kWorkCliqueSearches, (unsigned long long)npair, lane);
         } else {
-            const int lgnb = tset_lgnb(nT, kCliqueWarpSlots);   // nT <= 256: 4 slots per member
-            if (lgnb < 0) {                                     // the options clamp big_t to 256
+            TWin tw;
+            t_range(T, ts, L, tw.tmin, tw.tmax);
+            const int32_t nlow = (int32_t)__reduce_add_sync(
+                0xffffffffu, (unsigned)twin_below<kCliqueWarpWin>(T, nT, tw.tmax, 32, lane));
+            const bool win = use_window(nlow, nT);
+            const int32_t nset = win ? nlow : nT;           // members in the hash set
+            tw.bm = bm;
+            tw.set = setw[wid];
+            tw.wbits = win ? kCliqueWarpWin : 0u;
+            tw.lowmax = !win ? tw.tmax : nlow > 0 ? tw.tmax - kCliqueWarpWin : -1;
+            tw.lowspan = tw.lowmax >= tw.tmin ? (uint32_t)(tw.lowmax - tw.tmin) + 1u : 0u;
+            tw.lgnb = nset > 0 ? tset_lgnb(nset, kCliqueWarpSlots) : 1;   // nset <= 256: 4 slots per member
+            if (tw.lgnb < 0) {                              // the options clamp big_t to 256
                 if (lane == 0) set_status(cv.status, ST_INTERNAL);
                 continue;
             }
-            tset_build(T, nT, setw[wid], lgnb, 32, lane);
-            CliqueAcc acc;
-            int tw = -1;
-            for (int32_t k = 0; k < nT; ++k) {
-                const int t = type_of_index(ts, k);
-                if (t != tw) {
-                    flush_k(acc, tw, sK, L, lane, false);
-                    tw = t;
-                }
-                probes += (unsigned long long)scan_member(g, T[k], setw[wid], lgnb, acc, lane);
-            }
-            flush_k(acc, tw, sK, L, lane, false);
+            if (win) twin_bits<kCliqueWarpWin>(T, nT, tw.tmax, bm, 32, lane, true);
+            if (nset > 0) tset_build(T, nT, setw[wid], tw.lgnb, 32, lane, tw.lowmax);
+            else __syncwarp();                              // (tset_build ends with __syncwarp)
+            const unsigned long long probes = scan_members_warp<A>(g, T, nT, ts, tw, sK, lane);
+            add_work(cv.work, kWorkCliqueProbes, probes, lane);
+            __syncwarp();
+            if (win) twin_bits<kCliqueWarpWin>(T, nT, tw.tmax, bm, 32, lane, false);
         }
         __syncwarp();
         for (int k = lane; k < LL; k += 32) km[k] = sK[(k / L) * kMaxL + (k % L)];
         __syncwarp();
     }
-    add_work(cv.work, kWorkCliqueProbes, probes, lane);
-    add_work(cv.work, kWorkCliqueSearches, searches, lane);
 }
 
 // the members of T taken by the CTA's warps from a shared counter (in
 // order, so each warp's member types only rise)
+template <class A>
 __device__ __forceinline__ unsigned long long big_members(const GraphView &g, const int32_t *T, int32_t nT,
-                                                          const int32_t *ts, const int4 *set, int lgnb,
-                                                          unsigned long long *sK, int *next, int lane) {
-    CliqueAcc acc;
+                                                          const int32_t *ts, const TWin &tw, unsigned long long *sK,
+                                                          int *next, int lane) {
+    CliqueAcc<A> acc;
     unsigned long long probes = 0;
-    int tw = -1;
+    int t = -1;
     for (;;) {
         int32_t m = 0;
         if (lane == 0) m = atomicAdd(next, 1);
         m = __shfl_sync(0xffffffffu, m, 0);
         if (m >= nT) break;
-        const int t = type_of_index(ts, m);
-        if (t != tw) {
-            flush_k(acc, tw, sK, g.L, lane, true);
-            tw = t;
+        const int tm = type_of_index(ts, m);
+        if (tm != t) {
+            flush_k(acc, t, sK, g.L, lane, true);
+            t = tm;
         }
-        probes += (unsigned long long)scan_member(g, T[m], set, lgnb, acc, lane);
+        probes += (unsigned long long)scan_member(g, T[m], tw, acc, lane);
     }
-    flush_k(acc, tw, sK, g.L, lane, true);
+    flush_k(acc, t, sK, g.L, lane, true);
     return probes;
 }
 
-// CTA per edge for the listed edges with a large T; the set of T lives in
+// CTA per edge for the listed edges with a large T; the hash set lives in
 // shared memory up to kBigSetSmem slots, else in this CTA's global slice
 // (2 slots per member).
 constexpr int kBigSetSmem = 1 << 13;
 constexpr int kBigThreads = 256;
+constexpr int kBigWin = 1 << 15;             // window bits (4 KB)
+template <class A>
 __global__ void __launch_bounds__(kBigThreads, 5) k_clique_big(GraphView g, CountView cv, int64_t e0,
                                                           const int32_t *__restrict__ big_list,
                                                           const unsigned long long *__restrict__ big_count,
                                                           int32_t *set_scratch, int64_t set_stride) {
     __shared__ unsigned long long sK[kMaxL * kMaxL];
-    __shared__ int s_next;
+    __shared__ uint32_t bm[kBigWin / 32 + 1];            // + the zero word of clamped lookups
+    __shared__ int s_next, s_low;
     extern __shared__ int4 set_smem[];
     const int L = g.L, LL = L * L;
     const int lane = threadIdx.x & 31;
     const int64_t nb = (int64_t)*big_count;
     unsigned long long probes = 0;
+    for (int x = threadIdx.x; x <= kBigWin / 32; x += blockDim.x) bm[x] = 0u;
     for (int64_t k = blockIdx.x; k < nb; k += gridDim.x) {
         const int64_t e = big_list[k];
         const int64_t er = e - e0;
         const int32_t nT = (int32_t)(cv.toffs[er + 1] - cv.toffs[er]);
         for (int x = threadIdx.x; x < kMaxL * kMaxL; x += blockDim.x) sK[x] = 0;
-        if (threadIdx.x == 0) s_next = 0;
+        if (threadIdx.x == 0) {
+            s_next = 0;
+            s_low = 0;
+        }
         int32_t ts[kMaxL + 1];
         t_bounds(cv, L, e, ts);
         const int32_t *T = cv.tlist + cv.toffs[er];
-        const int lgs = tset_lgnb(nT, kBigSetSmem);
-        if (lgs >= 0) {                                     // CTA-uniform
-            tset_build(T, nT, set_smem, lgs, blockDim.x, threadIdx.x);   // ends with a barrier
-            probes += big_members(g, T, nT, ts, set_smem, lgs, sK, &s_next, lane);
-        } else {                                            // global slice: 2^lg >= 2 nT slots
+        TWin tw;
+        t_range(T, ts, L, tw.tmin, tw.tmax);
+        __syncthreads();                                    // s_low zero, the previous edge done
+        const unsigned low = __reduce_add_sync(0xffffffffu,
+                                               (unsigned)twin_below<kBigWin>(T, nT, tw.tmax, blockDim.x, threadIdx.x));
+        if (lane == 0 && low) atomicAdd(&s_low, (int)low);
+        __syncthreads();
+        const int32_t nlow = s_low;
+        const bool win = use_window(nlow, nT);              // CTA-uniform
+        const int32_t nset = win ? nlow : nT;
+        tw.bm = bm;
+        tw.wbits = win ? kBigWin : 0u;
+        tw.lowmax = !win ? tw.tmax : nlow > 0 ? tw.tmax - kBigWin : -1;
+        tw.lowspan = tw.lowmax >= tw.tmin ? (uint32_t)(tw.lowmax - tw.tmin) + 1u : 0u;
+        const int32_t xmax = tw.lowmax;
+        if (win) twin_bits<kBigWin>(T, nT, tw.tmax, bm, blockDim.x, threadIdx.x, true);
+        const int lgs = nset > 0 ? tset_lgnb(nset, kBigSetSmem) : 1;
+        if (lgs >= 0) {
+            tw.set = set_smem;
+            tw.lgnb = lgs;
+            if (nset > 0) tset_build(T, nT, set_smem, lgs, blockDim.x, threadIdx.x, xmax);   // ends with a barrier
+            else __syncthreads();
+        } else {                                            // global slice: 2^lg >= 2 nset slots
             int lg = 1;
-            while ((4 << lg) < 2 * nT) ++lg;
+            while ((4 << lg) < 2 * nset) ++lg;
             int4 *set = reinterpret_cast<int4 *>(set_scratch + (int64_t)blockIdx.x * set_stride);
-            tset_build(T, nT, set, lg, blockDim.x, threadIdx.x);
-            probes += big_members(g, T, nT, ts, set, lg, sK, &s_next, lane);
+            tw.set = set;
+            tw.lgnb = lg;
+            tset_build(T, nT, set, lg, blockDim.x, threadIdx.x, xmax);
         }
+        probes += big_members<A>(g, T, nT, ts, tw, sK, &s_next, lane);
         __syncthreads();
         for (int x = threadIdx.x; x < LL; x += blockDim.x) cv.kmat[er * LL + x] = sK[(x / L) * kMaxL + (x % L)];
+        if (win) twin_bits<kBigWin>(T, nT, tw.tmax, bm, blockDim.x, threadIdx.x, false);
         __syncthreads();
     }
     add_work(cv.work, kWorkCliqueBigProbes, probes, lane);
@@ -1914,7 +2083,8 @@ static PaView pa_view(const Graph &G) {
 void prepare_edges(Graph &G, int k, cudaStream_t s) {
     raise_smem_limit((const void *)k_edge3, hist_bytes(G.L, 3));
     raise_smem_limit((const void *)k_epi4, epi4_smem_bytes(G.L, epi4_copies(G.L)));
-    raise_smem_limit((const void *)k_clique_big, kBigSetSmem * sizeof(int32_t));
+    raise_smem_limit((const void *)k_clique_big<uint32_t>, kBigSetSmem * sizeof(int32_t));
+    raise_smem_limit((const void *)k_clique_big<unsigned long long>, kBigSetSmem * sizeof(int32_t));
     raise_smem_limit((const void *)k_wedge_heavy, (size_t)kHeavyCap * (1 + G.L) * sizeof(int32_t));
     if (k == 4 && !G.set_scratch.p) {
         // a set of capacity >= 2 max degree per CTA, for edges whose T exceeds shared memory
@@ -2270,14 +2440,20 @@ static int64_t launch_edges4(Graph &G, int64_t b, int64_t e, const Tile *tiles, 
     }
     {
         KernelTimer kt(G, s, "k_clique");
-        k_clique<<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e, big_t);
+        if (G.L <= 5) k_clique<uint32_t><<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e, big_t);
+        else k_clique<unsigned long long><<<grid_for(ne, 8, sms * 32), 256, 0, s>>>(gv, cv, b, e, big_t);
         ++launches;
     }
     {
         KernelTimer kt(G, s, "k_clique_big");
-        k_clique_big<<<G.big_blocks, 256, kBigSetSmem * sizeof(int32_t), s>>>(
-            gv, cv, b, G.big_list.as<int32_t>(), G.big_count.as<unsigned long long>(), G.set_scratch.as<int32_t>(),
-            G.set_stride);
+        if (G.L <= 5)
+            k_clique_big<uint32_t><<<G.big_blocks, 256, kBigSetSmem * sizeof(int32_t), s>>>(
+                gv, cv, b, G.big_list.as<int32_t>(), G.big_count.as<unsigned long long>(), G.set_scratch.as<int32_t>(),
+                G.set_stride);
+        else
+            k_clique_big<unsigned long long><<<G.big_blocks, 256, kBigSetSmem * sizeof(int32_t), s>>>(
+                gv, cv, b, G.big_list.as<int32_t>(), G.big_count.as<unsigned long long>(), G.set_scratch.as<int32_t>(),
+                G.set_stride);
         ++launches;
     }
     if (n_tiles > 0 && G.pa_active) {
