@@ -1025,7 +1025,9 @@ __device__ __forceinline__ int type_of_index(const int32_t *ts, int32_t k) {
 // hash lookups (entries between the smallest member and the window, and
 // every entry within T's range in the hash form) are taken by the lanes
 // that need them, once per round of four, when any lane of the warp
-// does.  Each lane counts its hits by
+// does.  Only members below the window check for them: N+(w) holds ids
+// above w, so a member in the window meets no member below it.  Each lane
+// counts its hits by
 // type of x in the fields of one register (no warp-wide step inside the
 // scan, so a lane's four lookups overlap); the warp sums the fields with
 // __reduce_add_sync before any can overflow and when the member type t
@@ -1175,19 +1177,19 @@ __device__ __forceinline__ void flush_k(CliqueAcc<A> &a, int tw, unsigned long l
 // one lookup of entry `ent` (slot u of a round): the window bit (d is
 // clamped to wbits, whose word and bit are always zero) counted at once,
 // and bit u of `slow` set when the entry falls in the hash set's range
-template <class A>
+template <bool kSlow, class A>
 __device__ __forceinline__ void look(const TWin &tw, uint32_t ent, CliqueAcc<A> &a, unsigned &slow, int u) {
     const int32_t x = (int32_t)(ent & (uint32_t)kIdMask);
     const uint32_t d = min((uint32_t)(tw.tmax - x), tw.wbits);
     const uint32_t word = tw.bm[d >> 5];
     a.add(((word >> (d & 31u)) & 1u) != 0u, ent);
-    slow |= ((uint32_t)(x - tw.tmin) < tw.lowspan ? 1u : 0u) << u;
+    if (kSlow) slow |= ((uint32_t)(x - tw.tmin) < tw.lowspan ? 1u : 0u) << u;
 }
 
 // the hash lookups of the round's slow entries, when any lane has one
-template <class A>
+template <bool kSlow, class A>
 __device__ __forceinline__ void look_slow(const TWin &tw, const uint32_t *ent, CliqueAcc<A> &a, unsigned slow) {
-    if (__any_sync(0xffffffffu, slow != 0u)) {
+    if (kSlow && __any_sync(0xffffffffu, slow != 0u)) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if ((slow >> u) & 1u) a.add(tset_has(tw.set, tw.lgnb, (int32_t)(ent[u] & (uint32_t)kIdMask)), ent[u]);
@@ -1195,10 +1197,13 @@ __device__ __forceinline__ void look_slow(const TWin &tw, const uint32_t *ent, C
 }
 
 // member w of T: the whole warp scans N+(w), 128 entries a round (full
-// rounds without bounds checks, then the partial one); returns |N+(w)|
-template <class A>
-__device__ __forceinline__ int32_t scan_member(const GraphView &g, int32_t w, const TWin &tw, CliqueAcc<A> &a,
-                                               int lane) {
+// rounds without bounds checks, then the partial one); returns |N+(w)|.
+// kSlow: w may have hash-set members in N+(w), i.e. w <= lowmax (N+(w)
+// holds ids above w only, so a member in the window meets window members
+// only).
+template <bool kSlow, class A>
+__device__ __forceinline__ int32_t scan_list(const GraphView &g, int32_t w, const TWin &tw, CliqueAcc<A> &a,
+                                             int lane) {
     const int64_t pb = g.plus_off[w];
     const int32_t np = (int32_t)(g.plus_off[w + 1] - pb);
     const int32_t *p = g.plus_adj + pb + lane;
@@ -1209,8 +1214,8 @@ __device__ __forceinline__ int32_t scan_member(const GraphView &g, int32_t w, co
         for (int u = 0; u < 4; ++u) ent[u] = (uint32_t)__ldg(p + 32 * u);
         unsigned slow = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) look(tw, ent[u], a, slow, u);
-        look_slow(tw, ent, a, slow);
+        for (int u = 0; u < 4; ++u) look<kSlow>(tw, ent[u], a, slow, u);
+        look_slow<kSlow>(tw, ent, a, slow);
         if (++a.since == CliqueAcc<A>::R) a.drain(g.L);
     }
     if (r0 < np) {
@@ -1225,12 +1230,18 @@ __device__ __forceinline__ int32_t scan_member(const GraphView &g, int32_t w, co
             const bool v = r0 + 32 * u + lane < np;
             valid |= (v ? 1u : 0u) << u;
             uint32_t e = v ? ent[u] : (uint32_t)kIdMask;    // an id above every member: no hit, not slow
-            look(tw, e, a, slow, u);
+            look<kSlow>(tw, e, a, slow, u);
         }
-        look_slow(tw, ent, a, slow & valid);
+        look_slow<kSlow>(tw, ent, a, slow & valid);
         if (++a.since == CliqueAcc<A>::R) a.drain(g.L);
     }
     return np;
+}
+
+template <class A>
+__device__ __forceinline__ int32_t scan_member(const GraphView &g, int32_t w, const TWin &tw, CliqueAcc<A> &a,
+                                               int lane) {
+    return w <= tw.lowmax ? scan_list<true>(g, w, tw, a, lane) : scan_list<false>(g, w, tw, a, lane);
 }
 
 // the members of T, warp-serially, into K (sK) by member type
