@@ -105,39 +105,112 @@ __device__ __forceinline__ int pair_idx(int L, int t, int u) {   // t <= u
 }
 
 // ------------------------------------------------------------------ k_tri
-// Warp per edge: c_e^t = |Gamma_i^t cap Gamma_j^t| (Cor. 1; Thm. 2's O(Delta)),
-// each typed pair by binary search or merge (isect).
+// Warp per edge: c_e^t = |Gamma_i^t cap Gamma_j^t| (Cor. 1; Thm. 2's O(Delta)).
+// Binary search form: the shorter side of every typed pair, concatenated
+// over t, is one list of sum_t min(d_i^t, d_j^t) entries that the lanes
+// stride over (so the lanes are busy across type boundaries); each entry is
+// searched in the other side's segment of its type.  Lane q < L holds type
+// q's segments; per round every lane finds its entry's type from the
+// prefix ends (in registers) and the segments by shuffles.  Hits are
+// counted by type in the 8-bit fields of one register per lane (emptied
+// every 255 rounds).  Merge form (isect): one typed pair at a time.
+struct TypedPairs {
+    int64_t sa, sb;             // lane q < L: start of the shorter / longer type-q segment
+    int32_t nb;                 // length of the longer one
+    int32_t excl;               // entries of the shorter segments of types < q
+    int32_t incl[kMaxL];        // every lane: entries of types <= q, for each q
+    int32_t total;              // entries of all shorter segments
+};
+
+// the typed pairs of edge (i, j), each side's segment of type q on lane q
+__device__ __forceinline__ void typed_pairs(const GraphView &g, int32_t i, int32_t j, int lane, TypedPairs &tp) {
+    const int L = g.L;
+    int64_t si = 0, sj = 0;
+    int32_t di = 0, dj = 0;
+    if (lane < L) {
+        const int32_t *oi = g.toff + (int64_t)i * (L + 1), *oj = g.toff + (int64_t)j * (L + 1);
+        const int32_t a0 = oi[lane], b0 = oj[lane];
+        si = g.rp[i] + a0;
+        sj = g.rp[j] + b0;
+        di = oi[lane + 1] - a0;
+        dj = oj[lane + 1] - b0;
+    }
+    const bool sw = di > dj;
+    tp.sa = sw ? sj : si;
+    tp.sb = sw ? si : sj;
+    const int32_t na = sw ? dj : di;
+    tp.nb = sw ? di : dj;
+    int32_t inc = na;
+#pragma unroll
+    for (int s = 1; s < kMaxL; s <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, s);
+        if (lane >= s) inc += y;
+    }
+    tp.excl = inc - na;
+#pragma unroll
+    for (int q = 0; q < kMaxL; ++q) tp.incl[q] = __shfl_sync(0xffffffffu, inc, q);   // = total for q >= L
+    tp.total = tp.incl[kMaxL - 1];
+}
+
 template <bool kMerge>
 __global__ void __launch_bounds__(256) k_tri(GraphView g, CountView cv) {
     const int lane = threadIdx.x & 31;
+    const int L = g.L;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < g.m; e += nw) {
         const int32_t i = g.e_lo[e], j = g.e_hi[e];
-        for (int t = 0; t < g.L; ++t) {
-            int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
-            int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
-            if (ei == bi || ej == bj) {                     // an empty typed segment (warp-uniform)
-                if (lane == 0) cv.C[e * g.L + t] = 0;
-                continue;
-            }
-            if (ei - bi > ej - bj) {
-                int64_t x = bi; bi = bj; bj = x;
-                x = ei; ei = ej; ej = x;
-            }
-            unsigned cnt = 0;
-            if (kMerge && isect_use_merge(g.isect_modes, ei - bi, ej - bj)) {
-                isect_merge(g.adj, bi, ei, bj, ej, lane,
-                            [&](bool found, int64_t, int64_t, int32_t) { cnt += found ? 1u : 0u; });
-            } else {
-                for (int64_t s = bi + lane; s < ei; s += 32) {
-                    const int32_t w = g.adj[s];
-                    const int64_t r = lower_bound_i32(g.adj, bj, ej, w);
-                    cnt += (r < ej && g.adj[r] == w) ? 1u : 0u;
+        if (kMerge) {
+            for (int t = 0; t < L; ++t) {
+                int64_t bi = seg_begin(g, i, t), ei = seg_end(g, i, t);
+                int64_t bj = seg_begin(g, j, t), ej = seg_end(g, j, t);
+                if (ei == bi || ej == bj) {                 // an empty typed segment (warp-uniform)
+                    if (lane == 0) cv.C[e * L + t] = 0;
+                    continue;
                 }
+                if (ei - bi > ej - bj) {
+                    int64_t x = bi; bi = bj; bj = x;
+                    x = ei; ei = ej; ej = x;
+                }
+                unsigned cnt = 0;
+                isect<true>(g.adj, g.isect_modes, bi, ei, bj, ej, lane,
+                            [&](bool found, int64_t, int64_t, int32_t) { cnt += found ? 1u : 0u; });
+                cnt = warp_sum_u32(cnt);
+                if (lane == 0) cv.C[e * L + t] = cnt;
             }
-            cnt = warp_sum_u32(cnt);
-            if (lane == 0) cv.C[e * g.L + t] = cnt;
+            continue;
         }
+        TypedPairs tp;
+        typed_pairs(g, i, j, lane, tp);
+        unsigned long long acc = 0, kreg = 0;
+        int since = 0;
+        for (int32_t p0 = 0; p0 < tp.total; p0 += 32) {
+            const int32_t p = p0 + lane;
+            int t = 0;
+#pragma unroll
+            for (int q = 0; q < kMaxL - 1; ++q) t += tp.incl[q] <= p ? 1 : 0;
+            const int64_t sa = __shfl_sync(0xffffffffu, tp.sa, t);
+            const int64_t sb = __shfl_sync(0xffffffffu, tp.sb, t);
+            const int32_t nb = __shfl_sync(0xffffffffu, tp.nb, t);
+            const int32_t ex = __shfl_sync(0xffffffffu, tp.excl, t);
+            if (p < tp.total) {
+                const int32_t w = g.adj[sa + (p - ex)];
+                const int64_t r = lower_bound_i32(g.adj, sb, sb + nb, w);
+                acc += (unsigned long long)(r < sb + nb && g.adj[r] == w) << (8 * t);
+            }
+            if (++since == 255) {
+                for (int q = 0; q < L; ++q) {
+                    const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (8 * q)) & 0xffu);
+                    kreg += lane == q ? v : 0u;
+                }
+                acc = 0;
+                since = 0;
+            }
+        }
+        for (int q = 0; q < L; ++q) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (8 * q)) & 0xffu);
+            kreg += lane == q ? v : 0u;
+        }
+        if (lane < L) cv.C[e * L + lane] = (uint32_t)kreg;
     }
 }
 
@@ -1153,6 +1226,9 @@ struct CliqueAcc {
     __device__ __forceinline__ void add(bool hit, uint32_t ent) {
         acc += (A)hit << (F * (ent >> kTypeShift));
     }
+    __device__ __forceinline__ void add_bit(uint32_t bit, uint32_t ent) {   // bit: 0 or 1
+        acc += (A)bit << (F * (ent >> kTypeShift));
+    }
     __device__ __forceinline__ void drain(int L) {
         for (int q = 0; q < L; ++q) {
             const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> (F * q)) & ((1u << F) - 1u));
@@ -1182,7 +1258,7 @@ __device__ __forceinline__ void look(const TWin &tw, uint32_t ent, CliqueAcc<A> 
     const int32_t x = (int32_t)(ent & (uint32_t)kIdMask);
     const uint32_t d = min((uint32_t)(tw.tmax - x), tw.wbits);
     const uint32_t word = tw.bm[d >> 5];
-    a.add(((word >> (d & 31u)) & 1u) != 0u, ent);
+    a.add_bit(__funnelshift_r(word, 0u, d) & 1u, ent);       // bit d % 32 of the word
     if (kSlow) slow |= ((uint32_t)(x - tw.tmin) < tw.lowspan ? 1u : 0u) << u;
 }
 
