@@ -430,13 +430,21 @@ tg_status tg_count_directed3(tg_graph *g, uint32_t *per_edge_out, int64_t *globa
 
 /* Work counters (diagnostics for the benchmark's roofline; no effect on the
  * counts).  While enabled, the counting kernels add the units of work they
- * did to per-handle counters, slot TG_WORK_*: the hash-set lookups of the
+ * did to per-handle counters, slot TG_WORK_*: the set-of-T lookups of the
  * 4-clique scans (one per entry of N+(w) for every member w of T, Alg. 3's
- * 4-clique branch) by the warp-per-edge and CTA-per-edge kernels, and the
- * pair searches of edges with few pairs.  Off by default. */
+ * 4-clique branch) by the warp-per-edge and CTA-per-edge kernels, the pair
+ * searches of edges with few pairs, and the SM clock cycles the CTAs of the
+ * hub wedge pass spent waiting for their tickets' dependencies and working
+ * on tickets of each kind (fill the counter tables, read them, clear them
+ * by walking the wedges, clear them by zeroing).  Off by default. */
 #define TG_WORK_CLIQUE_PROBES 0
 #define TG_WORK_CLIQUE_SEARCHES 1
 #define TG_WORK_CLIQUE_BIG_PROBES 2
+#define TG_WORK_HUB_WAIT_CYCLES 3
+#define TG_WORK_HUB_FILL_CYCLES 4
+#define TG_WORK_HUB_READ_CYCLES 5
+#define TG_WORK_HUB_WALK_CLEAR_CYCLES 6
+#define TG_WORK_HUB_ZERO_CLEAR_CYCLES 7
 #define TG_WORK_SLOTS 8
 tg_status tg_set_work_counting(tg_graph *g, int32_t on);
 

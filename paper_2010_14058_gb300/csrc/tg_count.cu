@@ -582,12 +582,11 @@ __global__ void __launch_bounds__(kAnchorThreads, 2) k_wedge_heavy(GraphView g, 
 
 struct HubView {
     const int32_t *hubs;        // hub node ids
-    const int64_t *hub_base;    // first node of each hub's graph
+    const int64_t *hub_base;    // first node of each hub's graph (read when batched)
     const int64_t *woff;        // [n_items + 1] first wedge of each item
-    const int32_t *vb;          // adj position of the item's first w
-    const int32_t *sv;          // adj position of v in the hub's row
-    const int32_t *hub;         // hub index of the item
-    const uint8_t *tt;          // type of v << 4 | type of w
+    const int4 *item;           // per item: adj position of its first w, adj position of v in the
+                                // hub's row, hub index, type of u << 8 | type of v << 4 | type of w
+    bool batched;               // several graphs: tables are indexed from each hub's graph's first node
 };
 
 constexpr int kHubThreads = 256;
@@ -649,8 +648,8 @@ __global__ void __launch_bounds__(256) k_hub_cnt(GraphView g, const int32_t *__r
 }
 
 __global__ void k_hub_items(GraphView g, int64_t ni, const int32_t *__restrict__ cnt, const int64_t *__restrict__ pos,
-                            const int32_t *__restrict__ sv_of, const int32_t *__restrict__ hub_of, int32_t *vb,
-                            int32_t *sv, int32_t *hub, uint8_t *tt, int64_t *icnt) {
+                            const int32_t *__restrict__ sv_of, const int32_t *__restrict__ hub_of,
+                            const int32_t *__restrict__ hubs, int4 *item, int64_t *icnt) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= ni) return;
     const int32_t c = cnt[idx];
@@ -659,10 +658,8 @@ __global__ void k_hub_items(GraphView g, int64_t ni, const int32_t *__restrict__
     const int tw = (int)(idx - kv * g.L);
     const int32_t s = sv_of[kv];
     const int32_t v = g.adj[s];
-    vb[j] = (int32_t)seg_begin(g, v, tw);
-    sv[j] = s;
-    hub[j] = hub_of[kv];
-    tt[j] = (uint8_t)((g.ty[v] << 4) | tw);
+    const int32_t h = hub_of[kv];
+    item[j] = make_int4((int32_t)seg_begin(g, v, tw), s, h, (g.ty[hubs[h]] << 8) | (g.ty[v] << 4) | tw);
     icnt[j] = c;
 }
 
@@ -694,11 +691,13 @@ __device__ __forceinline__ int64_t hub_find_item(const int64_t *__restrict__ wof
 // One phase of the hub wedge pass over the wedges [x0r, x1r) of one group of
 // hubs (items [i0, i1), first hub h0; hub h's table at tbl + (h - h0) *
 // stride).  Warp wi of nwi takes one contiguous run of the range, 32 wedges
-// at a time, one wedge per lane.  Counters: kPacked = two 16-bit counters
-// per 32-bit word (types 2k and 2k+1; every count is at most the hub's
-// degree, below 2^16 when this layout is chosen), else one 32-bit counter
-// per type.  The tables are read and cleared at L2 (ld/st.cg): other CTAs of
-// the same launch update them, so no L1 copy may be trusted.
+// at a time, one wedge per lane; the item window of the next 32 wedges is
+// loaded while the current ones are worked on.  Counters: kPacked = two
+// 16-bit counters per 32-bit word (types 2k and 2k+1; every count is at
+// most the hub's degree, below 2^16 when this layout is chosen), else one
+// 32-bit counter per type.  The tables are read and cleared at L2
+// (ld/st.cg): other CTAs of the same launch update them, so no L1 copy may
+// be trusted.
 template <bool kPacked>
 __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubView &hv, int64_t i0, int64_t i1,
                            int64_t x0r, int64_t x1r, int32_t h0, uint32_t *tbl, int64_t stride, int phase, int wi,
@@ -712,11 +711,11 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
     const int64_t nnz = cv.a_stride;
     uint32_t *A = cv.A - cv.a_base;                         // indexed by absolute slot
     int64_t j = hub_find_item(hv.woff, i0, i1, x0, lane);
+    int64_t wo = j + lane < i1 ? hv.woff[j + lane] : INT64_MAX;
     for (; x0 < xe; x0 += 32) {
         // the wedges x0 .. x0+31 lie in items j .. j+31 (every item is non-empty)
         const int64_t x = x0 + lane;
         const bool act = x < xe;
-        const int64_t wo = j + lane < i1 ? hv.woff[j + lane] : INT64_MAX;
         int k = 0;
 #pragma unroll
         for (int st = 16; st > 0; st >>= 1) {
@@ -728,25 +727,29 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
         const int k31 = __shfl_sync(0xffffffffu, k, 31);
         const int64_t wnext = k31 < 31 ? __shfl_sync(0xffffffffu, wo, k31 < 31 ? k31 + 1 : 31)
                                        : (j + 32 < i1 ? hv.woff[j + 32] : INT64_MAX);
+        // first item of the next 32 wedges (the item of x0 + 32), and its window
+        const int64_t jn = (wnext <= x0 + 32) ? j + k31 + 1 : j + k31;
+        const int64_t won = x0 + 32 < xe && jn + lane < i1 ? hv.woff[jn + lane] : INT64_MAX;
         int32_t svp = 0;
         int tw = 0;
         uint32_t c[kMaxL];
 #pragma unroll
         for (int t = 0; t < kMaxL; ++t) c[t] = 0;
         if (act) {
-            const int32_t hh = hv.hub[it];
-            const uint8_t tt = hv.tt[it];
-            const int tv = tt >> 4;
-            tw = tt & 15;
-            svp = hv.sv[it];
-            const int64_t pos = (int64_t)hv.vb[it] + (x - wstart);
+            const int4 rec = hv.item[it];
+            const int32_t hh = rec.z;
+            const int tv = (rec.w >> 4) & 15;
+            tw = rec.w & 15;
+            svp = rec.y;
+            const int64_t pos = (int64_t)rec.x + (x - wstart);
             const int32_t w = g.adj[pos];
-            uint32_t *row = tbl + (int64_t)(hh - h0) * stride + (w - hv.hub_base[hh]) * RW;
+            const int64_t base = hv.batched ? hv.hub_base[hh] : 0;
+            uint32_t *row = tbl + (int64_t)(hh - h0) * stride + (w - base) * RW;
             if (phase == 0) {
                 if (kPacked) atomicAdd(row + (tv >> 1), 1u << (16 * (tv & 1)));
                 else atomicAdd(row + tv, 1u);
             } else if (phase == 1) {
-                const int tu = g.ty[hv.hubs[hh]];
+                const int tu = rec.w >> 8;
                 uint32_t words[kMaxL];
 #pragma unroll
                 for (int q = 0; q < kMaxL; ++q) words[q] = q < RW ? __ldcg(row + q) : 0u;
@@ -765,28 +768,39 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
         if (phase == 1) {
             // per-item sums over the lanes of each item (items are contiguous runs of lanes)
             const int64_t key = act ? it : -1;
-            unsigned same = 0;
+            const int64_t key0 = __shfl_sync(0xffffffffu, key, 0);
+            if (__all_sync(0xffffffffu, !act || key == key0)) {
+                // one item: warp sums, added by lane 0 (always active here)
 #pragma unroll
-            for (int s = 0; s < 5; ++s) {
-                const int64_t kk = __shfl_up_sync(0xffffffffu, key, 1 << s);
-                if (lane >= (1 << s) && kk == key) same |= 1u << s;
-            }
-            const int64_t knext = __shfl_down_sync(0xffffffffu, key, 1);
-            const bool tail = act && (lane == 31 || knext != key);
-#pragma unroll
-            for (int t = 0; t < kMaxL; ++t) {
-                if (t >= L) break;
-                uint32_t v = c[t];
+                for (int t = 0; t < kMaxL; ++t) {
+                    if (t >= L) break;
+                    const uint32_t v = __reduce_add_sync(0xffffffffu, c[t]);
+                    if (lane == 0 && v) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + svp], v);
+                }
+            } else {
+                unsigned same = 0;
 #pragma unroll
                 for (int s = 0; s < 5; ++s) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, v, 1 << s);
-                    if (same & (1u << s)) v += y;
+                    const int64_t kk = __shfl_up_sync(0xffffffffu, key, 1 << s);
+                    if (lane >= (1 << s) && kk == key) same |= 1u << s;
                 }
-                if (tail && v) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + svp], v);
+                const int64_t knext = __shfl_down_sync(0xffffffffu, key, 1);
+                const bool tail = act && (lane == 31 || knext != key);
+#pragma unroll
+                for (int t = 0; t < kMaxL; ++t) {
+                    if (t >= L) break;
+                    uint32_t v = c[t];
+#pragma unroll
+                    for (int s = 0; s < 5; ++s) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, v, 1 << s);
+                        if (same & (1u << s)) v += y;
+                    }
+                    if (tail && v) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + svp], v);
+                }
             }
         }
-        // first item of the next 32 wedges: the item of x0 + 32
-        j = (wnext <= x0 + 32) ? j + k31 + 1 : j + k31;
+        j = jn;
+        wo = won;
     }
 }
 
@@ -842,9 +856,11 @@ __global__ void __launch_bounds__(kHubThreads, 5) k_wedge_hub(GraphView g, Count
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned long long *next = ctr;                         // ticket counter
     unsigned long long *done = ctr + 1;                     // [group][kind] tickets done
+    long long c0 = 0;                                       // work counting: clock at the ticket's start
     for (;;) {
         if (threadIdx.x == 0) {
             const int64_t t = (int64_t)atomicAdd(next, 1ull);
+            if (cv.work) c0 = clock64();
             bool ok = true;
             if (t < n_tickets) {
                 int64_t lo = 0, hi = n_segs;                // the run holding ticket t: segs[lo].t0 <= t
@@ -871,6 +887,11 @@ __global__ void __launch_bounds__(kHubThreads, 5) k_wedge_hub(GraphView g, Count
                 }
                 __threadfence();
             }
+            if (cv.work) {
+                const long long c1 = clock64();
+                atomicAdd(&cv.work[kWorkHubWait], (unsigned long long)(c1 - c0));
+                c0 = c1;
+            }
             s_t = t;
             s_ok = ok ? 1 : 0;
         }
@@ -892,6 +913,7 @@ __global__ void __launch_bounds__(kHubThreads, 5) k_wedge_hub(GraphView g, Count
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(&done[(int64_t)group * kHubKinds + kind], 1ull);
+            if (cv.work) atomicAdd(&cv.work[kWorkHubKind + kind], (unsigned long long)(clock64() - c0));
         }
     }
 }
@@ -2269,10 +2291,8 @@ static HubView hub_view(const Graph &G) {
     h.hubs = G.hubs.as<int32_t>();
     h.hub_base = G.hub_base.as<int64_t>();
     h.woff = G.item_woff.as<int64_t>();
-    h.vb = G.item_vb.as<int32_t>();
-    h.sv = G.item_sv.as<int32_t>();
-    h.hub = G.item_hub.as<int32_t>();
-    h.tt = G.item_tt.as<uint8_t>();
+    h.item = G.item_rec.as<int4>();
+    h.batched = G.ngraphs > 1;
     return h;
 }
 
@@ -2303,18 +2323,14 @@ static void prepare_hubs(Graph &G, cudaStream_t s) {
     TG_CK(cudaMemcpyAsync(&G.n_items, pos.as<int64_t>() + NI, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TG_CK(cudaStreamSynchronize(s));
     const int64_t ni = std::max<int64_t>(G.n_items, 1);
-    G.item_vb.alloc(sizeof(int32_t) * ni);
-    G.item_sv.alloc(sizeof(int32_t) * ni);
-    G.item_hub.alloc(sizeof(int32_t) * ni);
-    G.item_tt.alloc(ni);
+    G.item_rec.alloc(sizeof(int4) * ni);
     G.item_woff.alloc(sizeof(int64_t) * (G.n_items + 1));
     TBuf icnt(sizeof(int64_t) * (G.n_items + 1), s);
     TG_CK(cudaMemsetAsync(icnt.p, 0, sizeof(int64_t) * (G.n_items + 1), s));
     if (NI > 0) {
         k_hub_items<<<grid_for(NI, 256, 1 << 30), 256, 0, s>>>(gv, NI, cnt.as<int32_t>(), pos.as<int64_t>(),
                                                                sv_of.as<int32_t>(), hub_of.as<int32_t>(),
-                                                               G.item_vb.as<int32_t>(), G.item_sv.as<int32_t>(),
-                                                               G.item_hub.as<int32_t>(), G.item_tt.as<uint8_t>(),
+                                                               G.hubs.as<int32_t>(), G.item_rec.as<int4>(),
                                                                icnt.as<int64_t>());
         TG_CK(cudaGetLastError());
     }

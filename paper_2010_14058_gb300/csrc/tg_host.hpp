@@ -136,7 +136,7 @@ struct Graph {
     int64_t n_heavy_dense = 0;          // leading heavy anchors with more than kHeavyFit wedges
     // hub anchors (ascending id) and their wedge items: one item per
     // (hub, lower-priority neighbour v, type of w) with at least one wedge
-    DBuf hubs, hub_base, item_woff, item_vb, item_sv, item_hub, item_tt;
+    DBuf hubs, hub_base, item_woff, item_rec;
     int64_t n_hubs = 0, n_items = 0;
     std::vector<int32_t> h_hub_id;      // hub node ids
     std::vector<int64_t> h_hub_wedges;  // wedges of each hub
@@ -245,7 +245,7 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch, &work, &hub_tables, &dsign, &doutdeg, &dcls, &darcs, &dgacc, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_vb, &item_sv, &item_hub, &item_tt,
+                             &set_scratch, &work, &hub_tables, &dsign, &doutdeg, &dcls, &darcs, &dgacc, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_rec,
                 &pa_cls, &pa_gacc};
     }
     int64_t device_bytes() const {

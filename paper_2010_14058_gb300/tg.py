@@ -407,7 +407,8 @@ def tg_get_timing(g: Graph, max_entries: int = 32) -> dict:
     return {names[i].decode(): (ms[i], int(launches[i])) for i in range(n.value)}
 
 
-WORK_SLOTS = {"clique_probes": 0, "clique_searches": 1, "clique_big_probes": 2}
+WORK_SLOTS = {"clique_probes": 0, "clique_searches": 1, "clique_big_probes": 2, "hub_wait_cycles": 3,
+              "hub_fill_cycles": 4, "hub_read_cycles": 5, "hub_walk_clear_cycles": 6, "hub_zero_clear_cycles": 7}
 
 
 def tg_set_work_counting(g: "Graph", on: bool = True) -> None:
