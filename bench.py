@@ -245,13 +245,14 @@ def w_alg_bytes(g: dict, tsize, S: int) -> dict:
     return {"bytes": float(s + 4.0 * S * len(src)), "model": "upper bound (nodes of T counted from both sides)"}
 
 
-def kernel_units(g: dict, light_anchor_max: int = 64, hub_min: int = 1 << 16) -> dict:
+def kernel_units(g: dict, light_anchor_max: int = 64, hub_min: int = 1 << 14) -> dict:
     """Work units of the count kernels, computed on the host from the graph:
     degree-priority wedges (the search for the 4-cycles behind P) split
     by the anchor class the build assigns (light: at most light_anchor_max
-    wedges; hub: more than hub_min), oriented (anchor, neighbour) pairs per
-    class, and the shorter
-    side of every typed intersection, sum_e sum_t min(d_i^t, d_j^t)."""
+    wedges; hub: more than hub_min; the defaults are the library's
+    tg_options light_anchor_max_wedges and hub_min_wedges), oriented
+    (anchor, neighbour) pairs per class, and the shorter side of every
+    typed intersection, sum_e sum_t min(d_i^t, d_j^t)."""
     rp, col, ty, n, L = g["row_ptr"], g["col"].astype(np.int64), g["types"], g["n"], g["L"]
     deg = np.diff(rp)
     rank = np.empty(n, np.int64)
@@ -305,6 +306,10 @@ def algorithmic_bytes(u: dict, m: int, L: int, S: int, t_nodes: int, cu: dict | 
                   intersection 4 B/entry, its typed triangle row 4L;
       k_wedge_*   per wedge: the far node's id 4 + its 4-cycle slot 4 read +
                   4 written; per (anchor, neighbour) pair: L slots 8 B each;
+                  k_wedge_hub, when the library's work counters give them:
+                  per hub wedge its far node's id 4, per nonzero 4-cycle
+                  slot update (a wedge and a type of the fourth node, or a
+                  (hub, neighbour, type) sum) the slot read and written 8;
       k_tsum      per edge: endpoints 8, shorter sides as k_tri, C row 4L,
                   the three L x L sums 24 L^2; per triangle node: its id
                   written 4, two edge ids 8, two typed-triangle rows 8L,
@@ -323,7 +328,8 @@ def algorithmic_bytes(u: dict, m: int, L: int, S: int, t_nodes: int, cu: dict | 
         "k_tri": 8.0 * m + 4.0 * u["typed_min_sum"] + 4.0 * L * m,
         "k_wedge_light": 12.0 * u["wedges_light"] + 8.0 * L * u["pairs_light"],
         "k_wedge_heavy": 12.0 * u["wedges_heavy"] + 8.0 * L * u["pairs_heavy"],
-        "k_wedge_hub": 12.0 * u["wedges_hub"] + 8.0 * L * u["pairs_hub"],
+        "k_wedge_hub": 4.0 * u["hub_wedges_counted"] + 8.0 * u["hub_slot_updates"] if "hub_slot_updates" in u else
+        12.0 * u["wedges_hub"] + 8.0 * L * u["pairs_hub"],
         "k_tsum": (8.0 + 4 * L + 24 * LL) * m + 4.0 * u["typed_min_sum"] + (12.0 + 12 * L + 4) * t_nodes,
         "k_clique": 4.0 * t_nodes + 8.0 * LL * m if cu is None else
         4.0 * (cu["t_small"] + cu["k_small"]) + 8.0 * LL * (m - cu["edges_big"]),
@@ -517,6 +523,9 @@ def run_ours(args):
         t_nodes = 3 * int(gl_host[b2:b2 + lay["global_block_size"][2]].sum())   # sum_e |T_e|
         cu = clique_units(pe, L)
         units.update({"clique": cu})
+        if work.get("hub_wedges"):
+            units.update({"hub_wedges_counted": float(work["hub_wedges"]),
+                          "hub_slot_updates": float(work["hub_slot_updates"])})
         abytes = algorithmic_bytes(units, m, L, S, t_nodes, cu)
         for name, (kms, nl) in kernel_ms.items():
             if abytes.get(name) is None or kms <= 0:

@@ -436,7 +436,10 @@ tg_status tg_count_directed3(tg_graph *g, uint32_t *per_edge_out, int64_t *globa
  * searches of edges with few pairs, and the SM clock cycles the CTAs of the
  * hub wedge pass spent waiting for their tickets' dependencies and working
  * on tickets of each kind (fill the counter tables, read them, clear them
- * by walking the wedges, clear them by zeroing).  Off by default. */
+ * by walking the wedges, clear them by zeroing), the wedges of the hub
+ * anchors and the nonzero 4-cycle slot updates the hub pass made (one per
+ * wedge (v, w) and type t of the fourth node with a nonzero count, and one
+ * per (hub, v, type) sum).  Off by default. */
 #define TG_WORK_CLIQUE_PROBES 0
 #define TG_WORK_CLIQUE_SEARCHES 1
 #define TG_WORK_CLIQUE_BIG_PROBES 2
@@ -445,7 +448,9 @@ tg_status tg_count_directed3(tg_graph *g, uint32_t *per_edge_out, int64_t *globa
 #define TG_WORK_HUB_READ_CYCLES 5
 #define TG_WORK_HUB_WALK_CLEAR_CYCLES 6
 #define TG_WORK_HUB_ZERO_CLEAR_CYCLES 7
-#define TG_WORK_SLOTS 8
+#define TG_WORK_HUB_WEDGES 8            /* wedges of the hub anchors (fill tickets) */
+#define TG_WORK_HUB_SLOT_UPDATES 9      /* nonzero 4-cycle slot updates of the hub pass */
+#define TG_WORK_SLOTS 16
 tg_status tg_set_work_counting(tg_graph *g, int32_t on);
 
 /* Synchronises the handle's stream, copies min(n, TG_WORK_SLOTS) counters

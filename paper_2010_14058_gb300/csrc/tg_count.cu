@@ -698,7 +698,7 @@ __device__ __forceinline__ int64_t hub_find_item(const int64_t *__restrict__ wof
 // 32-bit counter per type.  The tables are read and cleared at L2
 // (ld/st.cg): other CTAs of the same launch update them, so no L1 copy may
 // be trusted.
-template <bool kPacked>
+template <bool kPacked, bool kCount>
 __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubView &hv, int64_t i0, int64_t i1,
                            int64_t x0r, int64_t x1r, int32_t h0, uint32_t *tbl, int64_t stride, int phase, int wi,
                            int nwi, int lane) {
@@ -708,6 +708,7 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
     int64_t x0 = x0r + wi * per;
     const int64_t xe = min(x1r, x0 + per);
     if (x0 >= xe) return;                                   // warp-uniform
+    if (kCount && phase == 0 && lane == 0) atomicAdd(&cv.work[kWorkHubWedges], (unsigned long long)(xe - x0));
     const int64_t nnz = cv.a_stride;
     uint32_t *A = cv.A - cv.a_base;                         // indexed by absolute slot
     int64_t j = hub_find_item(hv.woff, i0, i1, x0, lane);
@@ -766,6 +767,13 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
             }
         }
         if (phase == 1) {
+            // (work counting) the round's nonzero slot updates: per wedge, then per item sum
+            unsigned nupd = 0;
+            if (kCount) {
+#pragma unroll
+                for (int t = 0; t < kMaxL; ++t) nupd += t < L && c[t] ? 1u : 0u;
+                nupd = __reduce_add_sync(0xffffffffu, nupd);
+            }
             // per-item sums over the lanes of each item (items are contiguous runs of lanes)
             const int64_t key = act ? it : -1;
             const int64_t key0 = __shfl_sync(0xffffffffu, key, 0);
@@ -776,6 +784,7 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
                     if (t >= L) break;
                     const uint32_t v = __reduce_add_sync(0xffffffffu, c[t]);
                     if (lane == 0 && v) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + svp], v);
+                    if (kCount) nupd += v ? 1u : 0u;       // (warp-uniform)
                 }
             } else {
                 unsigned same = 0;
@@ -796,8 +805,10 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
                         if (same & (1u << s)) v += y;
                     }
                     if (tail && v) atomicAdd(&A[(int64_t)(t * L + tw) * nnz + svp], v);
+                    if (kCount) nupd += __popc(__ballot_sync(0xffffffffu, tail && v));
                 }
             }
+            if (kCount && lane == 0 && nupd) atomicAdd(&cv.work[kWorkHubSlotUpdates], (unsigned long long)nupd);
         }
         j = jn;
         wo = won;
@@ -844,7 +855,7 @@ __device__ bool wait_done(const unsigned long long *ctr, unsigned long long targ
     return false;
 }
 
-template <bool kPacked>
+template <bool kPacked, bool kCount>
 __global__ void __launch_bounds__(kHubThreads, 5) k_wedge_hub(GraphView g, CountView cv, HubView hv,
                                                            const HubSegment *__restrict__ segs, int64_t n_segs,
                                                            int64_t n_tickets, const HubGroup *__restrict__ groups,
@@ -906,7 +917,8 @@ __global__ void __launch_bounds__(kHubThreads, 5) k_wedge_hub(GraphView g, Count
             if (kind == 3) {
                 for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) __stcg(tbl + x, 0u);
             } else {
-                hub_wedges<kPacked>(g, cv, hv, gr.i0, gr.i1, x0, x1, gr.h0, tbl, stride, kind, wid, nwarp, lane);
+                hub_wedges<kPacked, kCount>(g, cv, hv, gr.i0, gr.i1, x0, x1, gr.h0, tbl, stride, kind, wid, nwarp,
+                                            lane);
             }
         }
         __syncthreads();
@@ -2460,16 +2472,19 @@ static int64_t launch_hubs(Graph &G, size_t ci, cudaStream_t s) {
     const HubView hv = hub_view(G);
     const int grid = sm_count() * kHubCtasPerSm;
     KernelTimer kt(G, s, "k_wedge_hub");
-    if (G.hub_packed)
-        k_wedge_hub<true><<<grid, kHubThreads, 0, s>>>(gv, cv, hv, P.segs.as<HubSegment>(), P.n_segs, P.n_tickets,
-                                                       P.groups.as<HubGroup>(), P.ntick.as<int64_t>(),
-                                                       P.ctr.as<unsigned long long>(), G.hub_tables.as<uint32_t>(),
-                                                       G.hub_buf_words, G.hub_stride);
-    else
-        k_wedge_hub<false><<<grid, kHubThreads, 0, s>>>(gv, cv, hv, P.segs.as<HubSegment>(), P.n_segs, P.n_tickets,
-                                                        P.groups.as<HubGroup>(), P.ntick.as<int64_t>(),
-                                                        P.ctr.as<unsigned long long>(), G.hub_tables.as<uint32_t>(),
-                                                        G.hub_buf_words, G.hub_stride);
+    auto launch = [&](auto kern) {
+        kern<<<grid, kHubThreads, 0, s>>>(gv, cv, hv, P.segs.as<HubSegment>(), P.n_segs, P.n_tickets,
+                                          P.groups.as<HubGroup>(), P.ntick.as<int64_t>(), P.ctr.as<unsigned long long>(),
+                                          G.hub_tables.as<uint32_t>(), G.hub_buf_words, G.hub_stride);
+    };
+    const bool count = cv.work != nullptr;                  // the work-counting form (diagnostics)
+    if (G.hub_packed) {
+        if (count) launch(k_wedge_hub<true, true>);
+        else launch(k_wedge_hub<true, false>);
+    } else {
+        if (count) launch(k_wedge_hub<false, true>);
+        else launch(k_wedge_hub<false, false>);
+    }
     TG_CK(cudaGetLastError());
     return 1;
 }

@@ -33,7 +33,8 @@ constexpr int32_t kIdMask = (1 << kTypeShift) - 1;
 constexpr int kHeavyCap = 4096;                    // shared-memory hash rows of a heavy anchor
 // slots of the optional work counters (tg_set_work_counting; TG_WORK_*)
 enum : int { kWorkCliqueProbes = 0, kWorkCliqueSearches = 1, kWorkCliqueBigProbes = 2, kWorkHubWait = 3,
-             kWorkHubKind = 4 /* + ticket kind 0..3 */, kWorkSlots = 8 };
+             kWorkHubKind = 4 /* + ticket kind 0..3 */, kWorkHubWedges = 8, kWorkHubSlotUpdates = 9,
+             kWorkSlots = 16 };
 constexpr int kHeavyFit = kHeavyCap / 4 * 3;       // its load limit (distinct wedge ends)
 
 // Persistent hub pass (tg_count.cu): a group of hubs whose counter tables

@@ -408,7 +408,8 @@ def tg_get_timing(g: Graph, max_entries: int = 32) -> dict:
 
 
 WORK_SLOTS = {"clique_probes": 0, "clique_searches": 1, "clique_big_probes": 2, "hub_wait_cycles": 3,
-              "hub_fill_cycles": 4, "hub_read_cycles": 5, "hub_walk_clear_cycles": 6, "hub_zero_clear_cycles": 7}
+              "hub_fill_cycles": 4, "hub_read_cycles": 5, "hub_walk_clear_cycles": 6, "hub_zero_clear_cycles": 7,
+              "hub_wedges": 8, "hub_slot_updates": 9}
 
 
 def tg_set_work_counting(g: "Graph", on: bool = True) -> None:
@@ -419,8 +420,8 @@ def tg_set_work_counting(g: "Graph", on: bool = True) -> None:
 def tg_get_work(g: "Graph") -> dict:
     """Work counters accumulated since the last call (then cleared)."""
     import numpy as np
-    out = np.zeros(8, dtype=np.int64)
-    _check(load().tg_get_work(g.handle, out.ctypes.data, 8), "tg_get_work")
+    out = np.zeros(16, dtype=np.int64)
+    _check(load().tg_get_work(g.handle, out.ctypes.data, 16), "tg_get_work")
     return {name: int(out[k]) for name, k in WORK_SLOTS.items()}
 
 
