@@ -189,7 +189,7 @@ def load_peaks():
 # DRAM bytes (read + write) per launch of a kernel, from the ncu capture
 # summarised under profiles/ for that workload and the current kernel code
 # (an entry is removed when its kernel changes).
-TRAFFIC = {}
+TRAFFIC = {("cl_large", "k_wedge_hub"): 283.908528e9, ("cl_large", "k_clique_big"): 2.538992e9}
 
 # Issue-limited peak of the 4-clique lookups: 152 SMs x 4 schedulers x 32
 # lanes x the maximum SM clock give the lane-instruction rate; one lookup

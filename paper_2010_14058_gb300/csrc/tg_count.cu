@@ -713,6 +713,7 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
     uint32_t *A = cv.A - cv.a_base;                         // indexed by absolute slot
     int64_t j = hub_find_item(hv.woff, i0, i1, x0, lane);
     int64_t wo = j + lane < i1 ? hv.woff[j + lane] : INT64_MAX;
+    unsigned long long nupd_run = 0;                        // (work counting) the warp's slot updates
     for (; x0 < xe; x0 += 32) {
         // the wedges x0 .. x0+31 lie in items j .. j+31 (every item is non-empty)
         const int64_t x = x0 + lane;
@@ -768,7 +769,7 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
         }
         if (phase == 1) {
             // (work counting) the round's nonzero slot updates: per wedge, then per item sum
-            unsigned nupd = 0;
+            unsigned nupd = 0;                              // (work counting) this round's, warp-wide
             if (kCount) {
 #pragma unroll
                 for (int t = 0; t < kMaxL; ++t) nupd += t < L && c[t] ? 1u : 0u;
@@ -808,11 +809,12 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
                     if (kCount) nupd += __popc(__ballot_sync(0xffffffffu, tail && v));
                 }
             }
-            if (kCount && lane == 0 && nupd) atomicAdd(&cv.work[kWorkHubSlotUpdates], (unsigned long long)nupd);
+            if (kCount) nupd_run += nupd;
         }
         j = jn;
         wo = won;
     }
+    if (kCount && lane == 0 && nupd_run) atomicAdd(&cv.work[kWorkHubSlotUpdates], nupd_run);
 }
 
 // The hub pass as one persistent launch over a ticket queue.  The hubs are
