@@ -118,7 +118,9 @@ typedef struct {
                                          warp per edge in the 4-clique pass (CTA per edge above) */
     int32_t light_anchor_max_wedges;  /* wedge anchors with at most this many wedges: warp per anchor
                                          (at most 2048, and what one CTA's shared memory holds for L) */
-    int32_t anchor_table_budget_mb;   /* device memory for per-CTA wedge tables */
+    int32_t anchor_table_budget_mb;   /* device memory for the dense node tables of heavy anchors with
+                                         too many wedges for shared memory, one per CTA that takes them
+                                         (default 12,288; at most two CTAs per SM get one) */
     int32_t ctas_per_sm;              /* resident CTAs per SM for the per-edge kernels */
     int32_t cycle_budget_mb;          /* device memory for the per-slot 4-cycle array; a batch whose
                                          array would exceed it is counted in chunks of whole graphs */

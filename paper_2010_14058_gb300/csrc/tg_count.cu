@@ -471,10 +471,11 @@ __global__ void __launch_bounds__(kLightAnchorWarps * 32) k_wedge_light(GraphVie
 
 // Heavy anchors: one CTA per anchor, warps over the anchor's lower-priority
 // neighbours v.  The rows h[w][.] live in a shared-memory hash of kHeavyCap
-// entries; an anchor whose distinct w exceed 3/4 of it is redone against
-// the CTA's dense node table in global memory (cleared again by phase 2).
-// Anchors with more wedges than that limit go to the dense table directly:
-// on power-law graphs their wedge ends are almost all distinct.
+// entries.  Anchors with more wedges than 3/4 of it go to a dense node table
+// in global memory (cleared again by phase 2): on power-law graphs their
+// wedge ends are almost all distinct.  Only the first n_tables CTAs own a
+// table (the budget of anchor_table_budget_mb); the grid may be larger, and
+// the CTAs without a table take hash anchors only.
 
 __device__ int hash_insert_bounded(int32_t *keys, int cap, int32_t w, int *fill, int limit) {
     int h = hash_slot(w, cap);
@@ -495,70 +496,86 @@ __device__ int hash_insert_bounded(int32_t *keys, int cap, int32_t w, int *fill,
 
 __global__ void __launch_bounds__(kAnchorThreads, 2) k_wedge_heavy(GraphView g, CountView cv,
                                                                const int32_t *__restrict__ anchors,
-                                                               int64_t n_anchors, int64_t n_dense, int64_t n0,
-                                                               int64_t n1) {
+                                                               int64_t n_anchors, int64_t n_dense, int64_t n_tables,
+                                                               int64_t n0, int64_t n1) {
     extern __shared__ int32_t hsm[];
     __shared__ int s_fill, s_over;
     const int L = g.L;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     int32_t *keys = hsm;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(hsm + kHeavyCap);
-    uint32_t *tbl = cv.tables + (int64_t)blockIdx.x * cv.table_stride;
+    const bool has_table = blockIdx.x < n_tables;
+    uint32_t *tbl = cv.tables + (int64_t)(has_table ? blockIdx.x : 0) * cv.table_stride;
+    // a CTA without a dense table never falls back to one: its hash anchors
+    // have at most kHeavyFit distinct wedge ends, and with the limit at the
+    // capacity the fill count (distinct ends plus at most one in-flight
+    // insert per thread) cannot reach it
+    const int limit = has_table ? kHeavyFit : kHeavyCap - 1;
     const int64_t nnz = cv.a_stride;
     uint32_t *A = cv.A - cv.a_base;                          // indexed by absolute slot
-    for (int64_t a = blockIdx.x; a < n_anchors; a += gridDim.x) {
-        const int32_t u = anchors[a];
-        if (u < n0 || u >= n1) continue;                    // anchor outside this chunk (uniform per CTA)
-        const int tu = g.ty[u];
-        const int64_t base = g.node_off[graph_of_node(g, u)];
-        // the first n_dense anchors (wedges above the hash's load limit, sorted
-        // first) would overflow the hash: they go to the dense table at once
-        const bool pre_dense = a < n_dense;
-        if (!pre_dense) {
-            for (int k = threadIdx.x; k < kHeavyCap; k += blockDim.x) keys[k] = -1;
-            for (int k = threadIdx.x; k < kHeavyCap * L; k += blockDim.x) cnt[k] = 0;
-        }
-        if (threadIdx.x == 0) { s_fill = 0; s_over = pre_dense ? 1 : 0; }
-        __syncthreads();
-        int64_t ub;
-        int32_t uoff;
-        const int32_t nV = u_runs(g, u, lane, ub, uoff);
-        auto hash_rows = [&](int32_t w, bool insert) -> uint32_t * {
-            int h;
-            if (insert) {
-                h = hash_insert_bounded(keys, kHeavyCap, w, &s_fill, kHeavyCap * 3 / 4);
-                if (h < 0) { s_over = 1; return nullptr; }
-            } else {
-                h = hash_find(keys, kHeavyCap, w);
-                if (h < 0) return nullptr;
+    // pass 0: the first n_dense anchors (more wedges than the hash's load
+    // limit, sorted first) against the dense tables, by the CTAs that own
+    // one; pass 1: the other anchors against the shared-memory hash, by all
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t a_end = pass == 0 ? (has_table ? n_dense : 0) : n_anchors;
+        const int64_t a_step = pass == 0 ? n_tables : gridDim.x;
+        for (int64_t a = (pass == 0 ? 0 : n_dense) + blockIdx.x; a < a_end; a += a_step) {
+            const int32_t u = anchors[a];
+            if (u < n0 || u >= n1) continue;                // anchor outside this chunk (uniform per CTA)
+            const int tu = g.ty[u];
+            const int64_t base = g.node_off[graph_of_node(g, u)];
+            const bool pre_dense = pass == 0;
+            if (!pre_dense) {
+                for (int k = threadIdx.x; k < kHeavyCap; k += blockDim.x) keys[k] = -1;
+                for (int k = threadIdx.x; k < kHeavyCap * L; k += blockDim.x) cnt[k] = 0;
             }
-            return cnt + h * L;
-        };
-        auto dense_rows = [&](int32_t w, bool) -> uint32_t * { return tbl + (int64_t)(w - base) * L; };
-        if (!pre_dense) {
-            for (int32_t kv = wid; kv < nV; kv += nwarp) {
-                int tv;
-                const int64_t sv = u_slot(ub, uoff, kv, tv);
-                wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, hash_rows);
-            }
+            if (threadIdx.x == 0) { s_fill = 0; s_over = pre_dense ? 1 : 0; }
             __syncthreads();
-        }
-        const bool dense = s_over != 0;                     // uniform after the barrier
-        if (dense)
-            for (int32_t kv = wid; kv < nV; kv += nwarp) {
-                int tv;
-                const int64_t sv = u_slot(ub, uoff, kv, tv);
-                wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, dense_rows);
+            int64_t ub;
+            int32_t uoff;
+            const int32_t nV = u_runs(g, u, lane, ub, uoff);
+            auto hash_rows = [&](int32_t w, bool insert) -> uint32_t * {
+                int h;
+                if (insert) {
+                    h = hash_insert_bounded(keys, kHeavyCap, w, &s_fill, limit);
+                    if (h < 0) { s_over = 1; return nullptr; }
+                } else {
+                    h = hash_find(keys, kHeavyCap, w);
+                    if (h < 0) return nullptr;
+                }
+                return cnt + h * L;
+            };
+            auto dense_rows = [&](int32_t w, bool) -> uint32_t * { return tbl + (int64_t)(w - base) * L; };
+            if (!pre_dense) {
+                for (int32_t kv = wid; kv < nV; kv += nwarp) {
+                    int tv;
+                    const int64_t sv = u_slot(ub, uoff, kv, tv);
+                    wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, hash_rows);
+                }
+                __syncthreads();
             }
-        __syncthreads();
-        for (int phase = 1; phase < (dense ? 3 : 2); ++phase) {
-            for (int32_t kv = wid; kv < nV; kv += nwarp) {
-                int tv;
-                const int64_t sv = u_slot(ub, uoff, kv, tv);
-                if (dense) wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, phase, lane, dense_rows);
-                else wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, phase, lane, hash_rows);
+            const bool dense = s_over != 0;                 // uniform after the barrier
+            if (dense && !has_table) {                      // excluded above; reported, never miscounted
+                if (threadIdx.x == 0) set_status(cv.status, ST_INTERNAL);
+                __syncthreads();
+                continue;
             }
+            if (dense)
+                for (int32_t kv = wid; kv < nV; kv += nwarp) {
+                    int tv;
+                    const int64_t sv = u_slot(ub, uoff, kv, tv);
+                    wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, 0, lane, dense_rows);
+                }
             __syncthreads();
+            for (int phase = 1; phase < (dense ? 3 : 2); ++phase) {
+                for (int32_t kv = wid; kv < nV; kv += nwarp) {
+                    int tv;
+                    const int64_t sv = u_slot(ub, uoff, kv, tv);
+                    if (dense) wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, phase, lane, dense_rows);
+                    else wedge_v(g, A, nnz, u, tu, g.adj[sv], tv, sv, phase, lane, hash_rows);
+                }
+                __syncthreads();
+            }
         }
     }
 }
@@ -2513,9 +2530,9 @@ static int64_t launch_wedges(Graph &G, const Graph::Chunk &c, cudaStream_t s) {
     if (G.n_hubs > 0) launches += launch_hubs(G, (size_t)(&c - G.chunks.data()), s);
     if (G.n_anchors_heavy > 0) {
         KernelTimer kt(G, s, "k_wedge_heavy");
-        k_wedge_heavy<<<G.n_tables, kAnchorThreads, (size_t)kHeavyCap * (1 + L) * sizeof(int32_t), s>>>(
-            gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy, G.n_heavy_dense,
-                                                             c.n0, c.n1);
+        const int grid = (int)std::min<int64_t>(std::max<int64_t>(G.n_tables, 2 * sms), G.n_anchors_heavy);
+        k_wedge_heavy<<<std::max(grid, G.n_tables), kAnchorThreads, (size_t)kHeavyCap * (1 + L) * sizeof(int32_t), s>>>(
+            gv, cv, G.anchors_heavy.as<int32_t>(), G.n_anchors_heavy, G.n_heavy_dense, G.n_tables, c.n0, c.n1);
         ++launches;
     }
     TG_CK(cudaGetLastError());

@@ -291,7 +291,7 @@ inline void fill_defaults(tg_options *o) {
     std::memset(o, 0, sizeof(*o));
     o->light_edge_max_degree = 256;
     o->light_anchor_max_wedges = 64;
-    o->anchor_table_budget_mb = 4096;
+    o->anchor_table_budget_mb = 12288;
     o->ctas_per_sm = 3;
     o->cycle_budget_mb = 16384;
     o->hub_min_wedges = 1 << 14;
