@@ -561,6 +561,9 @@ def run_ours(args):
                         "peak_kind": peak_kind, "unit": "GB/s", "frac": pk["frac"],
                         "algorithmic_bytes": abytes[top], "ms_per_step": pk["ms_per_step"],
                         "traffic": TRAFFIC.get((args.workload, top))}
+            if roofline["traffic"]:
+                # the measured DRAM bytes of a launch over its CUDA-event time
+                roofline["traffic_frac"] = round(roofline["traffic"] / (pk["ms_per_step"] / 1e3) / 1e9 / peak, 5)
         # compulsory traffic of the whole count: CSR and types read once,
         # outputs written once -- the headline "% of HBM roofline"
         cb = 8.0 * m + 8.0 * g["n"] + g["n"] + 4.0 * S * m + 8.0 * G

@@ -104,6 +104,17 @@ def test_chung_lu_with_hubs(options):
     assert_parity(g, options=options)
 
 
+@pytest.mark.parametrize("budget_mb", [1, 12288])
+def test_heavy_anchors_with_few_dense_tables(budget_mb):
+    # 506 heavy anchors and no hubs; 64 of them have more wedges than the
+    # shared-memory hash holds and go to dense node tables.  A 1 MB table
+    # budget gives 10 tables (100 KB each), so 10 CTAs take those 64 and the
+    # rest of the grid (two CTAs per SM) only hash anchors; 12 GB gives every
+    # CTA a table.
+    g = graphgen.chung_lu(5000, 40000, 2.1, 900.0, 5, 19)
+    assert_parity(g, options={"hub_min_wedges": 1 << 30, "anchor_table_budget_mb": budget_mb})
+
+
 # typed set intersection forced to one method in every length bucket
 ALL_BINARY = {"isect_modes": 0b01010101}
 ALL_MERGE = {"isect_modes": 0b10101010}
