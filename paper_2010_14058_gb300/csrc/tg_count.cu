@@ -786,7 +786,7 @@ __device__ void hub_wedges(const GraphView &g, const CountView &cv, const HubVie
         }
         if (phase == 1) {
             // (work counting) the round's nonzero slot updates: per wedge, then per item sum
-            unsigned nupd = 0;                              // (work counting) this round's, warp-wide
+            unsigned nupd = 0;                              // (work counting) these 32 wedges' updates, warp-wide
             if (kCount) {
 #pragma unroll
                 for (int t = 0; t < kMaxL; ++t) nupd += t < L && c[t] ? 1u : 0u;
