@@ -14,7 +14,9 @@ Three independent routes over the same output layout (see oracle.c):
 Alg. 5 by direct enumeration; :func:`position_aware` the position-aware
 typed counts of Sec. 5 (Def. 8), per edge and global; :func:`directed3`
 and :func:`directed3_brute` the directed typed 3-node graphlets of Sec. 4.8
-(oriented graphs given by their out-neighbour CSR).
+(oriented graphs given by their out-neighbour CSR); :func:`edge_typed3`
+and :func:`edge_typed3_brute` the typed 3-node graphlets of a graph whose
+edges also carry types (Def. 1's xi, classes by Defs. 4-5).
 
 All counts are exact int64.  Parity with these is the acceptance bar for
 the GPU path (bit-exact).
@@ -80,6 +82,10 @@ _SIGS = {
     "oracle_directed3": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_directed3_brute": ("i64 vp vp vp i32 vp vp", "i32"),
     "oracle_directed_edges": ("i64 vp vp vp i32 vp vp vp", "i32"),
+    "oracle_et_per_edge_slots": ("i32 i32", "i64"),
+    "oracle_et_global_slots": ("i32 i32", "i64"),
+    "oracle_edge_typed3": ("i64 vp vp vp vp i32 i32 vp vp", "i32"),
+    "oracle_edge_typed3_brute": ("i64 vp vp vp vp i32 i32 vp vp", "i32"),
     "oracle_graph_open": ("i64 vp vp vp i32 vp", "vp"),
     "oracle_graph_close": ("vp", "i32"),
     "oracle_graph_paper_edges": ("vp i32 vp i64 vp vp vp i32", "i32"),
@@ -335,6 +341,43 @@ def directed3_brute(g, per_edge: bool = True, lib=None):
     """Every 3-node subset of a small oriented graph -> same layout as directed3."""
     lib = lib or _load()
     return _directed(lib.oracle_directed3_brute, g, per_edge, lib)
+
+
+# ------------------------------------------- edge types (Def. 1, Defs. 4-5)
+
+def edge_typed_per_edge_slots(L: int, X: int, lib=None) -> int:
+    """L X path slots, then L X(X+1)/2 triangle slots."""
+    lib = lib or _load()
+    return int(lib.oracle_et_per_edge_slots(L, X))
+
+
+def edge_typed_global_slots(L: int, X: int, lib=None) -> int:
+    lib = lib or _load()
+    return int(lib.oracle_et_global_slots(L, X))
+
+
+def _edge_typed(fn, g, edge_types, X, per_edge, lib):
+    rp, col, ty = _args(g)
+    xi = np.ascontiguousarray(edge_types, dtype=np.uint8)
+    L = g["L"]
+    pe = np.zeros((g["m"], edge_typed_per_edge_slots(L, X, lib)), dtype=np.int64) if per_edge else None
+    gl = np.zeros(edge_typed_global_slots(L, X, lib), dtype=np.int64)
+    _check(fn(g["n"], _p(rp), _p(col), _p(ty), _p(xi), L, X, _p(pe), _p(gl)))
+    return pe, gl
+
+
+def edge_typed3(g, edge_types, X: int, per_edge: bool = True, lib=None):
+    """Alg. 1 with the typed sets split by edge type -> (per_edge int64
+    [m, L X + L X(X+1)/2] or None, global int64 [edges, 3-paths, triangles
+    by node-type and edge-type multisets]); edge_types: one per entry of col."""
+    lib = lib or _load()
+    return _edge_typed(lib.oracle_edge_typed3, g, edge_types, X, per_edge, lib)
+
+
+def edge_typed3_brute(g, edge_types, X: int, per_edge: bool = True, lib=None):
+    """Every 3-node subset of a small graph -> same layout as edge_typed3."""
+    lib = lib or _load()
+    return _edge_typed(lib.oracle_edge_typed3_brute, g, edge_types, X, per_edge, lib)
 
 
 class OpenGraph:

@@ -77,7 +77,7 @@
 #define OR_MAX_L 16
 
 /* Planted mistakes for the pin tests: a test compiles a separate copy of
- * this file with -DORACLE_MUTANT=k (k = 1..12) and checks that the pins fail.
+ * this file with -DORACLE_MUTANT=k (k = 1..16) and checks that the pins fail.
  * The default build (ORACLE_MUTANT undefined) contains none of them. */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
@@ -1569,5 +1569,247 @@ int oracle_directed_edges(int64_t n, const int64_t *out_row_ptr, const int32_t *
         memcpy(orient, D.eo, (size_t)D.m);
     }
     dgraph_close(&D);
+    return rc;
+}
+
+/* ======================================================================
+ * Edge-typed 3-node graphlets (Def. 1's edge types xi; Defs. 4-5: the
+ * class of a typed graphlet is its shape with the multisets of its node
+ * types and of its edge types).
+ *
+ * Per edge e = (i, j), i < j in the caller's ids, every third node k of
+ * type t adds 1 to one slot:
+ *   k in S_i or S_j (a 3-path through e): slot (t, x) of the path block,
+ *     x the type of k's edge to i (S_i) or to j (S_j) -- the path's class
+ *     ({phi_i, phi_j, t}, {xi_ij, x}) is the same either way;
+ *   k in T (a triangle): slot (t, {xi_ik, xi_jk}) of the triangle block.
+ * Per-edge layout: [L][X] paths, then [L][X(X+1)/2] triangles, the pair of
+ * edge types ranked as a sorted 2-multiset over [0, X).
+ * Global layout: [edges: multisets of 2 node types x X edge types]
+ * [3-paths: multisets of 3 node types x multisets of 2 edge types]
+ * [triangles: multisets of 3 node types x multisets of 3 edge types],
+ * the node-type multiset rank the major index.
+ * ==================================================================== */
+
+#define OR_MAX_X 8
+
+int64_t oracle_et_per_edge_slots(int L, int X) { return (int64_t)L * X + (int64_t)L * npairs(X); }
+
+int64_t oracle_et_global_slots(int L, int X) {
+    return binom(L + 1, 2) * X + binom(L + 2, 3) * binom(X + 1, 2) + binom(L + 2, 3) * binom(X + 2, 3);
+}
+
+typedef struct { int32_t v; uint8_t x; } eent_t;
+static int cmp_eent(const void *p, const void *q) {
+    int32_t a = ((const eent_t *)p)->v, b = ((const eent_t *)q)->v;
+    return (a > b) - (a < b);
+}
+
+typedef struct {
+    int64_t n, m;
+    int L, X;
+    const int64_t *rp;
+    int32_t *adj;              /* rows sorted by id */
+    uint8_t *xi;               /* edge type of each entry */
+    const uint8_t *phi;
+    int64_t *eu, *ev;          /* edges u < v, lexicographic */
+} egraph_t;
+
+static void egraph_close(egraph_t *E) { free(E->adj); free(E->xi); free(E->eu); free(E->ev); }
+
+/* edge type of {u, v}, or -1 when u and v are not adjacent */
+static int egraph_type(const egraph_t *E, int64_t u, int64_t v) {
+    int64_t lo = E->rp[u], hi = E->rp[u + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (E->adj[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return (lo < E->rp[u + 1] && E->adj[lo] == v) ? E->xi[lo] : -1;
+}
+
+/* copies and sorts the rows with their edge types; a simple symmetric graph
+ * whose two entries of every edge carry the same type below X */
+static int egraph_open(egraph_t *E, int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *phi,
+                       const uint8_t *xi, int L, int X) {
+    memset(E, 0, sizeof(*E));
+    if (n < 0 || L < 1 || L > OR_MAX_L || X < 1 || X > OR_MAX_X) return ERR_ARG;
+    int64_t nnz = rp[n];
+    if (rp[0] != 0 || nnz < 0 || (nnz & 1)) return ERR_GRAPH;
+    for (int64_t v = 0; v < n; ++v) if (rp[v + 1] < rp[v] || phi[v] >= L) return ERR_GRAPH;
+    for (int64_t k = 0; k < nnz; ++k) if (col[k] < 0 || col[k] >= n || xi[k] >= X) return ERR_GRAPH;
+    E->n = n; E->m = nnz / 2; E->L = L; E->X = X; E->rp = rp; E->phi = phi;
+    E->adj = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    E->xi = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    E->eu = (int64_t *)malloc((size_t)(E->m > 0 ? E->m : 1) * sizeof(int64_t));
+    E->ev = (int64_t *)malloc((size_t)(E->m > 0 ? E->m : 1) * sizeof(int64_t));
+    eent_t *tmp = (eent_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(eent_t));
+    if (!E->adj || !E->xi || !E->eu || !E->ev || !tmp) { free(tmp); return ERR_MEM; }
+    for (int64_t k = 0; k < nnz; ++k) tmp[k] = (eent_t){col[k], xi[k]};
+    for (int64_t v = 0; v < n; ++v) qsort(tmp + rp[v], (size_t)(rp[v + 1] - rp[v]), sizeof(eent_t), cmp_eent);
+    for (int64_t k = 0; k < nnz; ++k) { E->adj[k] = tmp[k].v; E->xi[k] = tmp[k].x; }
+    free(tmp);
+    int64_t e = 0;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t k = rp[u]; k < rp[u + 1]; ++k) {
+            int64_t v = E->adj[k];
+            if (v == u) return ERR_GRAPH;                                        /* self-loop */
+            if (k > rp[u] && E->adj[k - 1] == v) return ERR_GRAPH;               /* duplicate */
+            if (egraph_type(E, v, u) != E->xi[k]) return ERR_GRAPH;              /* asymmetric, or types differ */
+            if (u < v) {
+                if (e >= E->m) return ERR_GRAPH;
+                E->eu[e] = u; E->ev[e] = v; ++e;
+            }
+        }
+    if (e != E->m) return ERR_GRAPH;
+    return OK;
+}
+
+/* global slot of a class: block 0 (an edge), 1 (a 3-path), 2 (a triangle);
+ * nt node types and nt - 1 (edge) or the shape's edge types */
+static int64_t et_global_slot(int L, int X, int block, const int *nodes, const int *edges) {
+    const int64_t rn = multiset_rank(L, block == 0 ? 2 : 3, nodes);
+    const int64_t re = block == 0 ? edges[0] : multiset_rank(X, block == 1 ? 2 : 3, edges);
+    if (rn < 0 || re < 0) return -1;                                   /* (a wrong rank is reported) */
+    if (block == 0) return rn * X + re;
+    const int64_t off1 = binom(L + 1, 2) * X, off2 = off1 + binom(L + 2, 3) * binom(X + 1, 2);
+    if (block == 1) return off1 + rn * binom(X + 1, 2) + re;
+    return off2 + rn * binom(X + 2, 3) + re;
+}
+
+/* Alg. 1 with the sets split by edge type: mark Gamma_i with the type of
+ * each node's edge to i, scan Gamma_j (T and S_j), then the rest of Gamma_i
+ * (S_i).  per_edge_out: int64 [m][oracle_et_per_edge_slots] or NULL;
+ * global_out: int64 [oracle_et_global_slots] or NULL. */
+int oracle_edge_typed3(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *types,
+                       const uint8_t *edge_types, int L, int X, int64_t *per_edge_out, int64_t *global_out) {
+    egraph_t E;
+    int rc = egraph_open(&E, n, row_ptr, col, types, edge_types, L, X);
+    if (rc != OK) { egraph_close(&E); return rc; }
+    const int64_t S = oracle_et_per_edge_slots(L, X), PX = npairs(X), Gs = oracle_et_global_slots(L, X);
+    int16_t *mark = (int16_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int16_t));   /* 1 + type of the edge to i */
+    int64_t *row = (int64_t *)malloc((size_t)S * sizeof(int64_t));
+    int64_t *raw = (int64_t *)calloc((size_t)Gs, sizeof(int64_t));
+    if (!mark || !row || !raw) { free(mark); free(row); free(raw); egraph_close(&E); return ERR_MEM; }
+    for (int64_t e = 0; e < E.m && rc == OK; ++e) {
+        const int64_t i = E.eu[e], j = E.ev[e];
+        const int xij = egraph_type(&E, i, j);
+        memset(row, 0, (size_t)S * sizeof(int64_t));
+        for (int64_t k = E.rp[i]; k < E.rp[i + 1]; ++k) if (E.adj[k] != j) mark[E.adj[k]] = (int16_t)(1 + E.xi[k]);
+        for (int64_t k = E.rp[j]; k < E.rp[j + 1]; ++k) {                  /* T and S_j */
+            const int64_t w = E.adj[k];
+            if (w == i) continue;
+            const int t = types[w], xj = E.xi[k];
+            if (mark[w] > 0) {
+                const int xi_w = mark[w] - 1;
+                const int pair[2] = {xi_w, MUTANT(16) ? xi_w : xj};           /* planted: j's edge dropped */
+                const int64_t r = multiset_rank(X, 2, pair);
+                if (r < 0) { rc = ERR_REMAINDER; break; }                  /* (a wrong rank is reported) */
+                row[(int64_t)L * X + t * PX + r] += 1;
+                mark[w] = -1;                                              /* in T */
+            } else {
+                row[t * X + (MUTANT(15) ? xij : xj)] += 1;                  /* planted: the edge's own type */
+            }
+        }
+        for (int64_t k = E.rp[i]; k < E.rp[i + 1]; ++k) {                  /* S_i */
+            const int64_t w = E.adj[k];
+            if (w == j || mark[w] < 0) continue;
+            row[types[w] * X + E.xi[k]] += 1;
+        }
+        for (int64_t k = E.rp[i]; k < E.rp[i + 1]; ++k) mark[E.adj[k]] = 0;
+        if (per_edge_out) memcpy(per_edge_out + e * S, row, (size_t)S * sizeof(int64_t));
+        if (global_out) {
+            const int nodes2[2] = {types[i], types[j]}, edges1[1] = {xij};
+            const int64_t g2 = et_global_slot(L, X, 0, nodes2, edges1);
+            if (g2 < 0) rc = ERR_REMAINDER; else raw[g2] += 1;
+            for (int t = 0; t < L; ++t) {
+                const int nodes3[3] = {types[i], types[j], t};
+                for (int x = 0; x < X; ++x) {
+                    const int64_t v = row[t * X + x];
+                    const int edges2[2] = {xij, x};
+                    const int64_t gs = et_global_slot(L, X, 1, nodes3, edges2);
+                    if (gs < 0) rc = ERR_REMAINDER;
+                    else if (v) raw[gs] += v;
+                }
+                for (int x = 0; x < X; ++x)
+                    for (int y = x; y < X; ++y) {
+                        const int pair[2] = {x, y};
+                        const int64_t r = multiset_rank(X, 2, pair);
+                        const int edges3[3] = {xij, x, y};
+                        const int64_t gs = et_global_slot(L, X, 2, nodes3, edges3);
+                        if (r < 0 || gs < 0) { rc = ERR_REMAINDER; continue; }
+                        const int64_t v = row[(int64_t)L * X + t * PX + r];
+                        if (v) raw[gs] += v;
+                    }
+            }
+        }
+    }
+    if (global_out && rc == OK) {
+        /* Sec. 6: a 3-path is seen from its 2 edges, a triangle from its 3 */
+        const int64_t off1 = binom(L + 1, 2) * X, off2 = off1 + binom(L + 2, 3) * binom(X + 1, 2);
+        for (int64_t s = 0; s < Gs && rc == OK; ++s) {
+            const int64_t d = s < off1 ? 1 : (s < off2 ? 2 : 3);
+            if (raw[s] % d) rc = ERR_REMAINDER;
+            global_out[s] = raw[s] / d;
+        }
+    }
+    free(mark); free(row); free(raw);
+    egraph_close(&E);
+    return rc;
+}
+
+/* Every 3-node subset: its induced edges and their types; a connected one
+ * adds 1 to its class and, for each of its edges, to that edge's slot keyed
+ * by the third node.  Small graphs only. */
+int oracle_edge_typed3_brute(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *types,
+                             const uint8_t *edge_types, int L, int X, int64_t *per_edge_out, int64_t *global_out) {
+    egraph_t E;
+    int rc = egraph_open(&E, n, row_ptr, col, types, edge_types, L, X);
+    if (rc != OK) { egraph_close(&E); return rc; }
+    const int64_t S = oracle_et_per_edge_slots(L, X), PX = npairs(X);
+    if (per_edge_out) memset(per_edge_out, 0, (size_t)(E.m * S) * sizeof(int64_t));
+    if (global_out) memset(global_out, 0, (size_t)oracle_et_global_slots(L, X) * sizeof(int64_t));
+    for (int64_t e = 0; e < E.m; ++e)
+        if (global_out) {
+            const int nodes2[2] = {types[E.eu[e]], types[E.ev[e]]}, edges1[1] = {egraph_type(&E, E.eu[e], E.ev[e])};
+            const int64_t g2 = et_global_slot(L, X, 0, nodes2, edges1);
+            if (g2 < 0) rc = ERR_REMAINDER; else global_out[g2] += 1;
+        }
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t b = a + 1; b < n; ++b)
+            for (int64_t c = b + 1; c < n; ++c) {
+                const int64_t v[3] = {a, b, c};
+                int x[3][3], ne = 0, ed[3];
+                for (int p = 0; p < 3; ++p)
+                    for (int q = 0; q < 3; ++q) x[p][q] = p == q ? -1 : egraph_type(&E, v[p], v[q]);
+                for (int p = 0; p < 3; ++p)
+                    for (int q = p + 1; q < 3; ++q)
+                        if (x[p][q] >= 0) ed[ne++] = x[p][q];
+                if (ne < 2) continue;                                      /* not connected */
+                const int nodes3[3] = {types[a], types[b], types[c]};
+                const int64_t gs = et_global_slot(L, X, ne == 2 ? 1 : 2, nodes3, ed);
+                if (gs < 0) { rc = ERR_REMAINDER; continue; }
+                if (global_out) global_out[gs] += 1;
+                if (!per_edge_out) continue;
+                for (int p = 0; p < 3; ++p)
+                    for (int q = p + 1; q < 3; ++q) {
+                        if (x[p][q] < 0) continue;
+                        const int w = 3 - p - q;                           /* edge (v[p], v[q]), third node v[w] */
+                        int64_t lo = 0, hi = E.m;
+                        while (lo < hi) {
+                            int64_t mid = (lo + hi) / 2;
+                            if (E.eu[mid] < v[p] || (E.eu[mid] == v[p] && E.ev[mid] < v[q])) lo = mid + 1; else hi = mid;
+                        }
+                        const int t = types[v[w]];
+                        if (ne == 3) {
+                            const int pair[2] = {x[p][w], x[q][w]};
+                            const int64_t r = multiset_rank(X, 2, pair);
+                            if (r < 0) { rc = ERR_REMAINDER; continue; }
+                            per_edge_out[lo * S + (int64_t)L * X + t * PX + r] += 1;
+                        } else {
+                            per_edge_out[lo * S + t * X + (x[p][w] >= 0 ? x[p][w] : x[q][w])] += 1;
+                        }
+                    }
+            }
+    egraph_close(&E);
     return rc;
 }

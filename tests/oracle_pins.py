@@ -542,3 +542,143 @@ def directed_pins(lib=None):
                 and go[1:].sum() == go[1 + out_star] and gi[1:].sum() == gi[1 + in_star])
     check("directed stars", stars)
     return failed
+
+
+# ------------------------------------------- edge types (Def. 1, Defs. 4-5)
+
+def edge_types_for(g, X, seed):
+    """One seeded type in [0, X) per edge, written to both of its entries of col."""
+    rng = np.random.default_rng(seed)
+    rp, col = g["row_ptr"], g["col"]
+    xi = np.zeros(len(col), dtype=np.uint8)
+    seen = {}
+    for u in range(g["n"]):
+        for k in range(rp[u], rp[u + 1]):
+            key = (min(u, int(col[k])), max(u, int(col[k])))
+            if key not in seen:
+                seen[key] = int(rng.integers(0, X))
+            xi[k] = seen[key]
+    return xi
+
+
+def edge_types_from(g, fn):
+    """Edge types from a function of the edge {u, v} (u < v)."""
+    rp, col = g["row_ptr"], g["col"]
+    return np.array([fn(min(u, int(col[k])), max(u, int(col[k]))) for u in range(g["n"])
+                     for k in range(rp[u], rp[u + 1])], dtype=np.uint8)
+
+
+def et_offsets(L, X):
+    """Starts of the three global blocks: edges, 3-paths, triangles."""
+    n2 = len(multisets(L, 2)) * X
+    n3 = len(multisets(L, 3)) * len(multisets(X, 2))
+    return 0, n2, n2 + n3
+
+
+def et_merge_to_typed(g, L, X, pe, gl, lib=None):
+    """Per-edge rows and totals with the edge types summed out, in the
+    typed (node types only) 3-node layout of oracle.paper(k = 3)."""
+    import oracle
+    P = X * (X + 1) // 2
+    rows = np.concatenate([pe[:, :L * X].reshape(-1, L, X).sum(2), pe[:, L * X:].reshape(-1, L, P).sum(2)], 1)
+    glob = np.zeros(oracle.global_slots(L, 3, lib), dtype=np.int64)
+    o0, o1, o2 = et_offsets(L, X)
+    n3 = len(multisets(L, 3))
+    glob[:len(multisets(L, 2))] = gl[o0:o1].reshape(-1, X).sum(1)
+    glob[len(multisets(L, 2)):len(multisets(L, 2)) + n3] = gl[o1:o2].reshape(n3, -1).sum(1)
+    glob[len(multisets(L, 2)) + n3:] = gl[o2:].reshape(n3, -1).sum(1)
+    return rows, glob
+
+
+def edge_typed_pins(lib=None):
+    """Names of the edge-typed pins that fail for an oracle build."""
+    import oracle
+    failed = []
+
+    def check(name, fn):
+        try:
+            if not fn():
+                failed.append(name)
+        except oracle.OracleError:
+            failed.append(name + " (error)")
+
+    for seed in range(6):
+        L, X = [1, 2, 3][seed % 3], [2, 3, 1, 4, 2, 3][seed]
+        g = random_graph(8 + seed, 0.5, L, 900 + seed)
+        xi = edge_types_for(g, X, 950 + seed)
+
+        def vs_brute(g=g, xi=xi, X=X):
+            pe, gl = oracle.edge_typed3(g, xi, X, lib=lib)
+            pb, gb = oracle.edge_typed3_brute(g, xi, X, lib=lib)
+            return np.array_equal(pe, pb) and np.array_equal(gl, gb)
+        check(f"brute seed={seed}", vs_brute)
+
+        def sums_to_typed(g=g, xi=xi, X=X, L=L):
+            pe, gl = oracle.edge_typed3(g, xi, X, lib=lib)
+            rows, glob = et_merge_to_typed(g, L, X, pe, gl, lib)
+            pt, gt = oracle.paper(g, k=3, lib=lib)
+            return np.array_equal(rows, pt) and np.array_equal(glob, gt)
+        check(f"edge-type sums seed={seed}", sums_to_typed)
+
+    def relabelled_edge_types():
+        # a permutation s of the edge types moves path slot (t, x) to (t, s(x))
+        # and triangle slot (t, {x, y}) to (t, {s(x), s(y)})
+        L, X = 2, 3
+        g = random_graph(10, 0.5, L, 977)
+        xi = edge_types_for(g, X, 978)
+        s = np.array([2, 0, 1], dtype=np.uint8)
+        pe, _ = oracle.edge_typed3(g, xi, X, lib=lib)
+        pr, _ = oracle.edge_typed3(g, s[xi], X, lib=lib)
+        pairs_x = multisets(X, 2)
+        want = np.zeros_like(pe)
+        for t in range(L):
+            for x in range(X):
+                want[:, t * X + s[x]] = pe[:, t * X + x]
+            for p, (x, y) in enumerate(pairs_x):
+                q = pairs_x.index(tuple(sorted((int(s[x]), int(s[y])))))
+                want[:, L * X + t * len(pairs_x) + q] = pe[:, L * X + t * len(pairs_x) + p]
+        return np.array_equal(pr, want)
+    check("edge-type relabelling", relabelled_edge_types)
+
+    def typed_triangle():
+        # K3, node types 0 1 1, edge types {0,1}: 0, {0,2}: 1, {1,2}: 2
+        g = graph_from_edges(3, [(0, 1), (0, 2), (1, 2)], [0, 1, 1], 2)
+        xi = edge_types_from(g, lambda u, v: {(0, 1): 0, (0, 2): 1, (1, 2): 2}[(u, v)])
+        pe, gl = oracle.edge_typed3(g, xi, 3, lib=lib)
+        L, X, P = 2, 3, 6
+        want = np.zeros_like(pe)
+        pr = multisets(X, 2)
+        want[0, L * X + 1 * P + pr.index((1, 2))] = 1          # edge {0,1}: node 2 (type 1), edges 1 and 2
+        want[1, L * X + 1 * P + pr.index((0, 2))] = 1          # edge {0,2}: node 1 (type 1), edges 0 and 2
+        want[2, L * X + 0 * P + pr.index((0, 1))] = 1          # edge {1,2}: node 0 (type 0), edges 0 and 1
+        o0, o1, o2 = et_offsets(L, X)
+        wg = np.zeros_like(gl)
+        for (u, v), x in (((0, 1), 0), ((0, 2), 1), ((1, 2), 2)):
+            wg[o0 + multisets(L, 2).index(tuple(sorted((int(g["types"][u]), int(g["types"][v]))))) * X + x] += 1
+        wg[o2 + multisets(L, 3).index((0, 1, 1)) * len(multisets(X, 3)) + multisets(X, 3).index((0, 1, 2))] = 1
+        return np.array_equal(pe, want) and np.array_equal(gl, wg)
+    check("typed triangle", typed_triangle)
+
+    def star():
+        # K_{1,7}: centre 0, leaves 1..7 of one type, edge types 0 for leaves
+        # 1..4 and 1 for leaves 5..7: a leaf's edge of type x sees the other
+        # leaves as paths (type 1, their edge type); 3-paths by edge-type
+        # pair: C(4,2) {0,0}, 4*3 {0,1}, C(3,2) {1,1}
+        g = graph_from_edges(8, [(0, v) for v in range(1, 8)], [0] + [1] * 7, 2)
+        xi = edge_types_from(g, lambda u, v: 0 if v <= 4 else 1)
+        pe, gl = oracle.edge_typed3(g, xi, 2, lib=lib)
+        L, X = 2, 2
+        ok = True
+        for e, leaf in enumerate(range(1, 8)):
+            n0 = 4 - (1 if leaf <= 4 else 0)
+            n1 = 3 - (1 if leaf > 4 else 0)
+            ok &= pe[e, 1 * X + 0] == n0 and pe[e, 1 * X + 1] == n1 and pe[e].sum() == n0 + n1
+        o0, o1, o2 = et_offsets(L, X)
+        r3 = multisets(L, 3).index((0, 1, 1)) * len(multisets(X, 2))
+        ok &= gl[o1 + r3 + multisets(X, 2).index((0, 0))] == 6
+        ok &= gl[o1 + r3 + multisets(X, 2).index((0, 1))] == 12
+        ok &= gl[o1 + r3 + multisets(X, 2).index((1, 1))] == 3
+        ok &= gl[o1:o2].sum() == 21 and gl[o2:].sum() == 0
+        return bool(ok)
+    check("star", star)
+    return failed

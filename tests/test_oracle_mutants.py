@@ -9,7 +9,8 @@ triangles booked as 4-cycles and D missing one endpoint of each edge; in
 the position-aware counts of Sec. 5, the two sides of a 4-cycle key swapped
 and the degree-3 side of a tailed triangle swapped; in the directed counts
 of Sec. 4.8, the signs of S_j flipped and the edge's own orientation
-dropped from the class key.  The pin battery here (closed forms,
+dropped from the class key; in the edge-typed counts, a 3-path of S_j keyed
+by the edge's own type and a triangle keyed without j's edge.  The pin battery here (closed forms,
 layout enumeration, the brute-force and networkx-free subset count) must
 reject every one of them, on the CPU.
 """
@@ -20,9 +21,9 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_pins import (BLOCK_EDGES, burnside, directed_pins, expected_clique, expected_complete_bipartite,
-                         expected_cycle, expected_star, global_slot_pa, graph_from_edges, multisets, random_graph,
-                         slot_instance)
+from oracle_pins import (BLOCK_EDGES, burnside, directed_pins, edge_typed_pins, expected_clique,
+                         expected_complete_bipartite, expected_cycle, expected_star, global_slot_pa, graph_from_edges,
+                         multisets, random_graph, slot_instance)
 
 MUTANTS = {
     1: "Lemma 1 without the 4-cycle term",
@@ -39,6 +40,8 @@ MUTANTS = {
     12: "Sec. 5 tailed-triangle edge at the degree-3 node booked on the other side",
     13: "Sec. 4.8 S_j counted with the opposite arc direction",
     14: "Sec. 4.8 class key without the edge's own orientation",
+    15: "edge-typed 3-path of S_j keyed by the edge's own type",
+    16: "edge-typed triangle keyed without j's edge to the third node",
 }
 
 
@@ -122,6 +125,7 @@ def _battery(lib) -> list:
                        for b in range(9))
         check(f"position-aware seed={seed}", pa_sums)
     failed += directed_pins(lib)
+    failed += edge_typed_pins(lib)
     return failed
 
 
