@@ -76,6 +76,8 @@ def parse():
                     help="batched / serve: oracle time budget of that check (0: no limit)")
     ap.add_argument("--position-aware", action="store_true",
                     help="plain mode: also time the position-aware count (Sec. 5) of the same graph")
+    ap.add_argument("--edge-typed", action="store_true",
+                    help="plain mode: also time the edge-typed 3-node count of the workload, 4 seeded edge types")
     ap.add_argument("--directed", action="store_true",
                     help="plain mode: also time the directed typed 3-node count (Sec. 4.8) of the workload's "
                          "edges oriented by a seeded coin")
@@ -668,6 +670,48 @@ def run_ours(args):
                     "step": "tg_build_directed + tg_count_directed3 + tg_free, device-resident; each edge of the "
                             "workload oriented by a seeded coin"}
 
+    # edge-typed 3-node counts (Def. 1's edge types) of the same graph, 4
+    # seeded edge types: tg_build_edge_typed + tg_count_edge_typed3 per step
+    edge_typed = None
+    if args.edge_typed and rank == 0:
+        X = 4
+        xi = torch.as_tensor(graphgen.edge_types(g, X, CPU_SEED + 49), device=dev)
+        lay_x = tg.tg_edge_typed_layout(L, X)
+        pe_x = torch.empty((m, lay_x["per_edge_slots"]), dtype=torch.int32, device=dev)
+        gl_x = torch.empty(lay_x["global_slots"], dtype=torch.int64, device=dev)
+        x_ms = {}
+
+        def x_step(timing: bool):
+            h = tg.tg_build_edge_typed(rp, col, ty, xi, L, X, stream=stream)
+            if timing:
+                tg.tg_set_timing(h, True)
+            tg.tg_count_edge_typed3(h, pe_x, gl_x, stream=stream)
+            if timing:
+                for name, (kms, nl) in tg.tg_get_timing(h).items():
+                    x_ms[name] = x_ms.get(name, 0.0) + kms
+            st = tg.tg_query_status(h) if timing else 0
+            h.free()
+            return st
+
+        for _ in range(args.warmup):
+            x_step(False)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        x_status = 0
+        for _ in range(args.steps):
+            x_status = x_status or x_step(True)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        xms = b0.elapsed_time(b1)
+        edge_typed = {"value": round(m * args.steps / (xms / 1e3), 1), "unit": UNIT,
+                      "ms_per_step": round(xms / args.steps, 3), "status": tg.STATUS[x_status], "edge_types": X,
+                      "per_edge_slots": lay_x["per_edge_slots"], "global_slots": lay_x["global_slots"],
+                      "k_edge_typed3_ms_per_step": round(x_ms.get("k_edge_typed3", 0.0) / args.steps, 3),
+                      "step": "tg_build_edge_typed + tg_count_edge_typed3 + tg_free, device-resident; each edge "
+                              "of the workload typed by a seeded hash"}
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(g)
@@ -692,6 +736,8 @@ def run_ours(args):
             line["position_aware"] = position_aware
         if directed is not None:
             line["directed"] = directed
+        if edge_typed is not None:
+            line["edge_typed"] = edge_typed
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -103,6 +103,22 @@ def zipf_types(n: int, L: int, s: float, seed: int) -> np.ndarray:
     return t
 
 
+def edge_types(g: dict, X: int, seed: int) -> np.ndarray:
+    """One seeded edge type in [0, X) per entry of col, the same on both
+    entries of an edge: SplitMix64 (Steele, Lea and Flood 2014) of the pair
+    key min(u, v) * n + max(u, v), offset by the seed."""
+    rp, n = g["row_ptr"], int(g["n"])
+    col = g["col"].astype(np.uint64)
+    rows = np.repeat(np.arange(n, dtype=np.uint64), np.diff(rp))
+    gamma = 0x9E3779B97F4A7C15
+    offset = np.uint64(((seed + 1) * gamma) & 0xFFFFFFFFFFFFFFFF)
+    z = np.minimum(rows, col) * np.uint64(n) + np.maximum(rows, col) + offset
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    z ^= z >> np.uint64(31)
+    return (z % np.uint64(X)).astype(np.uint8)
+
+
 def erdos_renyi(n: int, m: int, L: int, seed: int) -> dict:
     """G(n, m): m distinct pairs uniform over all C(n,2); types uniform over L."""
     lib = _load()

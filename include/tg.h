@@ -430,6 +430,58 @@ tg_status tg_build_directed(int64_t n, int64_t n_arcs, const int64_t *out_row_pt
  * TG_ERR_CUDA. */
 tg_status tg_count_directed3(tg_graph *g, uint32_t *per_edge_out, int64_t *global_out, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Edge-typed typed 3-node graphlets (Def. 1's edge types xi; Defs. 4-5: the
+ * class of a typed graphlet is its shape with the multisets of its node
+ * types and of its edge types).
+ *
+ * Input: the symmetric CSR of tg_build plus edge_types (uint8, one per
+ * entry of col, in [0, X)); the two entries of an edge must carry the same
+ * type.  1 <= X <= TG_MAX_EDGE_TYPES.  Host or device pointers.
+ *
+ * Edges are numbered like tg_build's.  For edge {i, j} and each third node
+ * w of type t, per edge uint32 slots:
+ *   [0, L*X)       3-paths: slot t*X + x, x the type of w's edge to i (w in
+ *                  S_i) or to j (w in S_j) -- the path's class is the same;
+ *   [L*X, S)       triangles: slot L*X + t*P + rank(x, y), P = X(X+1)/2,
+ *                  {x, y} the types of w's edges to i and j, ranked as a
+ *                  sorted pair over [0, X) in lexicographic order.
+ * Global, int64, three blocks: edges (multisets of 2 node types x X edge
+ * types: rank2*X + xi), 3-paths (multisets of 3 node types x multisets of
+ * 2 edge types: rank3*C(X+1,2) + rank2), triangles (multisets of 3 node
+ * types x multisets of 3 edge types: rank3*C(X+2,3) + rank3); multisets
+ * sorted and ranked lexicographically; each instance counted once. */
+#define TG_MAX_EDGE_TYPES 4
+
+typedef struct {
+    int32_t L, X;
+    int64_t per_edge_slots;           /* L*X + L*X*(X+1)/2 */
+    int64_t triangle_offset;          /* L*X */
+    int64_t global_slots;
+    int64_t global_block_offset[3];   /* edges, 3-paths, triangles */
+    int64_t global_block_size[3];
+} tg_edge_typed_layout_t;
+
+/* Pure host function.  Errors: TG_ERR_TOO_MANY_TYPES (L or X), TG_ERR_INVALID_ARG. */
+tg_status tg_edge_typed_layout(int32_t L, int32_t X, tg_edge_typed_layout_t *out);
+
+/* Builds a handle for edge-typed counting (above).  Stream-ordered;
+ * synchronises to validate.  Errors: TG_ERR_INVALID_ARG,
+ * TG_ERR_TOO_MANY_TYPES, TG_ERR_INVALID_GRAPH (tg_build's checks, an edge
+ * type out of range or different on an edge's two entries),
+ * TG_ERR_TOO_LARGE, TG_ERR_OOM, TG_ERR_CUDA.  The handle also serves
+ * tg_count and the other node-typed calls. */
+tg_status tg_build_edge_typed(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                              const uint8_t *node_types, const uint8_t *edge_types, int32_t L, int32_t X,
+                              const tg_options *opt, void *stream, tg_graph **out);
+
+/* Edge-typed 3-node counts of a tg_build_edge_typed handle: per_edge_out
+ * uint32 [m][per_edge_slots] (may be NULL), global_out int64
+ * [global_slots] (may be NULL); host or device.  Device-detected errors
+ * through tg_query_status.  Errors: TG_ERR_INVALID_ARG (not an edge-typed
+ * handle), TG_ERR_OOM, TG_ERR_CUDA. */
+tg_status tg_count_edge_typed3(tg_graph *g, uint32_t *per_edge_out, int64_t *global_out, void *stream);
+
 /* Work counters (diagnostics for the benchmark's roofline; no effect on the
  * counts).  While enabled, the counting kernels add the units of work they
  * did to per-handle counters, slot TG_WORK_*: the set-of-T lookups of the

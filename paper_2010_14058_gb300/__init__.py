@@ -17,7 +17,8 @@ from .tg import (Graph, LibraryMissing, STATUS, STATUS_CODE, TGError, TG_MAX_TYP
                  tg_get_timing, tg_graphlet_weights, tg_last_error, tg_layout, tg_pa_labelling, tg_pa_layout,
                  tg_pa_slot_class, tg_query_status, tg_set_timing, tg_status_string,
                  tg_set_work_counting, tg_get_work, tg_build_directed, tg_count_directed3, tg_directed_layout,
-                 tg_directed_class_code, tg_count_handles)
+                 tg_directed_class_code, tg_count_handles, tg_build_edge_typed, tg_edge_typed_layout,
+                 tg_count_edge_typed3)
 
 __all__ = ["Graph", "LibraryMissing", "STATUS", "STATUS_CODE", "TGError", "TG_MAX_TYPES", "load", "tg_abi_version",
            "tg_build", "tg_build_batch", "tg_count", "tg_count3_static", "tg_count_batch", "tg_count_position_aware",
@@ -25,7 +26,8 @@ __all__ = ["Graph", "LibraryMissing", "STATUS", "STATUS_CODE", "TGError", "TG_MA
            "tg_free", "tg_get_timing", "tg_graphlet_weights", "tg_last_error", "tg_layout", "tg_pa_labelling",
            "tg_pa_layout", "tg_pa_slot_class", "tg_query_status", "tg_set_timing", "tg_status_string",
            "tg_set_work_counting", "tg_get_work", "tg_build_directed", "tg_count_directed3", "tg_directed_layout",
-           "tg_directed_class_code", "tg_count_handles",
+           "tg_directed_class_code", "tg_count_handles", "tg_build_edge_typed", "tg_edge_typed_layout",
+           "tg_count_edge_typed3",
            "to_device", "count"]
 
 

@@ -277,6 +277,83 @@ tg_status tg_count_directed3(tg_graph *gh, uint32_t *per_edge_out, int64_t *glob
     });
 }
 
+tg_status tg_edge_typed_layout(int32_t L, int32_t X, tg_edge_typed_layout_t *out) {
+    return guarded([&] {
+        check_types(L);
+        if (X < 1 || X > TG_MAX_EDGE_TYPES) throw Error{TG_ERR_TOO_MANY_TYPES, "edge types"};
+        if (!out) throw Error{TG_ERR_INVALID_ARG, "NULL"};
+        tg_edge_typed_layout_t r;
+        std::memset(&r, 0, sizeof(r));
+        r.L = L;
+        r.X = X;
+        const int64_t P = (int64_t)X * (X + 1) / 2;
+        r.per_edge_slots = (int64_t)L * X + (int64_t)L * P;
+        r.triangle_offset = (int64_t)L * X;
+        const int64_t c2 = (int64_t)L * (L + 1) / 2, c3 = (int64_t)L * (L + 1) * (L + 2) / 6;
+        r.global_block_size[0] = c2 * X;
+        r.global_block_size[1] = c3 * P;
+        r.global_block_size[2] = c3 * ((int64_t)X * (X + 1) * (X + 2) / 6);
+        r.global_block_offset[0] = 0;
+        r.global_block_offset[1] = r.global_block_size[0];
+        r.global_block_offset[2] = r.global_block_size[0] + r.global_block_size[1];
+        r.global_slots = tg::edge_typed_global_slots(L, X);
+        *out = r;
+    });
+}
+
+tg_status tg_build_edge_typed(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                              const uint8_t *node_types, const uint8_t *edge_types, int32_t L, int32_t X,
+                              const tg_options *opt, void *stream, tg_graph **out) {
+    return guarded([&] {
+        if (!out) throw Error{TG_ERR_INVALID_ARG, "out"};
+        *out = nullptr;
+        check_types(L);
+        if (X < 1 || X > TG_MAX_EDGE_TYPES) throw Error{TG_ERR_TOO_MANY_TYPES, "edge types"};
+        if (nnz > 0 && !edge_types) throw Error{TG_ERR_INVALID_ARG, "edge_types"};
+        cudaStream_t s = (cudaStream_t)stream;
+        const int64_t off[2] = {0, n};
+        tg_graph *h = nullptr;
+        build_common(1, off, n, nnz, row_ptr, col, node_types, L, opt, stream, &h);
+        try {
+            // device copies of the caller's CSR positions and their edge types
+            tg::TBuf drp(sizeof(int64_t) * (n + 1), s), dcol(sizeof(int32_t) * std::max<int64_t>(nnz, 1), s),
+                dxi(std::max<int64_t>(nnz, 1), s);
+            auto kind = [](const void *p) {
+                return tg::is_device_pointer(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            };
+            TG_CK(cudaMemcpyAsync(drp.p, row_ptr, sizeof(int64_t) * (n + 1), kind(row_ptr), s));
+            if (nnz > 0) {
+                TG_CK(cudaMemcpyAsync(dcol.p, col, sizeof(int32_t) * nnz, kind(col), s));
+                TG_CK(cudaMemcpyAsync(dxi.p, edge_types, nnz, kind(edge_types), s));
+            }
+            tg::prepare_edge_typed(h->g, X, drp.as<int64_t>(), dcol.as<int32_t>(), dxi.as<uint8_t>(), s);
+        } catch (...) {
+            tg_free(h);
+            throw;
+        }
+        *out = h;
+    });
+}
+
+tg_status tg_count_edge_typed3(tg_graph *gh, uint32_t *per_edge_out, int64_t *global_out, void *stream) {
+    return guarded([&] {
+        if (!gh || !gh->g.edge_typed) throw Error{TG_ERR_INVALID_ARG, "not an edge-typed handle"};
+        Graph &G = gh->g;
+        cudaStream_t s = (cudaStream_t)stream;
+        G.stream = s;
+        const int64_t X = G.et_X, P = X * (X + 1) / 2;
+        const size_t pe_bytes = (size_t)G.m * (size_t)(G.L * X + G.L * P) * sizeof(uint32_t);
+        const size_t gl_bytes = (size_t)G.et_global * sizeof(int64_t);
+        bool pe_staged = false, gl_staged = false;
+        uint32_t *pe = device_out(per_edge_out, pe_bytes, G.stage_pe, pe_staged);
+        int64_t *gl = device_out(global_out, gl_bytes, G.stage_gl, gl_staged);
+        G.last_launches = tg::run_edge_typed3(G, pe, gl, s);
+        if (pe_staged && pe_bytes) TG_CK(cudaMemcpyAsync(per_edge_out, pe, pe_bytes, cudaMemcpyDeviceToHost, s));
+        if (gl_staged) TG_CK(cudaMemcpyAsync(global_out, gl, gl_bytes, cudaMemcpyDeviceToHost, s));
+        if (pe_staged || gl_staged) TG_CK(cudaStreamSynchronize(s));
+    });
+}
+
 void tg_free(tg_graph *g) {
     if (!g) return;
     cudaStreamSynchronize(g->g.stream);

@@ -158,6 +158,12 @@ struct Graph {
     DBuf dsign, doutdeg, dcls, darcs, dgacc;
     int64_t d_global = 0;
     bool directed = false;
+    // edge-typed counts (tg_edge_typed.cu): edge type per slot, per-node
+    // neighbour counts by (node type, edge type), the totals' accumulator
+    DBuf etype, etdeg, etgacc;
+    int32_t et_X = 0;
+    int64_t et_global = 0;
+    bool edge_typed = false;
     int64_t hub_stride = 0, hub_buf_words = 0;  // words per hub table, per buffer
     bool hub_packed = false;                    // two 16-bit counters per word
     // counting state
@@ -245,7 +251,7 @@ struct Graph {
                              &e_slot_lo, &e_slot_hi, &delta, &anchors_light, &anchors_heavy, &edges_light,
                              &edges_heavy, &C, &tau, &A, &tables, &gacc, &status, &tiles_full, &stage_pe,
                              &stage_gl, &tcount, &toffs, &tlist, &tsum, &kmat, &big_list, &big_count, &scan_tmp,
-                             &set_scratch, &work, &hub_tables, &dsign, &doutdeg, &dcls, &darcs, &dgacc, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_rec,
+                             &set_scratch, &work, &hub_tables, &dsign, &doutdeg, &dcls, &darcs, &dgacc, &etype, &etdeg, &etgacc, &plus_off, &plus_adj, &hubs, &hub_base, &item_woff, &item_rec,
                 &pa_cls, &pa_gacc};
     }
     int64_t device_bytes() const {
@@ -333,6 +339,11 @@ void symmetrize_arcs(int64_t n, int64_t na, const int64_t *orp, const int32_t *o
                      int32_t *src, cudaStream_t s);
 void prepare_directed(Graph &G, int64_t na, const int32_t *src, const int32_t *ocol, cudaStream_t s);
 int64_t run_directed3(Graph &G, uint32_t *per_edge_out, int64_t *global_out, cudaStream_t s);
+// Edge-typed 3-node graphlets (tg_edge_typed.cu).
+int64_t edge_typed_global_slots(int L, int X);
+void prepare_edge_typed(Graph &G, int X, const int64_t *row_ptr, const int32_t *col, const uint8_t *edge_types,
+                        cudaStream_t s);
+int64_t run_edge_typed3(Graph &G, uint32_t *per_edge_out, int64_t *global_out, cudaStream_t s);
 // Sparse per-edge counts (tg_sparse.cu): returns the number of nonzero
 // pairs; writes them only while they fit `cap` (fits = false otherwise).
 int64_t count_sparse(Graph &G, int k, int64_t *row_off, uint16_t *slot, uint32_t *value, int64_t cap, bool &fits,

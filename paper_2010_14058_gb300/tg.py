@@ -41,6 +41,12 @@ class tg_pa_layout_t(ctypes.Structure):
                 ("global_block_size", ctypes.c_int64 * 9), ("graphlet_edges", ctypes.c_int32 * 9)]
 
 
+class tg_edge_typed_layout_t(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("X", ctypes.c_int32), ("per_edge_slots", ctypes.c_int64),
+                ("triangle_offset", ctypes.c_int64), ("global_slots", ctypes.c_int64),
+                ("global_block_offset", ctypes.c_int64 * 3), ("global_block_size", ctypes.c_int64 * 3)]
+
+
 class tg_directed_layout_t(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("per_edge_slots", ctypes.c_int64), ("global_slots", ctypes.c_int64),
                 ("classes", ctypes.c_int64)]
@@ -77,6 +83,10 @@ SIGNATURES = {
     "tg_build_directed": ([_i64, _i64, _vp, _vp, _vp, _i32, ctypes.POINTER(tg_options), _vp, ctypes.POINTER(_vp)],
                           _i32),
     "tg_count_directed3": ([_vp, _vp, _vp, _vp], _i32),
+    "tg_edge_typed_layout": ([_i32, _i32, ctypes.POINTER(tg_edge_typed_layout_t)], _i32),
+    "tg_build_edge_typed": ([_i64, _i64, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.POINTER(tg_options), _vp,
+                             ctypes.POINTER(_vp)], _i32),
+    "tg_count_edge_typed3": ([_vp, _vp, _vp, _vp], _i32),
     "tg_count_handles": ([_vp, _i32, _i32, _vp, _vp], _i32),
     "tg_pa_labelling": ([_i32, _i32, _i64, _vp], _i32),
     "tg_pa_slot_class": ([_i32, _i32, _i32, _i64, ctypes.POINTER(_i64)], _i32),
@@ -290,6 +300,31 @@ def tg_directed_class_code(L: int, rank: int) -> tuple:
 def tg_count_directed3(g: Graph, per_edge_out=None, global_out=None, stream=None) -> None:
     _check(load().tg_count_directed3(g.handle, _ptr(per_edge_out), _ptr(global_out), _stream(stream)),
            "tg_count_directed3")
+
+
+def tg_build_edge_typed(row_ptr, col, node_types, edge_types, L: int, X: int, options: dict | None = None,
+                        stream=None) -> Graph:
+    """Handle of a graph whose edges carry types too (one per entry of col, the
+    same on both entries of an edge; Def. 1's xi)."""
+    n = int(row_ptr.shape[0]) - 1
+    nnz = int(col.shape[0])
+    h = _vp()
+    _check(load().tg_build_edge_typed(n, nnz, _ptr(row_ptr), _ptr(col), _ptr(node_types), _ptr(edge_types), L, X,
+                                      _options(options), _stream(stream), ctypes.byref(h)), "tg_build_edge_typed")
+    return Graph(h.value)
+
+
+def tg_edge_typed_layout(L: int, X: int) -> dict:
+    lay = tg_edge_typed_layout_t()
+    _check(load().tg_edge_typed_layout(L, X, ctypes.byref(lay)), "tg_edge_typed_layout")
+    return {"L": lay.L, "X": lay.X, "per_edge_slots": lay.per_edge_slots, "triangle_offset": lay.triangle_offset,
+            "global_slots": lay.global_slots, "global_block_offset": list(lay.global_block_offset),
+            "global_block_size": list(lay.global_block_size)}
+
+
+def tg_count_edge_typed3(g: Graph, per_edge_out=None, global_out=None, stream=None) -> None:
+    _check(load().tg_count_edge_typed3(g.handle, _ptr(per_edge_out), _ptr(global_out), _stream(stream)),
+           "tg_count_edge_typed3")
 
 
 def tg_count_handles(graphs: list, k: int, global_out, stream=None) -> None:

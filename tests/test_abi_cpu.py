@@ -161,3 +161,15 @@ def test_directed_layout_and_class_codes_match_oracle(L, lib):
         assert oracle.directed_class(L, t, a) == r          # each representative is in its class
     with pytest.raises(tg.TGError):
         tg.tg_directed_class_code(L, lay["classes"])
+
+
+@pytest.mark.parametrize("L,X", [(1, 1), (2, 3), (5, 4), (8, 4)])
+def test_edge_typed_layout_matches_oracle(L, X, lib):
+    import paper_2010_14058_gb300 as tg
+    lay = tg.tg_edge_typed_layout(L, X)
+    assert lay["per_edge_slots"] == oracle.edge_typed_per_edge_slots(L, X)
+    assert lay["triangle_offset"] == L * X
+    assert lay["global_slots"] == oracle.edge_typed_global_slots(L, X)
+    assert lay["global_block_offset"] == [0, lay["global_block_size"][0], sum(lay["global_block_size"][:2])]
+    with pytest.raises(tg.TGError):
+        tg.tg_edge_typed_layout(L, 5)                  # more edge types than TG_MAX_EDGE_TYPES
