@@ -52,3 +52,16 @@ def test_out_of_range_types_are_rejected():
     xi = np.full(len(g["col"]), 2, dtype=np.uint8)
     with pytest.raises(oracle.OracleError):
         oracle.edge_typed3(g, xi, 2)
+
+
+def test_seeded_edge_types_are_symmetric_and_reproducible():
+    # the bench's input generator: one type per edge on both of its entries,
+    # the same for the same seed, spread over [0, X)
+    import graphgen
+    g = graphgen.chung_lu(3000, 20000, 2.1, 600.0, 3, 17)
+    xi = graphgen.edge_types(g, 4, 99)
+    assert np.array_equal(xi, graphgen.edge_types(g, 4, 99))
+    assert not np.array_equal(xi, graphgen.edge_types(g, 4, 98))
+    pe, gl = oracle.edge_typed3(g, xi, 4, per_edge=False)        # rejects unequal entries
+    counts = np.bincount(xi, minlength=4)
+    assert counts.min() > 0.2 * len(xi) and xi.max() < 4
